@@ -1,0 +1,200 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws random numbers and lays matrices out in memory; it holds
+none of the factorisation or inversion arithmetic.  Both the GPU tests and the
+CPU oracle take their inputs from here, so the two sides always see the same
+matrices.  Every generator works in float64 / complex128 on the host and the
+caller casts to the working precision.
+
+Layouts (shared with the C-ABI): matrix b has order n[b] and starts at element
+off[b] of a flat buffer.  Layout 0 = dense row-major n*n; layout 1 = upper
+triangle packed row by row (row i holds columns i..n-1), n(n+1)/2 elements.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+LAYOUT_DENSE = 0
+LAYOUT_PACKED = 1
+
+
+def tri(n):
+    """Number of elements in the upper triangle of an n x n matrix."""
+    return n * (n + 1) // 2
+
+
+@dataclass
+class Batch:
+    """A flat batch of Hermitian matrices plus their sizes and offsets."""
+    A: np.ndarray            # flat, float64 or complex128
+    n: np.ndarray            # int32 [batch]
+    off: np.ndarray          # int64 [batch]
+    layout: int
+    kappa: np.ndarray | None = None   # per-matrix 2-norm condition number, when the generator fixes it
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def batch(self):
+        return int(self.n.shape[0])
+
+    @property
+    def is_complex(self):
+        return np.iscomplexobj(self.A)
+
+    def matrix(self, b):
+        """Dense upper-triangular view (lower part zero) of matrix b, as a new array."""
+        n = int(self.n[b]); o = int(self.off[b])
+        M = np.zeros((n, n), dtype=self.A.dtype)
+        iu = np.triu_indices(n)
+        if self.layout == LAYOUT_PACKED:
+            M[iu] = self.A[o:o + tri(n)]
+        else:
+            M[iu] = self.A[o:o + n * n].reshape(n, n)[iu]
+        return M
+
+    def sizes_offsets(self):
+        return self.n, self.off
+
+
+def layout_offsets(n, layout):
+    """Contiguous element offsets for sizes n in the given layout."""
+    n = np.asarray(n, dtype=np.int64)
+    per = tri(n) if layout == LAYOUT_PACKED else n * n
+    off = np.zeros(n.shape[0], dtype=np.int64)
+    if n.shape[0] > 1:
+        off[1:] = np.cumsum(per)[:-1]
+    total = int(per.sum()) if n.shape[0] else 0
+    return off, total
+
+
+def pack(dense_by_index, n, layout, dtype):
+    """Lay out full matrices (a dict size -> (indices, stack)) into one flat buffer."""
+    off, total = layout_offsets(n, layout)
+    A = np.zeros(total, dtype=dtype)
+    for N, (idx, stack) in dense_by_index.items():
+        if len(idx) == 0:
+            continue
+        if layout == LAYOUT_PACKED:
+            iu = np.triu_indices(N)
+            vals = stack[:, iu[0], iu[1]]                       # [m, T]
+            pos = off[idx][:, None] + np.arange(tri(N))[None, :]
+        else:
+            vals = stack.reshape(len(idx), N * N)
+            pos = off[idx][:, None] + np.arange(N * N)[None, :]
+        A[pos] = vals
+    return A, off
+
+
+def _group(n):
+    out = {}
+    for N in np.unique(n):
+        out[int(N)] = np.nonzero(n == N)[0]
+    return out
+
+
+def _haar_orthogonal(rng, m, N):
+    """Q from the Householder QR of an N x N Gaussian, R's diagonal made positive."""
+    G = rng.standard_normal((m, N, N))
+    Q, Rq = np.linalg.qr(G)
+    s = np.sign(np.diagonal(Rq, axis1=1, axis2=2)).copy()
+    s[s == 0] = 1.0
+    return Q * s[:, None, :]
+
+
+def spd_gram_shift(batch, N, shift, seed, layout=LAYOUT_DENSE):
+    """A = B B^T + shift*I with B iid N(0,1), N x N (real)."""
+    rng = np.random.default_rng(seed)
+    B = rng.standard_normal((batch, N, N))
+    A = B @ np.transpose(B, (0, 2, 1)) + shift * np.eye(N)
+    A = 0.5 * (A + np.transpose(A, (0, 2, 1)))
+    n = np.full(batch, N, dtype=np.int32)
+    flat, off = pack({N: (np.arange(batch), A)}, n, layout, np.float64)
+    return Batch(flat, n, off, layout, meta={"kind": "gram_shift", "N": N, "shift": shift, "seed": seed})
+
+
+def mimo_covariance(batch, sizes=(4, 8, 16), sigma2=0.1, seed=1001, layout=LAYOUT_PACKED, chunk=65536,
+                    shuffle=True):
+    """A = H^H H + sigma2*I, H a 2N x N matrix of iid CN(0,1) entries (complex).
+
+    The batch holds the sizes in equal shares (the first batch % len(sizes)
+    sizes get one more), in an order shuffled with the seed.
+    """
+    rng = np.random.default_rng(seed)
+    k = len(sizes)
+    counts = [batch // k + (1 if i < batch % k else 0) for i in range(k)]
+    n = np.concatenate([np.full(c, s, dtype=np.int32) for s, c in zip(sizes, counts)])
+    if shuffle:
+        n = n[rng.permutation(batch)]
+    groups = _group(n)
+    dense = {}
+    for N, idx in groups.items():
+        stacks = []
+        for s in range(0, len(idx), chunk):
+            m = min(chunk, len(idx) - s)
+            H = (rng.standard_normal((m, 2 * N, N)) + 1j * rng.standard_normal((m, 2 * N, N))) * np.sqrt(0.5)
+            A = np.conj(np.transpose(H, (0, 2, 1))) @ H
+            A += sigma2 * np.eye(N)
+            stacks.append(A)
+        dense[N] = (idx, np.concatenate(stacks))
+    flat, off = pack(dense, n, layout, np.complex128)
+    return Batch(flat, n, off, layout, meta={"kind": "mimo", "sizes": list(sizes), "sigma2": sigma2, "seed": seed})
+
+
+def qr_spectrum(batch, n_of, lam_of, seed, layout=LAYOUT_DENSE, chunk=8192):
+    """A = Q diag(lam) Q^T, Q Haar-orthogonal from Householder QR of a Gaussian.
+
+    n_of(rng, batch) -> int32 sizes; lam_of(rng, m, N) -> [m, N] eigenvalues.
+    The result is symmetrised in float64.  kappa holds max(lam)/min(lam).
+    """
+    rng = np.random.default_rng(seed)
+    n = np.asarray(n_of(rng, batch), dtype=np.int32)
+    kappa = np.zeros(batch)
+    dense = {}
+    for N, idx in _group(n).items():
+        stacks = []
+        for s in range(0, len(idx), chunk):
+            m = min(chunk, len(idx) - s)
+            Q = _haar_orthogonal(rng, m, N)
+            lam = np.asarray(lam_of(rng, m, N), dtype=np.float64)
+            A = (Q * lam[:, None, :]) @ np.transpose(Q, (0, 2, 1))
+            A = 0.5 * (A + np.transpose(A, (0, 2, 1)))
+            stacks.append(A)
+            kappa[idx[s:s + m]] = lam.max(axis=1) / lam.min(axis=1)
+        dense[N] = (idx, np.concatenate(stacks))
+    flat, off = pack(dense, n, layout, np.float64)
+    return Batch(flat, n, off, layout, kappa=kappa, meta={"kind": "qr_spectrum", "seed": seed})
+
+
+def uneven_loguniform(batch, nmin=2, nmax=64, decades=3.0, seed=1002, layout=LAYOUT_DENSE):
+    """N ~ U{nmin..nmax}; lam_i = 10^U(0, decades) (log-uniform in [1, 10^decades])."""
+    return qr_spectrum(batch,
+                       lambda rng, b: rng.integers(nmin, nmax + 1, size=b),
+                       lambda rng, m, N: 10.0 ** rng.uniform(0.0, decades, size=(m, N)),
+                       seed, layout)
+
+
+def fixed_kappa(batch, N, kappa, seed=1003, layout=LAYOUT_DENSE):
+    """lam_1 = 1, lam_N = kappa, the rest log-uniform in between (kappa exact)."""
+    def lam(rng, m, NN):
+        L = 10.0 ** rng.uniform(0.0, np.log10(kappa), size=(m, NN))
+        L[:, 0] = 1.0
+        L[:, -1] = kappa
+        return L
+    return qr_spectrum(batch, lambda rng, b: np.full(b, N), lam, seed, layout)
+
+
+def log_spaced(N, decades=4.0, seed=1004, layout=LAYOUT_DENSE):
+    """A single matrix with lam_i = 10^(decades*(i-1)/(N-1))."""
+    return qr_spectrum(1, lambda rng, b: np.full(b, N),
+                       lambda rng, m, NN: np.tile(10.0 ** (decades * np.arange(NN) / max(NN - 1, 1)), (m, 1)),
+                       seed, layout, chunk=1)
+
+
+def gaussian(shape, seed, complex_=False):
+    """iid N(0,1) (complex: CN(0,1)) array, e.g. the weights W of a loss sum(W o X)."""
+    rng = np.random.default_rng(seed)
+    if complex_:
+        return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) * np.sqrt(0.5)
+    return rng.standard_normal(shape)
