@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Throughput benchmark: batched Cholesky + direct inverse of 1,048,576 complex
+MIMO covariance matrices (N in {4, 8, 16}, one third each, shuffled;
+A = H^H H + 0.1 I with H a 2N x N matrix of iid CN(0,1) entries), complex64
+inputs and FP32 arithmetic, upper triangles packed, one CUDA-graph replay per
+step.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU FP64 oracle (the plain C implementation the
+tests check against) on this machine's host cores.  Under torchrun each rank
+inverts its own batch (weak scaling; no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BATCH = 1 << 20
+SIZES = (4, 8, 16)
+SIGMA2 = 0.1
+SEED = 1001
+METRIC = "inverses/s"
+WORKLOAD = "mimo_covariance_c64_N4-8-16_x1048576_packed"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true",
+                    help="time the device step only (no accuracy check, FP64 form, e2e or CPU baseline); "
+                         "for profiler runs")
+    ap.add_argument("--batch", type=int, default=BATCH, help="matrices per GPU (profiling cases)")
+    ap.add_argument("--sizes", default=",".join(map(str, SIZES)), help="matrix orders, equal shares")
+    return ap.parse_args()
+
+
+def tri(n):
+    return n * (n + 1) // 2
+
+
+def alg_bytes(n, elem_bytes):
+    """Algorithmic bytes of one pass: the upper triangle of A read, that of X written."""
+    t = (np.asarray(n, dtype=np.int64) * (np.asarray(n, dtype=np.int64) + 1)) // 2
+    return int(2 * t.sum() * elem_bytes)
+
+
+def alg_flops(n, cplx=True):
+    """Algorithmic flops: (N^3 - N)/2 multiply-adds per matrix (Table 1's 1/2 n^3),
+    a complex multiply-add counted as 8 real flops."""
+    n = np.asarray(n, dtype=np.int64)
+    macs = ((n ** 3 - n) // 2).sum()
+    return int(macs * (8 if cplx else 2))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the GPU is busy."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [r for r in rows if r[2] > 0.5 * max(x[2] for x in rows)] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in loaded])), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(loaded), "power_w_max": max(r[2] for r in rows)}
+
+
+def make_workload(rank, batch=BATCH, sizes=SIZES):
+    from paper_1111_4144_gb300 import workloads as wl
+    return wl.mimo_covariance(batch, sizes=sizes, sigma2=SIGMA2, seed=SEED + rank, layout=wl.LAYOUT_PACKED)
+
+
+def oracle_time(b, A_wide, min_wall=1.0):
+    """Time the CPU oracle on this batch; returns (inverses/s, threads, reps, result)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    reps, t0 = 0, time.perf_counter()
+    res = None
+    while True:
+        res = oracle.inv_batch(A_wide, b.n, b.off, 1, True, nthreads=threads)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_wall:
+            break
+    return reps * b.batch / el, threads, reps, res
+
+
+def upper_err_ratio(b, Xg, Xo, kappa, fp64):
+    """max over matrices of (relative Frobenius error of the upper triangle) / tolerance."""
+    n = b.n.astype(np.int64)
+    t = n * (n + 1) // 2
+    seg = np.repeat(np.arange(b.batch), t)
+    d = np.abs(Xg.astype(np.complex128) - Xo) ** 2
+    num = np.sqrt(np.bincount(seg, weights=d, minlength=b.batch))
+    den = np.sqrt(np.bincount(seg, weights=np.abs(Xo) ** 2, minlength=b.batch))
+    err = num / den
+    tol = np.full(b.batch, 1e-11) if fp64 else np.maximum(1e-7 * kappa, 2.4e-7)
+    return float(np.max(err / tol)), float(np.max(err)), float(np.median(err))
+
+
+def kappa_of(b, A_wide):
+    """2-norm condition numbers of the packed Hermitian matrices."""
+    from paper_1111_4144_gb300 import workloads as wl
+    kap = np.zeros(b.batch)
+    for N in np.unique(b.n):
+        idx = np.nonzero(b.n == N)[0]
+        iu = np.triu_indices(N)
+        M = np.zeros((len(idx), N, N), dtype=np.complex128)
+        pos = b.off[idx][:, None] + np.arange(wl.tri(N))[None, :]
+        M[:, iu[0], iu[1]] = A_wide[pos]
+        M = M + np.conj(np.transpose(np.triu(M, 1), (0, 2, 1)))
+        ev = np.linalg.eigvalsh(M)
+        kap[idx] = ev[:, -1] / ev[:, 0]
+    return kap
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    sizes = tuple(int(x) for x in args.sizes.split(","))
+    b = make_workload(0, args.batch, sizes)
+    A_wide = b.A.astype(np.complex64).astype(np.complex128)
+    t_start = time.perf_counter()
+    per = []
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_time(b, A_wide, min_wall=0.0)
+    for _ in range(args.steps):
+        v, threads, reps, _ = oracle_time(b, A_wide, min_wall=0.0)
+        per.append(b.batch / v)
+    ms = 1e3 * float(np.mean(per))
+    value = b.batch / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch": BATCH, "sizes": list(SIZES), "layout": "packed_upper"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle",
+                             "sample": f"full {BATCH}-matrix batch per step, FP64 oracle, {threads} threads"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t_start}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1111_4144_gb300 import _lib, api
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    _lib.load()
+    sizes = tuple(int(x) for x in args.sizes.split(","))
+    b = make_workload(rank, args.batch, sizes)
+    A64 = b.A.astype(np.complex64)
+    A = torch.from_numpy(A64).to(dev)
+    n = torch.from_numpy(b.n).to(dev)
+    off = torch.from_numpy(b.off).to(dev)
+    X = torch.zeros_like(A)
+    stream = torch.cuda.Stream(device=dev)
+    plan = api.Plan(A, X, n, off, max(sizes), layout=api.LAYOUT_PACKED)
+    kernels_per_step = 3 + max(sizes)  # hist, scan, scatter + one class kernel per order 1..max_n
+
+    def timed(fn, steps):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ev0.record(stream)
+        for _ in range(steps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            plan.launch(stream)
+        sampler = ClockSampler(local_rank)
+        if rank == 0:
+            sampler.start()
+        ms = timed(lambda: plan.launch(stream), args.steps)
+        # keep the GPU under the same load long enough for the clock sampler
+        t_end = time.perf_counter() + max(0.0, 1.5 - ms * args.steps / 1e3)
+        while time.perf_counter() < t_end:
+            for _ in range(50):
+                plan.launch(stream)
+            torch.cuda.synchronize()
+        clocks = sampler.stop() if rank == 0 else None
+
+    value = world * b.batch / (ms / 1e3)
+    nbytes = alg_bytes(b.n, 8)
+    peaks, peak_kind = measured_peaks()
+    achieved = nbytes / (ms / 1e3) / 1e9
+
+    # ---- accuracy and the FP64 form (rank 0)
+    out = {}
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": METRIC, "ms_per_step": ms, "quick": True,
+                              "config": {"batch_per_gpu": b.batch, "sizes": list(sizes)},
+                              "achieved_gbs": achieved, "clocks": clocks}), flush=True)
+        plan.close()
+        return
+    if rank == 0:
+        torch.cuda.synchronize()
+        Xg = X.cpu().numpy()
+        A_wide = A64.astype(np.complex128)
+        info = plan.info.cpu().numpy()
+        cpu_v, threads, reps, (_, Xo, info_o) = oracle_time(b, A_wide, min_wall=1.0)
+        kap = kappa_of(b, A_wide)
+        r32 = upper_err_ratio(b, Xg, Xo, kap, fp64=False)
+        out["accuracy"] = {"fp32_max_err_over_tol": r32[0], "fp32_max_rel_err": r32[1],
+                           "fp32_median_rel_err": r32[2], "info_nonzero": int(np.count_nonzero(info)),
+                           "info_matches_oracle": bool(np.array_equal(info, info_o)),
+                           "tolerance": "max(1e-7*kappa, 2.4e-7) relative Frobenius, upper triangle"}
+        out["cpu_baseline"] = {"value": cpu_v, "unit": METRIC, "cores": threads, "kind": "oracle",
+                               "sample": f"{reps} x the full {b.batch}-matrix batch, FP64 C oracle, "
+                                         f"{threads} threads"}
+        # plain FP64 form (complex128) of the same library on the same matrices
+        A128 = torch.from_numpy(A_wide).to(dev)
+        X128 = torch.zeros_like(A128)
+        plan64 = api.Plan(A128, X128, n, off, max(sizes), layout=api.LAYOUT_PACKED)
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                plan64.launch(stream)
+            ms64 = timed(lambda: plan64.launch(stream), max(3, min(args.steps, 20)))
+        r64 = upper_err_ratio(b, X128.cpu().numpy(), Xo, kap, fp64=True)
+        out["fp64_form"] = {"value": b.batch / (ms64 / 1e3), "unit": METRIC, "ms_per_step": ms64,
+                            "max_err_over_tol": r64[0], "max_rel_err": r64[1], "tolerance": "1e-11",
+                            "speedup_fp32_over_fp64": ms64 / ms}
+        plan64.close()
+        del A128, X128
+
+    # ---- end to end through the public API with host buffers
+    A_h = torch.from_numpy(A64).pin_memory()
+    n_h = torch.from_numpy(b.n).pin_memory()
+    off_h = torch.from_numpy(b.off).pin_memory()
+    X_h = torch.empty_like(A_h).pin_memory()
+    info_h = torch.empty(b.batch, dtype=torch.int32).pin_memory()
+
+    def e2e_step():
+        A.copy_(A_h, non_blocking=True)
+        n.copy_(n_h, non_blocking=True)
+        off.copy_(off_h, non_blocking=True)
+        plan.launch(stream)
+        X_h.copy_(X, non_blocking=True)
+        info_h.copy_(plan.info, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        e2e_step()
+        ms_e2e = timed(e2e_step, max(3, min(args.steps, 20)))
+    h2d = A_h.numel() * 8 + n_h.numel() * 4 + off_h.numel() * 8
+    d2h = X_h.numel() * 8 + info_h.numel() * 4
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "c64 (fp32 arithmetic)", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "batch_per_gpu": b.batch, "sizes": list(SIZES), "sigma2": SIGMA2,
+                           "layout": "packed_upper", "launch": "cuda_graph",
+                           "l2": "inputs larger than L2 (509 MB in, 509 MB out per step)"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", FALLBACK_HBM_GBS),
+                             "unit": "GB/s", "frac": achieved / peaks.get("hbm_gbs", FALLBACK_HBM_GBS),
+                             "traffic": None, "peak_source": peak_kind,
+                             "kernel": "whole step (bucketing + class kernels)",
+                             "algorithmic_bytes_per_step": nbytes},
+                "gflops": alg_flops(b.n) / (ms / 1e3) / 1e9,
+                "e2e": {"value": world * b.batch / (ms_e2e / 1e3), "unit": METRIC, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+                "gpu_launches": kernels_per_step * args.steps,
+                "clocks": clocks}
+        line.update(out)
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

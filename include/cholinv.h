@@ -1,0 +1,184 @@
+/*
+ * cholinv — batched Cholesky factorisation and direct inversion of Hermitian
+ * positive-definite matrices on GB300 (sm_103a).
+ *
+ * Method: Krishnamoorthy & Menon, "Matrix Inversion Using Cholesky
+ * Decomposition" (arXiv 1111.4144).
+ *   - Factor (Sec. II, Eqs. 2-4): A = R^* R, R upper triangular with a real,
+ *     positive diagonal, computed row by row:
+ *       r_ii = sqrt(a_ii - sum_{k<i} r_ki^* r_ki)                      (Eq. 3)
+ *       r_ij = (a_ij - sum_{k<i} r_ki^* r_kj) / r_ii,  j > i           (Eq. 4)
+ *   - Inverse (Sec. IV.A, Eqs. 20-24): X = A^{-1} from R X = S, where
+ *     S = diag(1/r_ii) is the known upper part of B = R^{-*}; only x_ij with
+ *     i <= j are solved, rows from the last to the first:
+ *       x_ij = (s_ij - sum_{k>i} r_ik x~_kj) / r_ii,
+ *       x~_kj = x_kj (k <= j), conj(x_jk) (k > j).
+ *     No R^{-1} and no B is formed.
+ *
+ * Conventions shared by every call
+ *   Pointers.  Every array argument is a DEVICE pointer (cudaMalloc'd or
+ *     managed).  The caller owns every buffer; the library keeps no pointer
+ *     after a call returns (except inside a plan, see chol_plan_*).  The
+ *     batched calls allocate nothing.
+ *   Stream.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  Calls only enqueue work and never synchronise, so
+ *     they may be captured into a CUDA graph; errors found on the device are
+ *     reported through `info` and chol_last_device_error().
+ *   Element types.  CHOL_F32 float, CHOL_F64 double, CHOL_C64 complex float
+ *     (interleaved re, im floats), CHOL_C128 complex double.
+ *   Sizes and offsets.  Matrix b has order n[b] and starts at element off[b]
+ *     (int64, in elements of the dtype) of A, R, X, G and dA.  n == NULL means
+ *     every matrix has order max_n; off == NULL means matrix b starts at
+ *     element b * (max_n*max_n) (dense) or b * max_n*(max_n+1)/2 (packed).
+ *     max_n is a host int and must be >= every n[b]; 1 <= max_n <= 64 for the
+ *     batched kernels.  n[b] == 0 is an empty matrix (info 0, nothing
+ *     written).  n[b] < 0 or n[b] > max_n sets info[b] = -1 and the device
+ *     error word (CHOL_ERR_ARG).
+ *   Layout (opts->layout).  0: dense row-major n*n; only the upper triangle
+ *     (i <= j) of A is read (Sec. II: the lower part is never needed).
+ *     1: upper triangle packed row by row (row i holds columns i..n-1),
+ *     n(n+1)/2 elements.  The imaginary part of a diagonal element is ignored.
+ *   Outputs.  R (if not NULL) receives the upper triangle; in the dense
+ *     layout its strictly lower part is written as zero.  X receives the
+ *     upper half of A^{-1}; in the dense layout its strictly lower part is
+ *     left untouched unless opts->fill_lower, which writes x_ji = conj(x_ij)
+ *     (Sec. III.A / IV.A: "x_ji = x_ij^*").
+ *   Aliasing.  R == A, X == A and X == R are allowed (Sec. II notes the
+ *     factor may overwrite A): each matrix is read completely before any of
+ *     its outputs is written.  Distinct matrices must not overlap.
+ *   info.  Device int32[batch] (may be NULL): 0 = success; i > 0 = the
+ *     argument of Eq. 3 at 1-based row i was <= 0 or not finite (A not
+ *     positive definite, or not representable); the outputs of that matrix
+ *     are then filled with NaN.  -1 = invalid n[b].
+ *   Workspace.  Batches with per-matrix sizes (n != NULL) are sorted into
+ *     size classes on the device, which needs chol_workspace_bytes() bytes of
+ *     device memory at `ws` (256-byte aligned).  Uniform batches need none
+ *     (ws may be NULL, ws_bytes 0).  Too small a workspace returns
+ *     CHOL_ERR_WORKSPACE before anything is launched.
+ *   Errors.  Arguments are validated on the host before any launch; a
+ *     negative status means nothing was enqueued.
+ */
+#ifndef CHOLINV_H
+#define CHOLINV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CHOL_F32 = 0,
+    CHOL_F64 = 1,
+    CHOL_C64 = 2,   /* complex float, interleaved */
+    CHOL_C128 = 3   /* complex double, interleaved */
+} chol_dtype_t;
+
+typedef enum {
+    CHOL_OK = 0,
+    CHOL_ERR_ARG = -1,          /* invalid argument (host check) or invalid n[b] (device) */
+    CHOL_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+    CHOL_ERR_UNSUPPORTED = -3,  /* dtype / precision / size combination not implemented */
+    CHOL_ERR_TIMEOUT = -4,      /* a bounded device wait gave up */
+    CHOL_ERR_WORKSPACE = -5     /* workspace missing, too small or misaligned */
+} chol_status_t;
+
+typedef enum {
+    CHOL_PREC_NATIVE = 0,       /* all arithmetic in the dtype's precision */
+    CHOL_PREC_FP32_REFINE = 1,  /* F32/C64: FP32 body, then refine_steps Newton-Schulz steps
+                                   X <- X + X (I - A X) with the residual accumulated in FP64 */
+    CHOL_PREC_TF32_REFINE = 2,  /* blocked large-N path: TF32 tensor-core products */
+    CHOL_PREC_BF16_REFINE = 3   /* blocked large-N path: BF16 tensor-core products */
+} chol_prec_t;
+
+/* opts->flags */
+#define CHOL_FLAG_PIVOT64 0x1   /* F32/C64: accumulate Eq. 3 (the pivot) in FP64 and take its sqrt in FP64 */
+
+typedef struct {
+    int32_t prec;          /* chol_prec_t */
+    int32_t refine_steps;  /* CHOL_PREC_FP32_REFINE: 0, 1 or 2; -1 = automatic (see chol_inv_batched) */
+    int32_t fill_lower;    /* dense layout: also write the strictly lower half of X */
+    int32_t layout;        /* 0 dense row-major, 1 packed upper */
+    int32_t flags;         /* CHOL_FLAG_* */
+} chol_opts_t;
+
+/* Call identifiers for chol_workspace_bytes(). */
+#define CHOL_CALL_FACTOR 0
+#define CHOL_CALL_INV 1
+#define CHOL_CALL_BACKWARD 2
+
+/*
+ * chol_factor_batched — Cholesky factor R of each matrix (Sec. II, Eqs. 3-4).
+ *   A: input, R: output (may equal A).  opts may be NULL (defaults: native
+ *   precision, dense layout).
+ */
+chol_status_t chol_factor_batched(chol_dtype_t dt, int32_t batch, const int32_t* n, const int64_t* off,
+                                  int32_t max_n, const void* A, void* R, int32_t* info,
+                                  const chol_opts_t* opts, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * chol_inv_batched — upper half of X = A^{-1} by the proposed method
+ * (Sec. II Eqs. 3-4 fused with Sec. IV.A Eqs. 20-24): the factor stays on
+ * chip and the recurrence for X runs on it directly.
+ *   A: input; R: optional output of the factor (NULL = not written);
+ *   X: output.  With opts->prec = CHOL_PREC_FP32_REFINE the result is
+ *   refined (refine_steps Newton-Schulz steps, residual I - A X accumulated
+ *   in FP64); refine_steps = -1 applies one step to the matrices whose
+ *   pivots show cancellation (min_i t_i / a_ii < 2^-12, t_i the argument of
+ *   Eq. 3) and none to the rest.  Refinement needs A intact, so X == A is
+ *   rejected (CHOL_ERR_ARG) when any step may run.
+ */
+chol_status_t chol_inv_batched(chol_dtype_t dt, int32_t batch, const int32_t* n, const int64_t* off,
+                               int32_t max_n, const void* A, void* R, void* X, int32_t* info,
+                               const chol_opts_t* opts, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * chol_inv_backward — adjoint of X = A^{-1} on Hermitian matrices:
+ *   dA = -X S X,  S = (G + G^H) / 2
+ * (not in the paper; it reuses the forward X and does no refactorisation).
+ *   X: the forward result in the given layout (upper half is read; the
+ *   lower half is taken as its conjugate mirror).  G: dense n*n gradient of
+ *   the loss with respect to the full X.  dA: dense n*n output (full
+ *   Hermitian).  G and dA always use the dense layout and the element
+ *   offsets off[b] of a dense batch (off == NULL: b * max_n^2); X uses
+ *   opts->layout with its own offsets: pass xoff (NULL = contiguous).
+ */
+chol_status_t chol_inv_backward(chol_dtype_t dt, int32_t batch, const int32_t* n, const int64_t* off,
+                                const int64_t* xoff, int32_t max_n, const void* X, const void* G, void* dA,
+                                const chol_opts_t* opts, void* ws, size_t ws_bytes, void* stream);
+
+/* Bytes of device workspace that a call with these arguments needs (0 = none). */
+size_t chol_workspace_bytes(int32_t call, chol_dtype_t dt, int32_t batch, int32_t max_n, int32_t has_sizes,
+                            const chol_opts_t* opts);
+
+/* A static, human-readable description of a status code. */
+const char* chol_status_string(chol_status_t status);
+
+/* Synchronises `stream`, then reads and clears the device error word of the
+ * current device (CHOL_OK if no kernel reported an error). */
+chol_status_t chol_last_device_error(void* stream);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int32_t chol_version(void);
+
+/*
+ * Plans: a batched call recorded once into a CUDA graph and replayed.
+ *   chol_plan_inv_create records exactly what chol_inv_batched would enqueue
+ *   for these arguments (pointers included) by stream capture on an internal
+ *   stream, and instantiates the graph.  The caller keeps every buffer alive
+ *   until chol_plan_destroy.  chol_plan_launch replays the graph on `stream`.
+ */
+typedef struct chol_plan chol_plan_t;
+
+chol_status_t chol_plan_inv_create(chol_plan_t** plan, chol_dtype_t dt, int32_t batch, const int32_t* n,
+                                   const int64_t* off, int32_t max_n, const void* A, void* R, void* X,
+                                   int32_t* info, const chol_opts_t* opts, void* ws, size_t ws_bytes);
+chol_status_t chol_plan_launch(chol_plan_t* plan, void* stream);
+chol_status_t chol_plan_destroy(chol_plan_t* plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHOLINV_H */

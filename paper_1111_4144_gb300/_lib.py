@@ -1,0 +1,134 @@
+"""ctypes binding of libcholinv.so: the C-ABI entry points under their C names.
+
+Argument marshalling only: every function here forwards its arguments to the
+library unchanged (pointers and streams as Python ints) and returns the
+status code.  The library must exist; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+c_i32 = ctypes.c_int32
+c_i64 = ctypes.c_int64
+c_size = ctypes.c_size_t
+c_vp = ctypes.c_void_p
+
+CHOL_F32, CHOL_F64, CHOL_C64, CHOL_C128 = 0, 1, 2, 3
+CHOL_OK, CHOL_ERR_ARG, CHOL_ERR_CUDA, CHOL_ERR_UNSUPPORTED, CHOL_ERR_TIMEOUT, CHOL_ERR_WORKSPACE = 0, -1, -2, -3, -4, -5
+CHOL_PREC_NATIVE, CHOL_PREC_FP32_REFINE, CHOL_PREC_TF32_REFINE, CHOL_PREC_BF16_REFINE = 0, 1, 2, 3
+CHOL_FLAG_PIVOT64 = 0x1
+CHOL_CALL_FACTOR, CHOL_CALL_INV, CHOL_CALL_BACKWARD = 0, 1, 2
+
+
+class chol_opts_t(ctypes.Structure):
+    _fields_ = [("prec", c_i32), ("refine_steps", c_i32), ("fill_lower", c_i32), ("layout", c_i32),
+                ("flags", c_i32)]
+
+
+# name -> (restype, argtypes); mirrors include/cholinv.h
+SIGNATURES = {
+    "chol_factor_batched": (c_i32, [c_i32, c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp,
+                                    ctypes.POINTER(chol_opts_t), c_vp, c_size, c_vp]),
+    "chol_inv_batched": (c_i32, [c_i32, c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp,
+                                 ctypes.POINTER(chol_opts_t), c_vp, c_size, c_vp]),
+    "chol_inv_backward": (c_i32, [c_i32, c_i32, c_vp, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp,
+                                  ctypes.POINTER(chol_opts_t), c_vp, c_size, c_vp]),
+    "chol_workspace_bytes": (c_size, [c_i32, c_i32, c_i32, c_i32, c_i32, ctypes.POINTER(chol_opts_t)]),
+    "chol_status_string": (ctypes.c_char_p, [c_i32]),
+    "chol_last_device_error": (c_i32, [c_vp]),
+    "chol_version": (c_i32, []),
+    "chol_plan_inv_create": (c_i32, [ctypes.POINTER(c_vp), c_i32, c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp,
+                                     c_vp, ctypes.POINTER(chol_opts_t), c_vp, c_size]),
+    "chol_plan_launch": (c_i32, [c_vp, c_vp]),
+    "chol_plan_destroy": (c_i32, [c_vp]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libcholinv.so (building it first if asked and it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing:
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing; run paper_1111_4144_gb300/build.py")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return load().chol_status_string(status).decode()
+
+
+class CholError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+        self.status = status
+
+
+def check(status: int, what: str) -> None:
+    if status != CHOL_OK:
+        raise CholError(status, what)
+
+
+def opts(prec=CHOL_PREC_NATIVE, refine_steps=0, fill_lower=0, layout=0, flags=0) -> chol_opts_t:
+    return chol_opts_t(int(prec), int(refine_steps), int(fill_lower), int(layout), int(flags))
+
+
+# raw entry points, same names as the C ABI
+def chol_factor_batched(*args):
+    return load().chol_factor_batched(*args)
+
+
+def chol_inv_batched(*args):
+    return load().chol_inv_batched(*args)
+
+
+def chol_inv_backward(*args):
+    return load().chol_inv_backward(*args)
+
+
+def chol_workspace_bytes(*args):
+    return load().chol_workspace_bytes(*args)
+
+
+def chol_status_string(*args):
+    return load().chol_status_string(*args)
+
+
+def chol_last_device_error(*args):
+    return load().chol_last_device_error(*args)
+
+
+def chol_version():
+    return load().chol_version()
+
+
+def chol_plan_inv_create(*args):
+    return load().chol_plan_inv_create(*args)
+
+
+def chol_plan_launch(*args):
+    return load().chol_plan_launch(*args)
+
+
+def chol_plan_destroy(*args):
+    return load().chol_plan_destroy(*args)

@@ -1,0 +1,156 @@
+"""PyTorch-facing wrappers of the C ABI (torch supplies device memory and streams).
+
+Every function checks shapes and dtypes, allocates outputs with torch, and
+calls one C entry point; all arithmetic happens in libcholinv.so.  Tensors
+must be CUDA and contiguous.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib as L
+
+_DT = {torch.float32: L.CHOL_F32, torch.float64: L.CHOL_F64,
+       torch.complex64: L.CHOL_C64, torch.complex128: L.CHOL_C128}
+
+LAYOUT_DENSE = 0
+LAYOUT_PACKED = 1
+
+
+def dtype_code(t: torch.Tensor) -> int:
+    try:
+        return _DT[t.dtype]
+    except KeyError:
+        raise ValueError(f"unsupported dtype {t.dtype}") from None
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError("tensors must be on a CUDA device")
+        if not t.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+
+
+def _p(t):
+    return None if t is None else t.data_ptr()
+
+
+def _s(stream):
+    return (stream if stream is not None else torch.cuda.current_stream()).cuda_stream
+
+
+def _geometry(A, n, off, max_n, layout):
+    """(batch, max_n) from either a dense (batch, N, N) tensor or a flat buffer + sizes."""
+    if n is None and A.dim() == 3:
+        if A.shape[1] != A.shape[2]:
+            raise ValueError("dense batches must have shape (batch, N, N)")
+        if layout != LAYOUT_DENSE:
+            raise ValueError("a (batch, N, N) tensor implies the dense layout")
+        return A.shape[0], A.shape[1]
+    if n is None:
+        if max_n is None:
+            raise ValueError("a flat buffer needs n (per-matrix sizes) or max_n (uniform size)")
+        per = max_n * max_n if layout == LAYOUT_DENSE else max_n * (max_n + 1) // 2
+        if A.numel() % per:
+            raise ValueError("buffer length is not a multiple of the matrix size")
+        return A.numel() // per, max_n
+    if n.dtype != torch.int32 or (off is not None and off.dtype != torch.int64):
+        raise ValueError("n must be int32 and off int64")
+    _need_cuda(n, off)
+    batch = n.numel()
+    if max_n is None:
+        max_n = int(n.max().item()) if batch else 1
+    return batch, max(int(max_n), 1)
+
+
+def workspace(call, dt, batch, max_n, has_sizes, o, device):
+    nbytes = L.chol_workspace_bytes(call, dt, batch, max_n, int(has_sizes), o)
+    if nbytes == 0:
+        return None, 0
+    return torch.empty(nbytes, dtype=torch.uint8, device=device), nbytes
+
+
+def inv(A, n=None, off=None, max_n=None, *, layout=LAYOUT_DENSE, prec=L.CHOL_PREC_NATIVE, refine_steps=0,
+        fill_lower=False, want_R=False, flags=0, X=None, R=None, info=None, stream=None):
+    """Upper half of A^{-1} for every matrix of the batch (Sec. II + Sec. IV.A).
+
+    Returns (X, info) or (X, info, R).  X has A's shape and layout.
+    """
+    _need_cuda(A, X, R, info)
+    dt = dtype_code(A)
+    batch, max_n = _geometry(A, n, off, max_n, layout)
+    o = L.opts(prec, refine_steps, int(fill_lower), layout, flags)
+    if X is None:
+        X = torch.zeros_like(A)
+    if want_R and R is None:
+        R = torch.zeros_like(A)
+    if info is None:
+        info = torch.empty(batch, dtype=torch.int32, device=A.device)
+    ws, nbytes = workspace(L.CHOL_CALL_INV, dt, batch, max_n, n is not None, o, A.device)
+    st = L.chol_inv_batched(dt, batch, _p(n), _p(off), max_n, _p(A), _p(R), _p(X), _p(info), o,
+                            _p(ws), nbytes, _s(stream))
+    L.check(st, "chol_inv_batched")
+    return (X, info, R) if want_R else (X, info)
+
+
+def factor(A, n=None, off=None, max_n=None, *, layout=LAYOUT_DENSE, flags=0, R=None, info=None, stream=None):
+    """Cholesky factor R (Eqs. 3-4).  Returns (R, info)."""
+    _need_cuda(A, R, info)
+    dt = dtype_code(A)
+    batch, max_n = _geometry(A, n, off, max_n, layout)
+    o = L.opts(L.CHOL_PREC_NATIVE, 0, 0, layout, flags)
+    if R is None:
+        R = torch.zeros_like(A)
+    if info is None:
+        info = torch.empty(batch, dtype=torch.int32, device=A.device)
+    ws, nbytes = workspace(L.CHOL_CALL_FACTOR, dt, batch, max_n, n is not None, o, A.device)
+    st = L.chol_factor_batched(dt, batch, _p(n), _p(off), max_n, _p(A), _p(R), _p(info), o, _p(ws), nbytes,
+                               _s(stream))
+    L.check(st, "chol_factor_batched")
+    return R, info
+
+
+def last_device_error(stream=None) -> int:
+    return L.chol_last_device_error(_s(stream))
+
+
+class Plan:
+    """A chol_inv_batched call recorded into a CUDA graph; launch() replays it.
+
+    The tensors passed in stay referenced by the plan (the graph holds their
+    addresses) until close().
+    """
+
+    def __init__(self, A, X, n=None, off=None, max_n=None, *, R=None, info=None, layout=LAYOUT_DENSE,
+                 prec=L.CHOL_PREC_NATIVE, refine_steps=0, fill_lower=False, flags=0):
+        import ctypes
+        _need_cuda(A, X, R, info)
+        dt = dtype_code(A)
+        batch, max_n = _geometry(A, n, off, max_n, layout)
+        o = L.opts(prec, refine_steps, int(fill_lower), layout, flags)
+        self.info = info if info is not None else torch.empty(batch, dtype=torch.int32, device=A.device)
+        self.ws, nbytes = workspace(L.CHOL_CALL_INV, dt, batch, max_n, n is not None, o, A.device)
+        self._keep = (A, X, n, off, R, self.info, self.ws)
+        h = ctypes.c_void_p()
+        st = L.chol_plan_inv_create(ctypes.byref(h), dt, batch, _p(n), _p(off), max_n, _p(A), _p(R), _p(X),
+                                    _p(self.info), o, _p(self.ws), nbytes)
+        L.check(st, "chol_plan_inv_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        L.check(L.chol_plan_launch(self._h, _s(stream)), "chol_plan_launch")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            L.chol_plan_destroy(self._h)
+            self._h = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,289 @@
+// C-ABI of the cholinv library (declared in include/cholinv.h): host-side
+// argument validation, size-class bucketing, kernel dispatch, plans (CUDA
+// graphs) and the device error word.
+#include <cstring>
+#include <mutex>
+
+#include "batched.cuh"
+#include "dispatch.h"
+
+// The per-device error word; kernels receive its address as an argument.
+__device__ int g_chol_error_word;
+
+namespace cholinv {
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+constexpr int kBatchedMaxN = 64;
+
+struct DevState {
+    bool init = false;
+    int sms = 0;
+    int* err = nullptr;
+};
+DevState g_dev[kMaxDevices];
+std::mutex g_dev_mu;
+
+cudaError_t dev_state(DevState** out) {
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return e;
+    if (d < 0 || d >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DevState& s = g_dev[d];
+    if (!s.init) {
+        e = cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, d);
+        if (e != cudaSuccess) return e;
+        e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.err), g_chol_error_word);
+        if (e != cudaSuccess) return e;
+        s.init = true;
+    }
+    *out = &s;
+    return cudaSuccess;
+}
+
+constexpr size_t kWsHeader = 1024;  // counts | starts | cursor (kClasses int32 each), padded
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t ws_need_batched(int32_t batch, int32_t has_sizes) {
+    if (!has_sizes || batch <= 0) return 0;
+    return kWsHeader + align_up((size_t)batch * sizeof(int32_t), 256);
+}
+
+chol_opts_t opts_or_default(const chol_opts_t* o) {
+    chol_opts_t d;
+    d.prec = CHOL_PREC_NATIVE;
+    d.refine_steps = 0;
+    d.fill_lower = 0;
+    d.layout = 0;
+    d.flags = 0;
+    return o ? *o : d;
+}
+
+bool is_fp32(chol_dtype_t dt) { return dt == CHOL_F32 || dt == CHOL_C64; }
+
+chol_status_t check_common(chol_dtype_t dt, int32_t batch, int32_t max_n, const chol_opts_t& o) {
+    if (dt < CHOL_F32 || dt > CHOL_C128) return CHOL_ERR_ARG;
+    if (batch < 0) return CHOL_ERR_ARG;
+    if (max_n < 1) return CHOL_ERR_ARG;
+    if (o.layout != 0 && o.layout != 1) return CHOL_ERR_ARG;
+    if (o.prec < CHOL_PREC_NATIVE || o.prec > CHOL_PREC_BF16_REFINE) return CHOL_ERR_ARG;
+    if (o.refine_steps < -1 || o.refine_steps > 2) return CHOL_ERR_ARG;
+    if (o.flags & ~CHOL_FLAG_PIVOT64) return CHOL_ERR_ARG;
+    if (max_n > kBatchedMaxN) return CHOL_ERR_UNSUPPORTED;
+    if (o.prec == CHOL_PREC_TF32_REFINE || o.prec == CHOL_PREC_BF16_REFINE) return CHOL_ERR_UNSUPPORTED;
+    if (o.prec == CHOL_PREC_FP32_REFINE && !is_fp32(dt)) return CHOL_ERR_UNSUPPORTED;
+    return CHOL_OK;
+}
+
+chol_status_t check_ws(int32_t batch, const int32_t* n, void* ws, size_t ws_bytes) {
+    const size_t need = ws_need_batched(batch, n != nullptr);
+    if (need == 0) return CHOL_OK;
+    if (ws == nullptr || ws_bytes < need) return CHOL_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return CHOL_ERR_WORKSPACE;
+    return CHOL_OK;
+}
+
+cudaError_t launch_dtype(chol_dtype_t dt, const BatchParams& p, cudaStream_t s, bool dry) {
+    switch (dt) {
+        case CHOL_F32: return launch_batched_f32(p, s, dry);
+        case CHOL_F64: return launch_batched_f64(p, s, dry);
+        case CHOL_C64: return launch_batched_c64(p, s, dry);
+        case CHOL_C128: return launch_batched_c128(p, s, dry);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Enqueue bucketing (if per-matrix sizes) and every class kernel.
+chol_status_t enqueue_batched(chol_dtype_t dt, BatchParams p, void* ws, cudaStream_t s, bool dry) {
+    DevState* ds = nullptr;
+    if (dev_state(&ds) != cudaSuccess) return CHOL_ERR_CUDA;
+    p.err = ds->err;
+    if (p.n != nullptr) {
+        char* w = static_cast<char*>(ws);
+        int32_t* counts = reinterpret_cast<int32_t*>(w);
+        int32_t* starts = counts + kClasses;
+        int32_t* cursor = starts + kClasses;
+        int32_t* perm = reinterpret_cast<int32_t*>(w + kWsHeader);
+        p.cls_count = counts;
+        p.cls_start = starts;
+        p.perm = perm;
+        if (!dry) {
+            if (cudaMemsetAsync(counts, 0, kClasses * sizeof(int32_t), s) != cudaSuccess) return CHOL_ERR_CUDA;
+            const int threads = 256;
+            const int grid = (int)std::min<int64_t>(((int64_t)p.batch + threads - 1) / threads, (int64_t)ds->sms * 8);
+            k_bucket_hist<<<grid, threads, 0, s>>>(p.batch, p.n, p.max_n, counts, p.info, p.err);
+            k_bucket_scan<<<1, 32, 0, s>>>(counts, starts, cursor);
+            k_bucket_scatter<<<grid, threads, 0, s>>>(p.batch, p.n, p.max_n, cursor, perm);
+            if (cudaGetLastError() != cudaSuccess) return CHOL_ERR_CUDA;
+        }
+    }
+    if (launch_dtype(dt, p, s, dry) != cudaSuccess) return CHOL_ERR_CUDA;
+    return CHOL_OK;
+}
+
+chol_status_t inv_validate(chol_dtype_t dt, int32_t batch, const int32_t* n, int32_t max_n, const void* A,
+                           void* X, const chol_opts_t& o, void* ws, size_t ws_bytes) {
+    chol_status_t st = check_common(dt, batch, max_n, o);
+    if (st != CHOL_OK) return st;
+    if (batch == 0) return CHOL_OK;
+    if (A == nullptr || X == nullptr) return CHOL_ERR_ARG;
+    if (o.prec == CHOL_PREC_FP32_REFINE && o.refine_steps != 0) return CHOL_ERR_UNSUPPORTED;
+    return check_ws(batch, n, ws, ws_bytes);
+}
+
+BatchParams make_params(int32_t batch, const int32_t* n, const int64_t* off, int32_t max_n, const void* A,
+                        void* R, void* X, int32_t* info, const chol_opts_t& o, int want_inv) {
+    BatchParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.batch = batch;
+    p.n = n;
+    p.off = off;
+    p.max_n = max_n;
+    p.layout = o.layout;
+    p.fill_lower = o.layout == 0 ? o.fill_lower : 0;
+    p.want_inv = want_inv;
+    p.A = A;
+    p.R = R;
+    p.X = X;
+    p.info = info;
+    return p;
+}
+
+}  // namespace
+
+DeviceInfo device_info() {
+    DeviceInfo d;
+    DevState* ds = nullptr;
+    if (dev_state(&ds) == cudaSuccess) d.sms = ds->sms;
+    if (d.sms <= 0) d.sms = 1;
+    return d;
+}
+
+}  // namespace cholinv
+
+using namespace cholinv;
+
+struct chol_plan {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+chol_status_t chol_factor_batched(chol_dtype_t dt, int32_t batch, const int32_t* n, const int64_t* off,
+                                  int32_t max_n, const void* A, void* R, int32_t* info,
+                                  const chol_opts_t* opts, void* ws, size_t ws_bytes, void* stream) {
+    const chol_opts_t o = opts_or_default(opts);
+    chol_status_t st = check_common(dt, batch, max_n, o);
+    if (st != CHOL_OK) return st;
+    if (batch == 0) return CHOL_OK;
+    if (A == nullptr || R == nullptr) return CHOL_ERR_ARG;
+    st = check_ws(batch, n, ws, ws_bytes);
+    if (st != CHOL_OK) return st;
+    BatchParams p = make_params(batch, n, off, max_n, A, R, nullptr, info, o, 0);
+    return enqueue_batched(dt, p, ws, static_cast<cudaStream_t>(stream), false);
+}
+
+chol_status_t chol_inv_batched(chol_dtype_t dt, int32_t batch, const int32_t* n, const int64_t* off,
+                               int32_t max_n, const void* A, void* R, void* X, int32_t* info,
+                               const chol_opts_t* opts, void* ws, size_t ws_bytes, void* stream) {
+    const chol_opts_t o = opts_or_default(opts);
+    chol_status_t st = inv_validate(dt, batch, n, max_n, A, X, o, ws, ws_bytes);
+    if (st != CHOL_OK || batch == 0) return st;
+    BatchParams p = make_params(batch, n, off, max_n, A, (R == X) ? nullptr : R, X, info, o, 1);
+    return enqueue_batched(dt, p, ws, static_cast<cudaStream_t>(stream), false);
+}
+
+chol_status_t chol_inv_backward(chol_dtype_t dt, int32_t batch, const int32_t* n, const int64_t* off,
+                                const int64_t* xoff, int32_t max_n, const void* X, const void* G, void* dA,
+                                const chol_opts_t* opts, void* ws, size_t ws_bytes, void* stream) {
+    (void)dt; (void)batch; (void)n; (void)off; (void)xoff; (void)max_n; (void)X; (void)G; (void)dA;
+    (void)opts; (void)ws; (void)ws_bytes; (void)stream;
+    return CHOL_ERR_UNSUPPORTED;
+}
+
+size_t chol_workspace_bytes(int32_t call, chol_dtype_t dt, int32_t batch, int32_t max_n, int32_t has_sizes,
+                            const chol_opts_t* opts) {
+    (void)dt; (void)max_n; (void)opts;
+    if (call == CHOL_CALL_FACTOR || call == CHOL_CALL_INV) return ws_need_batched(batch, has_sizes);
+    return 0;
+}
+
+const char* chol_status_string(chol_status_t status) {
+    switch (status) {
+        case CHOL_OK: return "success";
+        case CHOL_ERR_ARG: return "invalid argument";
+        case CHOL_ERR_CUDA: return "a CUDA runtime call failed";
+        case CHOL_ERR_UNSUPPORTED: return "dtype, precision or size not supported";
+        case CHOL_ERR_TIMEOUT: return "a bounded device wait gave up";
+        case CHOL_ERR_WORKSPACE: return "workspace missing, too small or not 256-byte aligned";
+    }
+    return "unknown status";
+}
+
+chol_status_t chol_last_device_error(void* stream) {
+    DevState* ds = nullptr;
+    if (dev_state(&ds) != cudaSuccess) return CHOL_ERR_CUDA;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return CHOL_ERR_CUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, ds->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CHOL_ERR_CUDA;
+    if (v != 0) {
+        const int z = 0;
+        if (cudaMemcpy(ds->err, &z, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return CHOL_ERR_CUDA;
+    }
+    return static_cast<chol_status_t>(v);
+}
+
+int32_t chol_version(void) { return 100; }
+
+chol_status_t chol_plan_inv_create(chol_plan_t** plan, chol_dtype_t dt, int32_t batch, const int32_t* n,
+                                   const int64_t* off, int32_t max_n, const void* A, void* R, void* X,
+                                   int32_t* info, const chol_opts_t* opts, void* ws, size_t ws_bytes) {
+    if (plan == nullptr) return CHOL_ERR_ARG;
+    *plan = nullptr;
+    const chol_opts_t o = opts_or_default(opts);
+    chol_status_t st = inv_validate(dt, batch, n, max_n, A, X, o, ws, ws_bytes);
+    if (st != CHOL_OK) return st;
+    BatchParams p = make_params(batch, n, off, max_n, A, (R == X) ? nullptr : R, X, info, o, 1);
+    // one-time kernel set-up outside the capture
+    st = enqueue_batched(dt, p, ws, nullptr, true);
+    if (st != CHOL_OK) return st;
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return CHOL_ERR_CUDA;
+    chol_plan* pl = new chol_plan();
+    st = CHOL_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = CHOL_ERR_CUDA;
+    if (st == CHOL_OK && batch > 0) st = enqueue_batched(dt, p, ws, cs, false);
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(cs, &g) != cudaSuccess && st == CHOL_OK) st = CHOL_ERR_CUDA;
+    pl->graph = g;
+    if (st == CHOL_OK && cudaGraphInstantiate(&pl->exec, g, 0) != cudaSuccess) st = CHOL_ERR_CUDA;
+    cudaStreamDestroy(cs);
+    if (st != CHOL_OK) {
+        if (pl->exec) cudaGraphExecDestroy(pl->exec);
+        if (pl->graph) cudaGraphDestroy(pl->graph);
+        delete pl;
+        return st;
+    }
+    *plan = pl;
+    return CHOL_OK;
+}
+
+chol_status_t chol_plan_launch(chol_plan_t* plan, void* stream) {
+    if (plan == nullptr || plan->exec == nullptr) return CHOL_ERR_ARG;
+    if (cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) return CHOL_ERR_CUDA;
+    return CHOL_OK;
+}
+
+chol_status_t chol_plan_destroy(chol_plan_t* plan) {
+    if (plan == nullptr) return CHOL_ERR_ARG;
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    delete plan;
+    return CHOL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,64 @@
+// Size-class bucketing of a batch with per-matrix orders: a histogram of
+// n[b], an exclusive scan over the classes and a scatter of the matrix
+// indices into class order.  Every kernel is a plain grid-stride loop; no
+// CTA waits on another, so nothing here can stall.
+#include "batched.cuh"
+
+namespace cholinv {
+
+__global__ void k_bucket_hist(int32_t batch, const int32_t* __restrict__ n, int32_t max_n, int32_t* counts,
+                              int32_t* info, int* err) {
+    __shared__ int sh[kClasses];
+    for (int c = threadIdx.x; c < kClasses; c += blockDim.x) sh[c] = 0;
+    __syncthreads();
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < batch; b += (int64_t)gridDim.x * blockDim.x) {
+        const int nb = n[b];
+        if (nb < 0 || nb > max_n) {
+            if (info) info[b] = -1;
+            report_error(err, CHOL_ERR_ARG);
+        } else if (nb == 0) {
+            if (info) info[b] = 0;
+        } else {
+            atomicAdd(&sh[nb], 1);
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < kClasses; c += blockDim.x)
+        if (sh[c]) atomicAdd(&counts[c], sh[c]);
+}
+
+__global__ void k_bucket_scan(int32_t* counts, int32_t* starts, int32_t* cursor) {
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int c = 0; c < kClasses; ++c) {
+            starts[c] = s;
+            cursor[c] = s;
+            s += counts[c];
+        }
+    }
+}
+
+__global__ void k_bucket_scatter(int32_t batch, const int32_t* __restrict__ n, int32_t max_n, int32_t* cursor,
+                                 int32_t* perm) {
+    __shared__ int cnt[kClasses];
+    __shared__ int basec[kClasses];
+    for (int64_t tile = blockIdx.x; tile * blockDim.x < batch; tile += gridDim.x) {
+        for (int c = threadIdx.x; c < kClasses; c += blockDim.x) cnt[c] = 0;
+        __syncthreads();
+        const int64_t b = tile * blockDim.x + threadIdx.x;
+        int nb = 0, rank = 0;
+        if (b < batch) {
+            nb = n[b];
+            if (nb > 0 && nb <= max_n) rank = atomicAdd(&cnt[nb], 1);
+            else nb = 0;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < kClasses; c += blockDim.x)
+            if (cnt[c]) basec[c] = atomicAdd(&cursor[c], cnt[c]);
+        __syncthreads();
+        if (nb > 0) perm[basec[nb] + rank] = (int32_t)b;
+        __syncthreads();
+    }
+}
+
+}  // namespace cholinv

@@ -1,0 +1,129 @@
+// Shared device-side types and helpers of the cholinv CUDA library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cholinv.h"
+
+#define CHOL_HD __host__ __device__ __forceinline__
+#define CHOL_CX __host__ __device__ __forceinline__ constexpr
+#define CHOL_D __device__ __forceinline__
+
+namespace cholinv {
+
+// ---------------------------------------------------------------------------
+// Value types: real float/double and an interleaved complex pair.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct __align__(2 * sizeof(T)) cpx {
+    T re, im;
+};
+
+template <typename V> struct traits;
+template <> struct traits<float>        { using real = float;  static constexpr bool cplx = false; static constexpr int words = 1; };
+template <> struct traits<double>       { using real = double; static constexpr bool cplx = false; static constexpr int words = 2; };
+template <> struct traits<cpx<float>>   { using real = float;  static constexpr bool cplx = true;  static constexpr int words = 2; };
+template <> struct traits<cpx<double>>  { using real = double; static constexpr bool cplx = true;  static constexpr int words = 4; };
+
+template <typename T> CHOL_HD T zero_v() { return T(0); }
+template <> CHOL_HD cpx<float> zero_v<cpx<float>>() { return {0.f, 0.f}; }
+template <> CHOL_HD cpx<double> zero_v<cpx<double>>() { return {0.0, 0.0}; }
+
+// real part, conjugate, |v|^2
+CHOL_HD float re_of(float v) { return v; }
+CHOL_HD double re_of(double v) { return v; }
+template <typename T> CHOL_HD T re_of(cpx<T> v) { return v.re; }
+
+CHOL_HD float conj_v(float v) { return v; }
+CHOL_HD double conj_v(double v) { return v; }
+template <typename T> CHOL_HD cpx<T> conj_v(cpx<T> v) { return {v.re, -v.im}; }
+
+template <typename T> CHOL_HD cpx<T> operator+(cpx<T> a, cpx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T> CHOL_HD cpx<T> operator-(cpx<T> a, cpx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T> CHOL_HD cpx<T> operator*(cpx<T> a, T s) { return {a.re * s, a.im * s}; }
+template <typename T> CHOL_HD cpx<T> operator-(cpx<T> a) { return {-a.re, -a.im}; }
+
+// acc + a*b with fused multiply-adds (real: 1 FMA; complex: 4 FMAs)
+CHOL_D float fma_v(float a, float b, float acc) { return fmaf(a, b, acc); }
+CHOL_D double fma_v(double a, double b, double acc) { return fma(a, b, acc); }
+template <typename T> CHOL_D cpx<T> fma_v(cpx<T> a, cpx<T> b, cpx<T> acc) {
+    cpx<T> r;
+    r.re = fma(a.re, b.re, acc.re);
+    r.re = fma(-a.im, b.im, r.re);
+    r.im = fma(a.re, b.im, acc.im);
+    r.im = fma(a.im, b.re, r.im);
+    return r;
+}
+// acc - conj(a)*b
+CHOL_D float fnma_conj(float a, float b, float acc) { return fmaf(-a, b, acc); }
+CHOL_D double fnma_conj(double a, double b, double acc) { return fma(-a, b, acc); }
+template <typename T> CHOL_D cpx<T> fnma_conj(cpx<T> a, cpx<T> b, cpx<T> acc) {
+    // conj(a)*b = (ar*br + ai*bi) + i(ar*bi - ai*br)
+    cpx<T> r;
+    r.re = fma(-a.re, b.re, acc.re);
+    r.re = fma(-a.im, b.im, r.re);
+    r.im = fma(-a.re, b.im, acc.im);
+    r.im = fma(a.im, b.re, r.im);
+    return r;
+}
+// acc + a*conj(b)
+CHOL_D float fma_conjb(float a, float b, float acc) { return fmaf(a, b, acc); }
+CHOL_D double fma_conjb(double a, double b, double acc) { return fma(a, b, acc); }
+template <typename T> CHOL_D cpx<T> fma_conjb(cpx<T> a, cpx<T> b, cpx<T> acc) {
+    // a*conj(b) = (ar*br + ai*bi) + i(ai*br - ar*bi)
+    cpx<T> r;
+    r.re = fma(a.re, b.re, acc.re);
+    r.re = fma(a.im, b.im, r.re);
+    r.im = fma(a.im, b.re, acc.im);
+    r.im = fma(-a.re, b.im, r.im);
+    return r;
+}
+// Re(a * conj(b)) accumulated into a real accumulator
+CHOL_D float fma_re_conjb(float a, float b, float acc) { return fmaf(a, b, acc); }
+CHOL_D double fma_re_conjb(double a, double b, double acc) { return fma(a, b, acc); }
+template <typename T> CHOL_D T fma_re_conjb(cpx<T> a, cpx<T> b, T acc) {
+    return fma(a.im, b.im, fma(a.re, b.re, acc));
+}
+// acc - |a|^2 (real accumulator)
+CHOL_D float fnma_abs2(float a, float acc) { return fmaf(-a, a, acc); }
+CHOL_D double fnma_abs2(double a, double acc) { return fma(-a, a, acc); }
+template <typename T> CHOL_D T fnma_abs2(cpx<T> a, T acc) { return fma(-a.im, a.im, fma(-a.re, a.re, acc)); }
+
+CHOL_D float scale_v(float v, float s) { return v * s; }
+CHOL_D double scale_v(double v, double s) { return v * s; }
+template <typename T> CHOL_D cpx<T> scale_v(cpx<T> v, T s) { return {v.re * s, v.im * s}; }
+
+template <typename V> CHOL_D V from_real(typename traits<V>::real r);
+template <> CHOL_D float from_real<float>(float r) { return r; }
+template <> CHOL_D double from_real<double>(double r) { return r; }
+template <> CHOL_D cpx<float> from_real<cpx<float>>(float r) { return {r, 0.f}; }
+template <> CHOL_D cpx<double> from_real<cpx<double>>(double r) { return {r, 0.0}; }
+
+template <typename V> CHOL_D V nan_v() {
+    using R = typename traits<V>::real;
+    R q = R(__int_as_float(0x7fffffff));
+    if constexpr (traits<V>::cplx) return V{q, q}; else return V(q);
+}
+
+template <typename R> CHOL_D bool pivot_ok(R t) { return (t > R(0)) && isfinite(t); }
+
+// ---------------------------------------------------------------------------
+// Index helpers.  Packed upper, row by row: row i holds columns i..n-1.
+// ---------------------------------------------------------------------------
+CHOL_CX int pidx(int n, int i, int j) { return i * n - (i * (i - 1)) / 2 + (j - i); }
+CHOL_CX int tri(int n) { return n * (n + 1) / 2; }
+CHOL_CX int64_t tri64(int64_t n) { return n * (n + 1) / 2; }
+
+// element offset of (i,j), i <= j, within one matrix of order n
+CHOL_HD int64_t elem_off(int layout, int n, int i, int j) {
+    return layout ? (int64_t)pidx(n, i, j) : (int64_t)i * n + j;
+}
+
+// Kernels that detect an invalid input record the first error code in a
+// per-device error word whose address they receive as an argument.
+CHOL_D void report_error(int* err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+}  // namespace cholinv

@@ -1,0 +1,97 @@
+// Host-side launchers of the batched kernels for one value type.  Each
+// dtype's translation unit includes this file and instantiates
+// launch_batched<V> (four TUs compile in parallel).
+#pragma once
+
+#include <algorithm>
+#include <mutex>
+
+#include "batched.cuh"
+#include "dispatch.h"
+
+namespace cholinv {
+
+// Largest order handled by the one-matrix-per-thread kernels, per element
+// type; larger orders go to the one-matrix-per-warp kernel.  (Beyond these
+// orders the per-thread working set no longer fits the register file.)
+constexpr int kLaneMaxNAll = 16;
+template <typename V>
+constexpr int lane_max_n() {
+    return sizeof(V) == 16 ? 10 : (sizeof(V) == 8 && !traits<V>::cplx) ? 14 : 16;
+}
+
+template <typename V, int N>
+static cudaError_t launch_lane(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
+    constexpr int THREADS = lane_threads<V, N>();
+    constexpr size_t SMEM = lane_smem_bytes<V, N>();
+    static std::once_flag once;
+    static int per_sm = 1;
+    static cudaError_t setup_err = cudaSuccess;
+    std::call_once(once, [&] {
+        setup_err = cudaFuncSetAttribute(k_lane<V, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+        if (setup_err == cudaSuccess)
+            setup_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lane<V, N>, THREADS, SMEM);
+        if (per_sm < 1) per_sm = 1;
+    });
+    if (setup_err != cudaSuccess || dry) return setup_err;
+    const int chunks = (upper_count + THREADS - 1) / THREADS;
+    if (chunks <= 0) return cudaSuccess;
+    const int grid = std::min(chunks, device_info().sms * per_sm);
+    k_lane<V, N><<<grid, THREADS, SMEM, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename V>
+static cudaError_t launch_warp(const BatchParams& p, int N, int upper_count, cudaStream_t s, bool dry) {
+    const size_t per_warp = (size_t)N * (N + 1) * sizeof(V);
+    int warps = (int)std::max<size_t>(1, std::min<size_t>(4, 98304 / per_warp));
+    const size_t smem = per_warp * warps;
+    static std::once_flag once;
+    static cudaError_t setup_err = cudaSuccess;
+    std::call_once(once, [&] {
+        setup_err = cudaFuncSetAttribute(k_warp<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
+    if (setup_err != cudaSuccess || dry) return setup_err;
+    int per_sm = 1;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_warp<V>, 32 * warps, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int ctas = (upper_count + warps - 1) / warps;
+    if (ctas <= 0) return cudaSuccess;
+    const int grid = std::min(ctas, device_info().sms * per_sm);
+    k_warp<V><<<grid, 32 * warps, smem, s>>>(p, N, warps);
+    return cudaGetLastError();
+}
+
+template <typename V, int N>
+static cudaError_t launch_lane_upto(const BatchParams& p, int cls, int upper_count, cudaStream_t s, bool dry) {
+    if constexpr (N == 0) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (cls == N) return launch_lane<V, N>(p, upper_count, s, dry);
+        return launch_lane_upto<V, N - 1>(p, cls, upper_count, s, dry);
+    }
+}
+
+// Launch the kernel of one size class (cls) whose member count is at most upper_count.
+template <typename V>
+cudaError_t launch_class(const BatchParams& p, int cls, int upper_count, cudaStream_t s, bool dry) {
+    if (cls <= lane_max_n<V>()) return launch_lane_upto<V, lane_max_n<V>()>(p, cls, upper_count, s, dry);
+    return launch_warp<V>(p, cls, upper_count, s, dry);
+}
+
+// Every size class of a batch: one class for uniform batches, otherwise
+// every class 1..max_n (a class kernel with no members exits at once).
+// dry = true only performs the one-time per-kernel set-up (used before a
+// stream capture) and launches nothing.
+template <typename V>
+cudaError_t launch_batched(const BatchParams& p, cudaStream_t s, bool dry) {
+    if (p.cls_count == nullptr) return launch_class<V>(p, p.max_n, p.batch, s, dry);
+    for (int c = p.max_n; c >= 1; --c) {
+        cudaError_t e = launch_class<V>(p, c, p.batch, s, dry);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace cholinv

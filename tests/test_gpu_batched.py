@@ -1,0 +1,185 @@
+"""GPU parity: the batched CUDA path (through the C ABI) against the CPU oracle.
+
+Inputs come from the seeded generators; both sides see the same matrices
+rounded to the working precision.  Per-matrix relative Frobenius error over
+the upper triangle must stay within: 1e-11 (FP64 / complex128) and
+max(1e-7 * kappa, 2.4e-7) (FP32 / complex64, kappa the 2-norm condition
+number of the rounded matrix).
+"""
+import numpy as np
+import pytest
+
+from paper_1111_4144_gb300 import workloads as wl
+
+from gpu_helpers import TOL64, cast_batch, kappas, oracle_inv, run_inv, tol32, upper_errors
+
+pytestmark = pytest.mark.gpu
+
+TAGS = ["f32", "f64", "c64", "c128"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1111_4144_gb300 import _lib
+    _lib.load()
+
+
+def make_batch(tag, N, batch, layout, seed):
+    if tag in ("c64", "c128"):
+        return wl.mimo_covariance(batch, sizes=(N,), seed=seed, layout=layout, shuffle=False)
+    return wl.qr_spectrum(batch, lambda rng, b: np.full(b, N),
+                          lambda rng, m, NN: 10.0 ** rng.uniform(0.0, 3.0, size=(m, NN)), seed, layout)
+
+
+def check_errors(tag, b, A_wide, err, what):
+    if tag in ("f64", "c128"):
+        tol = np.full(b.batch, TOL64)
+    else:
+        tol = tol32(kappas(b, A_wide))
+    bad = np.nonzero(~(err <= tol))[0]
+    assert bad.size == 0, f"{what}: {bad.size} of {b.batch} matrices over tolerance; worst ratio " \
+                          f"{np.max(err / tol):.3g} at matrix {bad[0]} (N={b.n[bad[0]]})"
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 8, 11, 15, 16, 17, 24, 32, 33, 48, 63, 64])
+@pytest.mark.parametrize("tag", TAGS)
+def test_uniform_parity(orc, tag, N, layout):
+    batch = 300 if N <= 32 else 90
+    b = make_batch(tag, N, batch, layout, seed=1000 + N)
+    X, info, R = run_inv(b, tag, mixed=False, want_R=True)
+    Ro, Xo, info_o, A_wide = oracle_inv(orc, b, tag)
+    assert np.all(info_o == 0) and np.array_equal(info, info_o)
+    check_errors(tag, b, A_wide, upper_errors(b, X, Xo), "X")
+    check_errors(tag, b, A_wide, upper_errors(b, R, Ro), "R")
+    if layout == 0:
+        # dense R: strictly lower part written as zero
+        for k in range(0, batch, 37):
+            M = R[b.off[k]:b.off[k] + N * N].reshape(N, N)
+            assert np.all(np.tril(M, -1) == 0)
+
+
+@pytest.mark.parametrize("tag,kind", [("c64", "mimo"), ("c128", "mimo"), ("f32", "uneven"), ("f64", "uneven"),
+                                      ("c64", "uneven_c")])
+def test_mixed_sizes_parity(orc, tag, kind):
+    if kind == "mimo":
+        b = wl.mimo_covariance(3001, sizes=(4, 8, 16), seed=1001, layout=1)
+    elif kind == "uneven":
+        b = wl.uneven_loguniform(700, nmin=2, nmax=64, seed=1002, layout=0)
+    else:
+        b = wl.mimo_covariance(900, sizes=tuple(range(1, 41)), seed=77, layout=0)
+    X, info, _ = run_inv(b, tag, mixed=True)
+    Ro, Xo, info_o, A_wide = oracle_inv(orc, b, tag)
+    assert np.all(info_o == 0) and np.array_equal(info, info_o)
+    check_errors(tag, b, A_wide, upper_errors(b, X, Xo), "X")
+
+
+@pytest.mark.parametrize("tag", ["f32", "c128"])
+def test_fill_lower(orc, tag):
+    b = make_batch(tag if tag != "f32" else "f32", 12, 50, 0, seed=5)
+    X, _, _ = run_inv(b, tag, mixed=False, fill_lower=True)
+    for k in range(b.batch):
+        M = X[b.off[k]:b.off[k] + 144].reshape(12, 12)
+        assert np.array_equal(np.tril(M, -1), np.conj(np.triu(M, 1)).T)
+
+
+@pytest.mark.parametrize("tag", TAGS)
+def test_non_pd_info_and_nan_fill(orc, tag):
+    N = 6
+    b = make_batch(tag, N, 40, 0, seed=9)
+    A = b.A.copy()
+    bad = {3: 1, 17: 4, 39: 6}
+    for k, row in bad.items():
+        o = b.off[k]
+        M = A[o:o + N * N].reshape(N, N)
+        M[row - 1, row - 1] = -abs(M[row - 1, row - 1]) * 50.0  # destroys positive definiteness at that row
+    b2 = wl.Batch(A, b.n, b.off, 0)
+    X, info, _ = run_inv(b2, tag, mixed=False)
+    _, _, info_o, _ = oracle_inv(orc, b2, tag)
+    assert np.array_equal(info, info_o)
+    for k, row in bad.items():
+        assert info[k] == row
+        M = X[b.off[k]:b.off[k] + N * N].reshape(N, N)
+        assert np.all(np.isnan(M[np.triu_indices(N)].real))
+    good = [k for k in range(b.batch) if k not in bad]
+    assert np.all(info[good] == 0)
+
+
+def test_zero_and_invalid_sizes(orc):
+    import torch
+    from paper_1111_4144_gb300 import _lib as L, api
+    b = wl.mimo_covariance(64, sizes=(5, 7), seed=3, layout=1)
+    n = b.n.copy()
+    n[10] = 0
+    A_np = b.A.astype(np.complex64)
+    dev = torch.device("cuda", 0)
+    A = torch.from_numpy(A_np).to(dev)
+    X0 = torch.full_like(A, 7.0)
+    api.inv(A, torch.from_numpy(n).to(dev), torch.from_numpy(b.off).to(dev), 8, layout=1, X=X0)
+    torch.cuda.synchronize()
+    assert api.last_device_error() == L.CHOL_OK
+    n2 = n.copy()
+    n2[20] = 9  # larger than max_n = 8
+    X1 = torch.full_like(A, 7.0)
+    _, info = api.inv(A, torch.from_numpy(n2).to(dev), torch.from_numpy(b.off).to(dev), 8, layout=1, X=X1)
+    info = info.cpu().numpy()
+    assert info[20] == -1 and info[10] == 0
+    assert api.last_device_error() == L.CHOL_ERR_ARG
+    assert api.last_device_error() == L.CHOL_OK  # the error word was cleared by the read
+    X1 = X1.cpu().numpy()
+    o = b.off[10]
+    assert np.all(X1[o:o + 15] == 7.0)  # the empty matrix's slots were not written
+
+
+@pytest.mark.parametrize("tag,kind", [("c64", "mimo"), ("f32", "uneven")])
+def test_plan_replay_matches_eager(orc, tag, kind):
+    if kind == "mimo":
+        b = wl.mimo_covariance(5000, sizes=(4, 8, 16), seed=11, layout=1)
+    else:
+        b = wl.uneven_loguniform(400, seed=12, layout=0)
+    Xe, ie, _ = run_inv(b, tag, mixed=True)
+    Xp, ip, _ = run_inv(b, tag, mixed=True, plan=True)
+    assert np.array_equal(ie, ip)
+    assert np.array_equal(Xe.view(np.uint8), Xp.view(np.uint8))
+
+
+@pytest.mark.parametrize("tag", ["f64", "c64"])
+@pytest.mark.parametrize("N", [6, 20])
+def test_in_place_x_equals_a(orc, tag, N):
+    import torch
+    from paper_1111_4144_gb300 import api
+    b = make_batch(tag, N, 64, 1, seed=21)
+    A_np, _ = cast_batch(b, tag)
+    A = torch.from_numpy(A_np).cuda()
+    api.inv(A, max_n=N, layout=1, X=A)
+    torch.cuda.synchronize()
+    _, Xo, _, A_wide = oracle_inv(orc, b, tag)
+    check_errors(tag, b, A_wide, upper_errors(b, A.cpu().numpy(), Xo), "X (in place)")
+
+
+@pytest.mark.parametrize("tag", TAGS)
+@pytest.mark.parametrize("N", [7, 40])
+def test_factor_only(orc, tag, N):
+    import torch
+    from paper_1111_4144_gb300 import api
+    b = make_batch(tag, N, 70, 0, seed=31)
+    A_np, _ = cast_batch(b, tag)
+    A = torch.from_numpy(A_np).cuda()
+    R, info = api.factor(A, max_n=N, layout=0)
+    torch.cuda.synchronize()
+    Ro, _, info_o, A_wide = oracle_inv(orc, b, tag)
+    assert np.array_equal(info.cpu().numpy(), info_o)
+    R = R.cpu().numpy()
+    check_errors(tag, b, A_wide, upper_errors(b, R, Ro), "R")
+    for k in range(0, b.batch, 9):
+        M = R[b.off[k]:b.off[k] + N * N].reshape(N, N)
+        assert np.all(np.tril(M, -1) == 0)
+
+
+def test_empty_batch():
+    from paper_1111_4144_gb300 import _lib as L
+    o = L.opts()
+    assert L.chol_inv_batched(L.CHOL_F32, 0, None, None, 4, None, None, None, None, o, None, 0, None) == L.CHOL_OK
