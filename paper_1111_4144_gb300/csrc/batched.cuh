@@ -52,6 +52,9 @@ CHOL_D int class_count(const BatchParams& p, int N) {
 // The method on one matrix held in packed-upper order, N compile-time.
 // Acc::at(e) returns a reference to element e (registers or shared memory).
 // ---------------------------------------------------------------------------
+// (Loops below run over fixed trip counts with compile-time guards: with
+// bounds that depend on an outer index the front end leaves a register array
+// in local memory.)
 template <typename V, int N, class Acc>
 CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 1]) {
     using R = typename traits<V>::real;
@@ -60,11 +63,13 @@ CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 
     for (int i = 0; i < N; ++i) {
         V col[N > 0 ? N : 1];  // column i of R above the diagonal: r_ki, k < i
 #pragma unroll
-        for (int k = 0; k < i; ++k) col[k] = m.at(pidx(N, k, i));
+        for (int k = 0; k < N; ++k)
+            if (k < i) col[k] = m.at(pidx(N, k, i));
         // Eq. 3
         R t = re_of(m.at(pidx(N, i, i)));
 #pragma unroll
-        for (int k = 0; k < i; ++k) t = fnma_abs2(col[k], t);
+        for (int k = 0; k < N; ++k)
+            if (k < i) t = fnma_abs2(col[k], t);
         if (info == 0 && !pivot_ok(t)) info = i + 1;
         R rii = sqrt(t);
         R inv = R(1) / rii;
@@ -72,11 +77,14 @@ CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 
         m.at(pidx(N, i, i)) = from_real<V>(rii);
         // Eq. 4
 #pragma unroll
-        for (int j = i + 1; j < N; ++j) {
-            V s = m.at(pidx(N, i, j));
+        for (int j = 0; j < N; ++j) {
+            if (j > i) {
+                V s = m.at(pidx(N, i, j));
 #pragma unroll
-            for (int k = 0; k < i; ++k) s = fnma_conj(col[k], m.at(pidx(N, k, j)), s);
-            m.at(pidx(N, i, j)) = scale_v(s, inv);
+                for (int k = 0; k < N; ++k)
+                    if (k < i) s = fnma_conj(col[k], m.at(pidx(N, k, j)), s);
+                m.at(pidx(N, i, j)) = scale_v(s, inv);
+            }
         }
     }
     return info;
@@ -95,23 +103,30 @@ CHOL_D void inverse_unrolled(Acc& m, const typename traits<V>::real (&dinv)[N > 
         V row[N > 0 ? N : 1];
         V acc[N > 0 ? N : 1];
 #pragma unroll
-        for (int k = i + 1; k < N; ++k) { row[k] = m.at(pidx(N, i, k)); acc[k] = zero_v<V>(); }
+        for (int k = 0; k < N; ++k)
+            if (k > i) { row[k] = m.at(pidx(N, i, k)); acc[k] = zero_v<V>(); }
 #pragma unroll
-        for (int k = i + 1; k < N; ++k) {
+        for (int k = 0; k < N; ++k) {
+            if (k > i) {
 #pragma unroll
-            for (int c = k; c < N; ++c) {
-                V v = m.at(pidx(N, k, c));
-                acc[c] = fma_v(row[k], v, acc[c]);
-                if (c > k) acc[k] = fma_conjb(row[c], v, acc[k]);
+                for (int c = 0; c < N; ++c) {
+                    if (c >= k) {
+                        V v = m.at(pidx(N, k, c));
+                        acc[c] = fma_v(row[k], v, acc[c]);
+                        if (c > k) acc[k] = fma_conjb(row[c], v, acc[k]);
+                    }
+                }
             }
         }
         const R inv = dinv[i];
         R sd = R(0);
 #pragma unroll
-        for (int j = i + 1; j < N; ++j) {
-            V x = scale_v(acc[j], -inv);
-            m.at(pidx(N, i, j)) = x;
-            sd = fma_re_conjb(row[j], x, sd);
+        for (int j = 0; j < N; ++j) {
+            if (j > i) {
+                V x = scale_v(acc[j], -inv);
+                m.at(pidx(N, i, j)) = x;
+                sd = fma_re_conjb(row[j], x, sd);
+            }
         }
         m.at(pidx(N, i, i)) = from_real<V>((inv - sd) * inv);
     }
