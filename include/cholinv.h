@@ -148,6 +148,41 @@ chol_status_t chol_inv_backward(chol_dtype_t dt, int32_t batch, const int32_t* n
                                 const int64_t* xoff, int32_t max_n, const void* X, const void* G, void* dA,
                                 const chol_opts_t* opts, void* ws, size_t ws_bytes, void* stream);
 
+/*
+ * chol_inv_batched_noalloc — chol_inv_batched for callers that cannot
+ * allocate device memory.  The paper has no counterpart; this is a
+ * deployment variant of the same computation.
+ *
+ * Some callers cannot hand the library a workspace: code that runs while a
+ * global-mode stream capture is open on another thread (cudaMalloc is
+ * prohibited then), real-time host paths where an allocation's latency or
+ * failure is not acceptable, and plugins whose host application owns and
+ * pools all device memory.  This entry point takes the same arguments as
+ * chol_inv_batched without ws/ws_bytes and allocates nothing: the
+ * size-class bucketing that a batch with per-matrix sizes needs uses a
+ * fixed scratch array compiled into the library (1 KiB plus 4 bytes per
+ * matrix for CHOL_NOALLOC_MAX_BATCH matrices, about 4 MiB), which every GPU
+ * that loads the library holds until the process exits.
+ *
+ *   - n != NULL and batch > CHOL_NOALLOC_MAX_BATCH returns
+ *     CHOL_ERR_WORKSPACE before anything is launched (uniform batches,
+ *     n == NULL, need no scratch and have no limit).
+ *   - The first call on a device looks up the scratch array's device
+ *     address (cudaGetSymbolAddress, with that device current); make that
+ *     first call before any stream capture begins.
+ *   - Every call shares the one scratch array and the array keeps the last
+ *     call's contents (each call clears the counters it needs before use).
+ *     Calls whose executions overlap on the GPU (different streams, or
+ *     concurrent graph replays) race on it: serialise them.
+ *   - Inputs, outputs, info and the stream are the caller's, as for
+ *     chol_inv_batched; no cudaMalloc, cudaFree or allocating library
+ *     routine is called.
+ */
+#define CHOL_NOALLOC_MAX_BATCH 1048576
+chol_status_t chol_inv_batched_noalloc(chol_dtype_t dt, int32_t batch, const int32_t* n, const int64_t* off,
+                                       int32_t max_n, const void* A, void* R, void* X, int32_t* info,
+                                       const chol_opts_t* opts, void* stream);
+
 /* Bytes of device workspace that a call with these arguments needs (0 = none). */
 size_t chol_workspace_bytes(int32_t call, chol_dtype_t dt, int32_t batch, int32_t max_n, int32_t has_sizes,
                             const chol_opts_t* opts);

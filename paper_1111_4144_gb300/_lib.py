@@ -25,6 +25,7 @@ CHOL_OK, CHOL_ERR_ARG, CHOL_ERR_CUDA, CHOL_ERR_UNSUPPORTED, CHOL_ERR_TIMEOUT, CH
 CHOL_PREC_NATIVE, CHOL_PREC_FP32_REFINE, CHOL_PREC_TF32_REFINE, CHOL_PREC_BF16_REFINE = 0, 1, 2, 3
 CHOL_FLAG_PIVOT64 = 0x1
 CHOL_CALL_FACTOR, CHOL_CALL_INV, CHOL_CALL_BACKWARD = 0, 1, 2
+CHOL_NOALLOC_MAX_BATCH = 1048576
 
 
 class chol_opts_t(ctypes.Structure):
@@ -40,6 +41,8 @@ SIGNATURES = {
                                  ctypes.POINTER(chol_opts_t), c_vp, c_size, c_vp]),
     "chol_inv_backward": (c_i32, [c_i32, c_i32, c_vp, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp,
                                   ctypes.POINTER(chol_opts_t), c_vp, c_size, c_vp]),
+    "chol_inv_batched_noalloc": (c_i32, [c_i32, c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp,
+                                         ctypes.POINTER(chol_opts_t), c_vp]),
     "chol_workspace_bytes": (c_size, [c_i32, c_i32, c_i32, c_i32, c_i32, ctypes.POINTER(chol_opts_t)]),
     "chol_status_string": (ctypes.c_char_p, [c_i32]),
     "chol_last_device_error": (c_i32, [c_vp]),
@@ -104,6 +107,10 @@ def chol_inv_batched(*args):
 
 def chol_inv_backward(*args):
     return load().chol_inv_backward(*args)
+
+
+def chol_inv_batched_noalloc(*args):
+    return load().chol_inv_batched_noalloc(*args)
 
 
 def chol_workspace_bytes(*args):

@@ -237,6 +237,58 @@ chol_status_t chol_last_device_error(void* stream) {
     return static_cast<chol_status_t>(v);
 }
 
+// ---------------------------------------------------------------------------
+// chol_inv_batched_noalloc: the bucketing scratch of a batch with per-matrix
+// sizes lives in this fixed device array instead of a caller workspace.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+constexpr size_t kNoallocScratchBytes = kWsHeader + 4 * (size_t)CHOL_NOALLOC_MAX_BATCH;
+}
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+namespace {
+void* g_noalloc_ptr[kMaxDevices];
+std::mutex g_noalloc_mu;
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (host code cannot use the symbol itself as a device pointer).
+chol_status_t noalloc_scratch(void** out) {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) return CHOL_ERR_CUDA;
+    if (d < 0 || d >= kMaxDevices) return CHOL_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_ptr[d] == nullptr) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return CHOL_ERR_CUDA;
+        g_noalloc_ptr[d] = p;
+    }
+    *out = g_noalloc_ptr[d];
+    return CHOL_OK;
+}
+}  // namespace
+
+extern "C" {
+
+chol_status_t chol_inv_batched_noalloc(chol_dtype_t dt, int32_t batch, const int32_t* n, const int64_t* off,
+                                       int32_t max_n, const void* A, void* R, void* X, int32_t* info,
+                                       const chol_opts_t* opts, void* stream) {
+    const chol_opts_t o = opts_or_default(opts);
+    chol_status_t st = check_common(dt, batch, max_n, o);
+    if (st != CHOL_OK || batch == 0) return st;
+    if (A == nullptr || X == nullptr) return CHOL_ERR_ARG;
+    if (o.prec == CHOL_PREC_FP32_REFINE && o.refine_steps != 0) return CHOL_ERR_UNSUPPORTED;
+    if (n != nullptr && batch > CHOL_NOALLOC_MAX_BATCH) return CHOL_ERR_WORKSPACE;
+    void* scratch = nullptr;
+    if (n != nullptr) {
+        st = noalloc_scratch(&scratch);
+        if (st != CHOL_OK) return st;
+    }
+    BatchParams p = make_params(batch, n, off, max_n, A, (R == X) ? nullptr : R, X, info, o, 1);
+    return enqueue_batched(dt, p, scratch, static_cast<cudaStream_t>(stream), false);
+}
+
 int32_t chol_version(void) { return 100; }
 
 chol_status_t chol_plan_inv_create(chol_plan_t** plan, chol_dtype_t dt, int32_t batch, const int32_t* n,
