@@ -46,6 +46,8 @@ def parse():
                          "for profiler runs")
     ap.add_argument("--batch", type=int, default=BATCH, help="matrices per GPU (profiling cases)")
     ap.add_argument("--sizes", default=",".join(map(str, SIZES)), help="matrix orders, equal shares")
+    ap.add_argument("--uniform", action="store_true",
+                    help="profiling case: one order only (first of --sizes), no per-matrix sizes")
     return ap.parse_args()
 
 
@@ -211,6 +213,8 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     _lib.load()
     sizes = tuple(int(x) for x in args.sizes.split(","))
+    if args.uniform:
+        sizes = sizes[:1]
     b = make_workload(rank, args.batch, sizes)
     A64 = b.A.astype(np.complex64)
     A = torch.from_numpy(A64).to(dev)
@@ -218,8 +222,12 @@ def run_ours(args, rank, world, local_rank):
     off = torch.from_numpy(b.off).to(dev)
     X = torch.zeros_like(A)
     stream = torch.cuda.Stream(device=dev)
-    plan = api.Plan(A, X, n, off, max(sizes), layout=api.LAYOUT_PACKED)
-    kernels_per_step = 3 + max(sizes)  # hist, scan, scatter + one class kernel per order 1..max_n
+    if args.uniform:
+        plan = api.Plan(A, X, None, None, sizes[0], layout=api.LAYOUT_PACKED)
+        kernels_per_step = 1
+    else:
+        plan = api.Plan(A, X, n, off, max(sizes), layout=api.LAYOUT_PACKED)
+        kernels_per_step = 3 + max(sizes)  # hist, scan, scatter + one class kernel per order 1..max_n
 
     def timed(fn, steps):
         ev0 = torch.cuda.Event(enable_timing=True)

@@ -132,58 +132,169 @@ CHOL_D void inverse_unrolled(Acc& m, const typename traits<V>::real (&dinv)[N > 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async; sm_80+ PTX).
+// ---------------------------------------------------------------------------
+CHOL_D unsigned smem_u32(const void* p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
+
+template <int BYTES>
+CHOL_D void cp_async(void* dst_smem, const void* src) {
+    if constexpr (BYTES == 16) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(dst_smem)), "l"(src), "n"(BYTES)
+                     : "memory");
+    }
+}
+CHOL_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+CHOL_D void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory"); }
+
+// ---------------------------------------------------------------------------
+// Lane kernel layout.  A CTA handles THREADS matrices per chunk.  Shared
+// memory holds each matrix's packed triangle in 16-byte units (U elements
+// per unit); unit u of the matrix of thread q sits at [u][q] (row stride
+// LD = THREADS + 1 units), so a warp reading unit u of its 32 matrices, or a
+// loader writing consecutive units of one matrix, touches distinct banks.
+// ---------------------------------------------------------------------------
+template <typename V, int N>
+struct LaneCfg {
+    static constexpr int TN = tri(N);
+    static constexpr int U = 16 / (int)sizeof(V);      // elements per 16-byte unit
+    static constexpr int NU = (TN + U - 1) / U;        // units per matrix
+    // Registers hold the whole matrix when its packed triangle takes at most
+    // 144 32-bit words; larger matrices are worked in place in shared memory.
+    static constexpr bool REGS = TN * traits<V>::words <= 144;
+    static constexpr int UNIT_BYTES = 16;
+    static constexpr int bytes_per_matrix = NU * UNIT_BYTES;
+    // register-resident kernels double-buffer (load chunk k+1 while computing k)
+    static constexpr int NBUF = REGS ? 2 : 1;
+    static constexpr int THREADS = bytes_per_matrix * 128 * NBUF <= 98304 ? 128
+                                 : bytes_per_matrix * 64 * NBUF <= 98304 ? 64 : 32;
+    static constexpr int LD = THREADS + 1;             // units per shared row
+    static constexpr size_t BUF_BYTES = (size_t)NU * LD * UNIT_BYTES;
+    static constexpr size_t SMEM = NBUF * BUF_BYTES + (size_t)THREADS * (NBUF * sizeof(int64_t) + sizeof(int)) +
+                                   2 * (size_t)TN + 16;
+};
+
+template <typename V, int N>
+struct UnitRef {  // element e of the matrix of thread q inside a unit buffer
+    static CHOL_D V& at(uint4* buf, int q, int e) {
+        constexpr int U = LaneCfg<V, N>::U;
+        constexpr int LD = LaneCfg<V, N>::LD;
+        return reinterpret_cast<V*>(buf + (e / U) * LD + q)[e % U];
+    }
+};
+
 template <typename V, int TN>
 struct RegMat {
     V a[TN];
     CHOL_D V& at(int e) { return a[e]; }
 };
 
-template <typename V>
-struct SmemCol {
-    V* base;     // &buf[t]
-    int stride;  // elements between rows
-    CHOL_D V& at(int e) { return base[e * stride]; }
+template <typename V, int N>
+struct SmemMat {
+    uint4* buf;
+    int q;
+    CHOL_D V& at(int e) { return UnitRef<V, N>::at(buf, q, e); }
 };
 
-// Registers hold the whole matrix when its packed triangle takes at most this
-// many 32-bit words; larger matrices are worked in place in shared memory.
-constexpr int kRegWords = 144;
-
+// Stage the chunk's matrices into a unit buffer with cp.async (not waited on).
+// vec: every matrix starts on a 16-byte boundary and the layout is packed, so
+// whole units are copied; otherwise element by element (dense layout or
+// unaligned offsets).
 template <typename V, int N>
-constexpr bool lane_in_regs() { return tri(N) * traits<V>::words <= kRegWords; }
-
-// Threads per CTA of the lane kernel: as many as fit in ~96 KB of staging.
-template <typename V, int N>
-constexpr int lane_threads() {
-    constexpr int bytes = tri(N) * (int)sizeof(V);
-    return bytes * 128 <= 98304 ? 128 : bytes * 64 <= 98304 ? 64 : 32;
+CHOL_D void lane_stage(const BatchParams& p, const V* A, uint4* buf, const int64_t* s_off, const uint8_t* s_i,
+                       const uint8_t* s_j, int m, bool vec) {
+    using C = LaneCfg<V, N>;
+    const int t = threadIdx.x;
+    if (vec) {
+        for (int f = t; f < m * C::NU; f += C::THREADS) {
+            const int q = f / C::NU, u = f - q * C::NU;
+            const V* src = A + s_off[q] + u * C::U;
+            uint4* dst = buf + u * C::LD + q;
+            if ((u + 1) * C::U <= C::TN) {
+                cp_async<16>(dst, src);
+            } else {
+#pragma unroll
+                for (int r = 0; r < C::U; ++r)
+                    if (u * C::U + r < C::TN) cp_async<(int)sizeof(V)>(reinterpret_cast<V*>(dst) + r, src + r);
+            }
+        }
+    } else {
+        for (int f = t; f < m * C::TN; f += C::THREADS) {
+            const int q = f / C::TN, e = f - q * C::TN;
+            const int64_t g = p.layout ? (int64_t)e : (int64_t)s_i[e] * N + s_j[e];
+            cp_async<(int)sizeof(V)>(&UnitRef<V, N>::at(buf, q, e), A + s_off[q] + g);
+        }
+    }
+    cp_async_commit();
 }
+
+// Write the chunk's results (X, or R when factoring) from a unit buffer.
 template <typename V, int N>
-constexpr int lane_stride() { return lane_threads<V, N>() + 1; }
-template <typename V, int N>
-constexpr size_t lane_smem_bytes() {
-    return (size_t)tri(N) * lane_stride<V, N>() * sizeof(V) + (size_t)lane_threads<V, N>() * sizeof(int) +
-           2 * (size_t)tri(N) * sizeof(uint8_t) + 16;
+CHOL_D void lane_store(const BatchParams& p, V* out, uint4* buf, const int64_t* s_off, const int* s_info,
+                       const uint8_t* s_i, const uint8_t* s_j, int m, bool vec, bool is_factor, bool fill_lower) {
+    using C = LaneCfg<V, N>;
+    const int t = threadIdx.x;
+    if (vec) {
+        for (int f = t; f < m * C::NU; f += C::THREADS) {
+            const int q = f / C::NU, u = f - q * C::NU;
+            V* dst = out + s_off[q] + u * C::U;
+            uint4 v = buf[u * C::LD + q];
+            if (s_info[q] != 0) {
+                const V qn = nan_v<V>();
+#pragma unroll
+                for (int r = 0; r < C::U; ++r) reinterpret_cast<V*>(&v)[r] = qn;
+            }
+            if ((u + 1) * C::U <= C::TN) {
+                *reinterpret_cast<uint4*>(dst) = v;
+            } else {
+#pragma unroll
+                for (int r = 0; r < C::U; ++r)
+                    if (u * C::U + r < C::TN) dst[r] = reinterpret_cast<V*>(&v)[r];
+            }
+        }
+    } else {
+        for (int f = t; f < m * C::TN; f += C::THREADS) {
+            const int q = f / C::TN, e = f - q * C::TN;
+            const int64_t o = s_off[q];
+            const int i = s_i[e], j = s_j[e];
+            const bool bad = s_info[q] != 0;
+            const V v = bad ? nan_v<V>() : UnitRef<V, N>::at(buf, q, e);
+            if (p.layout) {
+                out[o + e] = v;
+            } else {
+                out[o + (int64_t)i * N + j] = v;
+                if (i != j) {
+                    if (is_factor) out[o + (int64_t)j * N + i] = bad ? nan_v<V>() : zero_v<V>();
+                    else if (fill_lower) out[o + (int64_t)j * N + i] = conj_v(v);
+                }
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Lane kernel: one matrix per thread.
 // ---------------------------------------------------------------------------
 template <typename V, int N>
-__global__ void __launch_bounds__(lane_threads<V, N>())
+__global__ void __launch_bounds__(LaneCfg<V, N>::THREADS)
 k_lane(BatchParams p) {
-    constexpr int THREADS = lane_threads<V, N>();
-    constexpr int TN = tri(N);
-    constexpr int LD = lane_stride<V, N>();
+    using C = LaneCfg<V, N>;
+    constexpr int THREADS = C::THREADS;
+    constexpr int TN = C::TN;
     using R = typename traits<V>::real;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* buf = reinterpret_cast<V*>(smem_raw);                                  // [TN][LD]
-    int* s_info = reinterpret_cast<int*>(buf + (size_t)TN * LD);              // [THREADS]
-    uint8_t* s_i = reinterpret_cast<uint8_t*>(s_info + THREADS);              // [TN] row of element e
-    uint8_t* s_j = s_i + TN;                                                  // [TN] column of element e
+    uint4* bufs = reinterpret_cast<uint4*>(smem_raw);                                // NBUF x [NU][LD] units
+    int64_t* s_offs = reinterpret_cast<int64_t*>(smem_raw + C::NBUF * C::BUF_BYTES);  // NBUF x [THREADS]
+    int* s_info = reinterpret_cast<int*>(s_offs + C::NBUF * THREADS);                 // [THREADS]
+    uint8_t* s_i = reinterpret_cast<uint8_t*>(s_info + THREADS);                      // [TN] row of element e
+    uint8_t* s_j = s_i + TN;                                                          // [TN] column of element e
 
-    for (int e = threadIdx.x; e < TN; e += THREADS) {
+    const int t = threadIdx.x;
+    for (int e = t; e < TN; e += THREADS) {
         int i = 0;
         while (pidx(N, i + 1, i + 1) <= e && i + 1 < N) ++i;
         s_i[e] = (uint8_t)i;
@@ -194,96 +305,108 @@ k_lane(BatchParams p) {
     const V* A = static_cast<const V*>(p.A);
     V* Xo = static_cast<V*>(p.X);
     V* Ro = static_cast<V*>(p.R);
-    const int t = threadIdx.x;
-    __syncthreads();
+    const bool store_R = p.R != nullptr && p.want_inv;
 
-    for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
-        const int base = chunk * THREADS;
-        const int m = min(THREADS, count - base);
-        // ---- stage: global -> shared (consecutive threads read consecutive elements of a matrix)
-        for (int f = t; f < m * TN; f += THREADS) {
-            const int q = f / TN, e = f - q * TN;
-            const int64_t b = member_index(p, N, base + q);
-            const int64_t o = matrix_offset(p, N, b);
-            const int64_t g = p.layout ? (int64_t)e : (int64_t)s_i[e] * N + s_j[e];
-            buf[e * LD + q] = A[o + g];
-        }
-        __syncthreads();
-        // ---- compute: thread t owns matrix base + t
-        int info = 0;
+    // Offsets of a chunk's matrices into s_off; returns (CTA-uniformly)
+    // whether whole 16-byte units can be copied.
+    auto chunk_offsets = [&](int chunk, int m, int64_t* s_off) {
+        int ok = 1;
         if (t < m) {
-            R dinv[N];
-            if constexpr (lane_in_regs<V, N>()) {
-                RegMat<V, TN> r;
+            const int64_t b = member_index(p, N, chunk * THREADS + t);
+            const int64_t o = matrix_offset(p, N, b);
+            s_off[t] = o;
+            ok = (o % C::U) == 0;
+        }
+        return __syncthreads_and(ok) != 0 && p.layout == 1;
+    };
+
+    if constexpr (C::REGS) {
+        // ---- register-resident: double-buffered, chunk k+1 loads while k computes
+        int chunk = blockIdx.x;
+        if (chunk >= nchunks) return;
+        int m = min(THREADS, count - chunk * THREADS);
+        bool vec = chunk_offsets(chunk, m, s_offs);
+        int cur = 0;
+        lane_stage<V, N>(p, A, bufs, s_offs, s_i, s_j, m, vec);
+        for (; chunk < nchunks; chunk += gridDim.x) {
+            uint4* buf = bufs + cur * (C::BUF_BYTES / 16);
+            int64_t* s_off = s_offs + cur * THREADS;
+            cp_async_wait<0>();
+            __syncthreads();
+            RegMat<V, TN> r;
 #pragma unroll
-                for (int e = 0; e < TN; ++e) r.a[e] = buf[e * LD + t];
+            for (int e = 0; e < TN; ++e) r.a[e] = UnitRef<V, N>::at(buf, t, e);
+            const int64_t my_off = t < m ? s_off[t] : 0;
+            // prefetch the next chunk into the other buffer
+            const int next = chunk + gridDim.x;
+            int m_next = 0;
+            bool vec_next = false;
+            if (next < nchunks) {
+                m_next = min(THREADS, count - next * THREADS);
+                vec_next = chunk_offsets(next, m_next, s_offs + (cur ^ 1) * THREADS);
+                lane_stage<V, N>(p, A, bufs + (cur ^ 1) * (C::BUF_BYTES / 16), s_offs + (cur ^ 1) * THREADS, s_i,
+                                 s_j, m_next, vec_next);
+            }
+            int info = 0;
+            R dinv[N];
+            if (t < m) {
                 info = factor_unrolled<V, N>(r, dinv);
-                if (p.R && p.want_inv) {
-                    // keep R for the store stage in the upper rows of the staging
-                    // buffer?  No: R and X share storage, so R is stored here.
-                    const int64_t b = member_index(p, N, base + t);
-                    const int64_t o = matrix_offset(p, N, b);
+                if (store_R) {
 #pragma unroll
                     for (int e = 0; e < TN; ++e) {
                         const int64_t g = p.layout ? (int64_t)e : (int64_t)s_i[e] * N + s_j[e];
-                        Ro[o + g] = info ? nan_v<V>() : r.a[e];
+                        Ro[my_off + g] = info ? nan_v<V>() : r.a[e];
+                    }
+                    if (!p.layout) {
+#pragma unroll
+                        for (int e = 0; e < TN; ++e)
+                            if (s_i[e] != s_j[e])
+                                Ro[my_off + (int64_t)s_j[e] * N + s_i[e]] = info ? nan_v<V>() : zero_v<V>();
                     }
                 }
                 if (p.want_inv) inverse_unrolled<V, N>(r, dinv);
 #pragma unroll
-                for (int e = 0; e < TN; ++e) buf[e * LD + t] = r.a[e];
-            } else {
-                SmemCol<V> s{buf + t, LD};
-                info = factor_unrolled<V, N>(s, dinv);
-                if (p.R && p.want_inv) {
-                    const int64_t b = member_index(p, N, base + t);
-                    const int64_t o = matrix_offset(p, N, b);
-                    for (int e = 0; e < TN; ++e) {
-                        const int64_t g = p.layout ? (int64_t)e : (int64_t)s_i[e] * N + s_j[e];
-                        Ro[o + g] = info ? nan_v<V>() : buf[e * LD + t];
-                    }
-                }
-                if (p.want_inv) inverse_unrolled<V, N>(s, dinv);
+                for (int e = 0; e < TN; ++e) UnitRef<V, N>::at(buf, t, e) = r.a[e];
+                s_info[t] = info;
             }
-            s_info[t] = info;
+            __syncthreads();
+            lane_store<V, N>(p, p.want_inv ? Xo : Ro, buf, s_off, s_info, s_i, s_j, m, vec, !p.want_inv,
+                             p.fill_lower != 0);
+            if (p.info)
+                for (int q = t; q < m; q += THREADS) p.info[member_index(p, N, chunk * THREADS + q)] = s_info[q];
+            __syncthreads();
+            m = m_next;
+            vec = vec_next;
+            cur ^= 1;
         }
-        __syncthreads();
-        // ---- store: shared -> global
-        V* out = p.want_inv ? Xo : Ro;
-        for (int f = t; f < m * TN; f += THREADS) {
-            const int q = f / TN, e = f - q * TN;
-            const int64_t b = member_index(p, N, base + q);
-            const int64_t o = matrix_offset(p, N, b);
-            const int i = s_i[e], j = s_j[e];
-            const bool bad = s_info[q] != 0;
-            V v = bad ? nan_v<V>() : buf[e * LD + q];
-            if (p.layout) {
-                out[o + e] = v;
-            } else {
-                out[o + (int64_t)i * N + j] = v;
-                if (i != j) {
-                    if (!p.want_inv) out[o + (int64_t)j * N + i] = bad ? nan_v<V>() : zero_v<V>();
-                    else if (p.fill_lower) out[o + (int64_t)j * N + i] = conj_v(v);
-                }
+    } else {
+        // ---- shared-memory-resident: one buffer, the method runs in place
+        uint4* buf = bufs;
+        int64_t* s_off = s_offs;
+        for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+            const int m = min(THREADS, count - chunk * THREADS);
+            const bool vec = chunk_offsets(chunk, m, s_off);
+            lane_stage<V, N>(p, A, buf, s_off, s_i, s_j, m, vec);
+            cp_async_wait<0>();
+            __syncthreads();
+            int info = 0;
+            R dinv[N];
+            SmemMat<V, N> sm{buf, t};
+            if (t < m) info = factor_unrolled<V, N>(sm, dinv);
+            if (t < m) s_info[t] = info;
+            if (store_R) {
+                __syncthreads();
+                lane_store<V, N>(p, Ro, buf, s_off, s_info, s_i, s_j, m, vec, true, false);
+                __syncthreads();
             }
+            if (p.want_inv && t < m) inverse_unrolled<V, N>(sm, dinv);
+            __syncthreads();
+            lane_store<V, N>(p, p.want_inv ? Xo : Ro, buf, s_off, s_info, s_i, s_j, m, vec, !p.want_inv,
+                             p.fill_lower != 0);
+            if (p.info)
+                for (int q = t; q < m; q += THREADS) p.info[member_index(p, N, chunk * THREADS + q)] = s_info[q];
+            __syncthreads();
         }
-        if (!p.want_inv || p.R == nullptr) {
-            // nothing else to write
-        } else if (!p.layout) {
-            // dense R: zero its strictly lower part
-            for (int f = t; f < m * TN; f += THREADS) {
-                const int q = f / TN, e = f - q * TN;
-                const int i = s_i[e], j = s_j[e];
-                if (i == j) continue;
-                const int64_t b = member_index(p, N, base + q);
-                const int64_t o = matrix_offset(p, N, b);
-                Ro[o + (int64_t)j * N + i] = s_info[q] ? nan_v<V>() : zero_v<V>();
-            }
-        }
-        if (p.info) {
-            for (int q = t; q < m; q += THREADS) p.info[member_index(p, N, base + q)] = s_info[q];
-        }
-        __syncthreads();
     }
 }
 

@@ -1,0 +1,316 @@
+// Group kernel: G threads (a power of two, G <= 32) share one matrix.
+//
+// Thread h of a group owns the columns j = c*G + h (c = 0..NC-1) and keeps
+// their upper parts in registers: first the columns of A, then of R, then of
+// X, each replacing the last in place.  A copy of the packed upper triangle
+// in shared memory (the matrix's "mirror") carries what a thread needs from
+// columns it does not own:
+//   Eq. 4, row i      needs column i of R above the diagonal  -> read from the mirror
+//   Sec. IV.A, row i  needs row i of R and, for x~_kj with k > j, row j of X
+//                                                            -> read from the mirror
+// Every new row of R or X is written to the mirror as it is produced, so at
+// the end the mirror holds the result and is stored with coalesced copies.
+// Rows are fully unrolled (N compile-time), so every register index is a
+// compile-time constant; ownership tests on the runtime lane index become
+// predicates, not branches.
+#pragma once
+
+#include "batched.cuh"
+
+namespace cholinv {
+
+template <typename V, int N, int G>
+struct GroupCfg {
+    static_assert(G >= 2 && G <= 32 && (G & (G - 1)) == 0, "G must be a power of two in [2, 32]");
+    static constexpr int TN = tri(N);
+    static constexpr int NC = (N + G - 1) / G;   // columns per thread
+    static constexpr int MPW = 32 / G;           // matrices per warp
+    static constexpr int WARPS = 4;
+    static constexpr int THREADS = 32 * WARPS;
+    static constexpr int MPC = MPW * WARPS;       // matrices per CTA chunk
+    // bytes of one matrix's mirror: whole 16-byte units, an odd number of them
+    // so that the groups of a warp hit different banks
+    static constexpr int UNITS0 = (TN * (int)sizeof(V) + 15) / 16;
+    static constexpr int UNITS = UNITS0 % 2 ? UNITS0 : UNITS0 + 1;
+    static constexpr int STRIDE = UNITS * 16;
+    static constexpr int U = 16 / (int)sizeof(V);
+    static constexpr size_t SMEM = (size_t)MPC * STRIDE + (size_t)MPC * (sizeof(int64_t) + sizeof(int)) +
+                                   2 * (size_t)TN + 16;
+};
+
+// Copy the chunk's matrices into the mirrors (cp.async, not waited on).
+template <typename V, int N, int G>
+CHOL_D void group_stage(const BatchParams& p, const V* A, unsigned char* mir, const int64_t* s_off,
+                        const uint8_t* s_i, const uint8_t* s_j, int m, bool vec) {
+    using C = GroupCfg<V, N, G>;
+    const int t = threadIdx.x;
+    if (vec) {
+        constexpr int FULL = C::TN / C::U;  // whole units per matrix
+        constexpr int TAIL = C::TN - FULL * C::U;
+        for (int f = t; f < m * FULL; f += C::THREADS) {
+            const int q = f / FULL, u = f - q * FULL;
+            cp_async<16>(mir + (size_t)q * C::STRIDE + u * 16, A + s_off[q] + u * C::U);
+        }
+        if constexpr (TAIL > 0) {
+            for (int f = t; f < m * TAIL; f += C::THREADS) {
+                const int q = f / TAIL, r = f - q * TAIL;
+                const int e = FULL * C::U + r;
+                cp_async<(int)sizeof(V)>(mir + (size_t)q * C::STRIDE + e * sizeof(V), A + s_off[q] + e);
+            }
+        }
+    } else {
+        for (int f = t; f < m * C::TN; f += C::THREADS) {
+            const int q = f / C::TN, e = f - q * C::TN;
+            const int64_t g = p.layout ? (int64_t)e : (int64_t)s_i[e] * N + s_j[e];
+            cp_async<(int)sizeof(V)>(mir + (size_t)q * C::STRIDE + e * sizeof(V), A + s_off[q] + g);
+        }
+    }
+    cp_async_commit();
+}
+
+// Store the mirrors (X, or R when factoring) to global memory.
+template <typename V, int N, int G>
+CHOL_D void group_store(const BatchParams& p, V* out, const unsigned char* mir, const int64_t* s_off,
+                        const int* s_info, const uint8_t* s_i, const uint8_t* s_j, int m, bool vec, bool is_factor,
+                        bool fill_lower) {
+    using C = GroupCfg<V, N, G>;
+    const int t = threadIdx.x;
+    if (vec) {
+        constexpr int FULL = C::TN / C::U;
+        constexpr int TAIL = C::TN - FULL * C::U;
+        for (int f = t; f < m * FULL; f += C::THREADS) {
+            const int q = f / FULL, u = f - q * FULL;
+            uint4 v = *reinterpret_cast<const uint4*>(mir + (size_t)q * C::STRIDE + u * 16);
+            if (s_info[q] != 0) {
+                const V qn = nan_v<V>();
+#pragma unroll
+                for (int r = 0; r < C::U; ++r) reinterpret_cast<V*>(&v)[r] = qn;
+            }
+            *reinterpret_cast<uint4*>(out + s_off[q] + u * C::U) = v;
+        }
+        if constexpr (TAIL > 0) {
+            for (int f = t; f < m * TAIL; f += C::THREADS) {
+                const int q = f / TAIL, r = f - q * TAIL;
+                const int e = FULL * C::U + r;
+                const V v = *reinterpret_cast<const V*>(mir + (size_t)q * C::STRIDE + e * sizeof(V));
+                out[s_off[q] + e] = s_info[q] ? nan_v<V>() : v;
+            }
+        }
+    } else {
+        for (int f = t; f < m * C::TN; f += C::THREADS) {
+            const int q = f / C::TN, e = f - q * C::TN;
+            const int64_t o = s_off[q];
+            const int i = s_i[e], j = s_j[e];
+            const bool bad = s_info[q] != 0;
+            const V v = bad ? nan_v<V>() : *reinterpret_cast<const V*>(mir + (size_t)q * C::STRIDE + e * sizeof(V));
+            if (p.layout) {
+                out[o + e] = v;
+            } else {
+                out[o + (int64_t)i * N + j] = v;
+                if (i != j) {
+                    if (is_factor) out[o + (int64_t)j * N + i] = bad ? nan_v<V>() : zero_v<V>();
+                    else if (fill_lower) out[o + (int64_t)j * N + i] = conj_v(v);
+                }
+            }
+        }
+    }
+}
+
+// Offset (in elements) of row r of the packed upper mirror, minus r, so that
+// element (r, j) sits at row_base(r) + j.
+CHOL_HD constexpr int row_base(int n, int r) { return r * n - (r * (r - 1)) / 2 - r; }
+
+// Threads per matrix for order N: the smallest power of two (2..32) whose
+// per-thread share of the columns fits in about 112 32-bit registers; 0 if
+// none does (the one-matrix-per-warp kernel takes those orders).
+template <typename V, int N>
+constexpr int group_size() {
+    for (int g = 2; g <= 32; g *= 2) {
+        int words = 0;
+        const int nc = (N + g - 1) / g;
+        for (int c = 0; c < nc; ++c) words += (c * g + g < N ? c * g + g : N) * traits<V>::words;
+        if (words <= 112) return g;
+    }
+    return 0;
+}
+
+template <typename V, int N, int G>
+__global__ void __launch_bounds__(GroupCfg<V, N, G>::THREADS)
+k_group(BatchParams p) {
+    using C = GroupCfg<V, N, G>;
+    using R = typename traits<V>::real;
+    constexpr int NC = C::NC;
+    constexpr int TN = C::TN;
+    constexpr int THREADS = C::THREADS;
+    constexpr int MPC = C::MPC;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* mirs = smem_raw;                                              // [MPC][STRIDE]
+    int64_t* s_off = reinterpret_cast<int64_t*>(smem_raw + (size_t)MPC * C::STRIDE);  // [MPC]
+    int* s_info = reinterpret_cast<int*>(s_off + MPC);                           // [MPC]
+    uint8_t* s_i = reinterpret_cast<uint8_t*>(s_info + MPC);                     // [TN]
+    uint8_t* s_j = s_i + TN;
+
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int h = t & (G - 1);           // position in the group
+    const int q = t / G;                 // matrix within the chunk
+    const int gbase = lane & ~(G - 1);   // first lane of this group
+    for (int e = t; e < TN; e += THREADS) {
+        int i = 0;
+        while (pidx(N, i + 1, i + 1) <= e && i + 1 < N) ++i;
+        s_i[e] = (uint8_t)i;
+        s_j[e] = (uint8_t)(e - pidx(N, i, i) + i);
+    }
+    const int count = class_count(p, N);
+    const int nchunks = (count + MPC - 1) / MPC;
+    const V* A = static_cast<const V*>(p.A);
+    V* Xo = static_cast<V*>(p.X);
+    V* Ro = static_cast<V*>(p.R);
+    const bool store_R = p.R != nullptr && p.want_inv;
+    __syncthreads();
+
+    for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+        const int m = min(MPC, count - chunk * MPC);
+        int ok = 1;
+        if (t < m) {
+            const int64_t b = member_index(p, N, chunk * MPC + t);
+            const int64_t o = matrix_offset(p, N, b);
+            s_off[t] = o;
+            ok = (o % C::U) == 0;
+        }
+        const bool vec = (__syncthreads_and(ok) != 0) && p.layout == 1;
+        group_stage<V, N, G>(p, A, mirs, s_off, s_i, s_j, m, vec);
+        cp_async_wait<0>();
+        __syncthreads();
+
+        const bool live = q < m;
+        V* M = reinterpret_cast<V*>(mirs + (size_t)(live ? q : 0) * C::STRIDE);
+        // own columns, upper parts, into registers
+        V col[NC][N];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int j = c * G + h;
+            const int jj = min(j, N - 1);
+#pragma unroll
+            for (int r = 0; r < N; ++r) {
+                if (r <= c * G + G - 1) {
+                    const V v = M[row_base(N, r) + jj];
+                    col[c][r] = (r <= j && j < N) ? v : zero_v<V>();
+                }
+            }
+        }
+        R dinv[N];
+        int info = 0;
+        // ---------------- factor, Eqs. 3-4, row by row
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            V ci[N > 0 ? N : 1];  // column i above the diagonal, from the mirror
+#pragma unroll
+            for (int k = 0; k < N; ++k)
+                if (k < i) ci[k] = M[row_base(N, k) + i];
+            V sv[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                if (i <= c * G + G - 1) {
+                    V s = col[c][i];
+#pragma unroll
+                    for (int k = 0; k < N; ++k)
+                        if (k < i) s = fnma_conj(ci[k], col[c][k], s);
+                    sv[c] = s;
+                }
+            }
+            const int co = i / G, ho = i % G;
+            const R tc = re_of(sv[co]);
+            const R tt = __shfl_sync(0xffffffffu, tc, gbase + ho);
+            if (info == 0 && !pivot_ok(tt)) info = i + 1;
+            const R rii = sqrt(tt);
+            const R inv = R(1) / rii;
+            dinv[i] = inv;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                if (i <= c * G + G - 1) {
+                    const int j = c * G + h;
+                    if (j < N && j >= i) {
+                        const V r = (j == i) ? from_real<V>(rii) : scale_v(sv[c], inv);
+                        col[c][i] = r;
+                        if (live) M[row_base(N, i) + j] = r;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (live && h == 0) s_info[q] = info;
+        if (store_R || !p.want_inv) {
+            __syncthreads();
+            group_store<V, N, G>(p, Ro, mirs, s_off, s_info, s_i, s_j, m, vec, true, false);
+            __syncthreads();
+        }
+        if (p.want_inv) {
+            // ---------------- proposed inverse, Sec. IV.A, rows N..1
+#pragma unroll
+            for (int i = N - 1; i >= 0; --i) {
+                V rr[N > 0 ? N : 1];  // row i of R
+#pragma unroll
+                for (int k = 0; k < N; ++k)
+                    if (k > i) rr[k] = M[row_base(N, i) + k];
+                const R inv = dinv[i];
+                V xs[NC];
+                R sd = R(0);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    if (c * G + G - 1 > i) {
+                        const int j = c * G + h;
+                        const bool act = j > i && j < N;
+                        const int jb = row_base(N, min(j, N - 1));
+                        V acc = zero_v<V>();
+#pragma unroll
+                        for (int k = 0; k < N; ++k) {
+                            if (k > i) {
+                                V xt;
+                                if (k <= c * G) {
+                                    xt = col[c][k];                       // k <= j: own column, row k
+                                } else if (k > c * G + G - 1) {
+                                    xt = conj_v(M[jb + k]);               // k > j: row j of X
+                                } else {
+                                    xt = (k <= j) ? col[c][k] : conj_v(M[jb + k]);
+                                }
+                                acc = fma_v(rr[k], xt, acc);
+                            }
+                        }
+                        xs[c] = scale_v(acc, -inv);
+                        // diagonal partial: r_ij conj(x_ij) over own columns
+                        if (act) sd = fma_re_conjb(col[c][i], xs[c], sd);
+                    }
+                }
+                __syncwarp();  // row i of R is read; it may now be overwritten
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    if (c * G + G - 1 > i) {
+                        const int j = c * G + h;
+                        if (j > i && j < N) {
+                            col[c][i] = xs[c];
+                            if (live) M[row_base(N, i) + j] = xs[c];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int d = G / 2; d > 0; d >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, d);
+                const V xd = from_real<V>((inv - sd) * inv);
+                const int co = i / G, ho = i % G;
+                if (h == ho) {
+                    col[co][i] = xd;
+                    if (live) M[row_base(N, i) + i] = xd;
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+            group_store<V, N, G>(p, Xo, mirs, s_off, s_info, s_i, s_j, m, vec, false, p.fill_lower != 0);
+        }
+        if (p.info)
+            for (int k = t; k < m; k += THREADS) p.info[member_index(p, N, chunk * MPC + k)] = s_info[k];
+        __syncthreads();
+    }
+}
+
+}  // namespace cholinv

@@ -8,22 +8,24 @@
 
 #include "batched.cuh"
 #include "dispatch.h"
+#include "group.cuh"
 
 namespace cholinv {
 
-// Largest order handled by the one-matrix-per-thread kernels, per element
-// type; larger orders go to the one-matrix-per-warp kernel.  (Beyond these
-// orders the per-thread working set no longer fits the register file.)
-constexpr int kLaneMaxNAll = 16;
-template <typename V>
-constexpr int lane_max_n() {
-    return sizeof(V) == 16 ? 10 : (sizeof(V) == 8 && !traits<V>::cplx) ? 14 : 16;
+// Kernel family per order N:
+//   lane  (one matrix per thread) while the packed triangle fits registers,
+//   group (G threads per matrix) up to order 32 when a G <= 32 fits,
+//   warp  (one matrix per warp, matrix in shared memory) otherwise.
+constexpr int kGroupMaxN = 32;
+template <typename V, int N>
+constexpr int kernel_kind() {  // 0 lane, 1 group, 2 warp
+    return LaneCfg<V, N>::REGS ? 0 : (N <= kGroupMaxN && group_size<V, N>() > 0) ? 1 : 2;
 }
 
 template <typename V, int N>
 static cudaError_t launch_lane(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
-    constexpr int THREADS = lane_threads<V, N>();
-    constexpr size_t SMEM = lane_smem_bytes<V, N>();
+    constexpr int THREADS = LaneCfg<V, N>::THREADS;
+    constexpr size_t SMEM = LaneCfg<V, N>::SMEM;
     static std::once_flag once;
     static int per_sm = 1;
     static cudaError_t setup_err = cudaSuccess;
@@ -63,20 +65,48 @@ static cudaError_t launch_warp(const BatchParams& p, int N, int upper_count, cud
     return cudaGetLastError();
 }
 
+template <typename V, int N, int G>
+static cudaError_t launch_group(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
+    using C = GroupCfg<V, N, G>;
+    static std::once_flag once;
+    static int per_sm = 1;
+    static cudaError_t setup_err = cudaSuccess;
+    std::call_once(once, [&] {
+        setup_err = cudaFuncSetAttribute(k_group<V, N, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (setup_err == cudaSuccess)
+            setup_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group<V, N, G>, C::THREADS, C::SMEM);
+        if (per_sm < 1) per_sm = 1;
+    });
+    if (setup_err != cudaSuccess || dry) return setup_err;
+    const int chunks = (upper_count + C::MPC - 1) / C::MPC;
+    if (chunks <= 0) return cudaSuccess;
+    const int grid = std::min(chunks, device_info().sms * per_sm);
+    k_group<V, N, G><<<grid, C::THREADS, C::SMEM, s>>>(p);
+    return cudaGetLastError();
+}
+
 template <typename V, int N>
-static cudaError_t launch_lane_upto(const BatchParams& p, int cls, int upper_count, cudaStream_t s, bool dry) {
+static cudaError_t launch_fixed(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
+    constexpr int kind = kernel_kind<V, N>();
+    if constexpr (kind == 0) return launch_lane<V, N>(p, upper_count, s, dry);
+    else if constexpr (kind == 1) return launch_group<V, N, group_size<V, N>()>(p, upper_count, s, dry);
+    else return launch_warp<V>(p, N, upper_count, s, dry);
+}
+
+template <typename V, int N>
+static cudaError_t launch_fixed_upto(const BatchParams& p, int cls, int upper_count, cudaStream_t s, bool dry) {
     if constexpr (N == 0) {
         return cudaErrorInvalidValue;
     } else {
-        if (cls == N) return launch_lane<V, N>(p, upper_count, s, dry);
-        return launch_lane_upto<V, N - 1>(p, cls, upper_count, s, dry);
+        if (cls == N) return launch_fixed<V, N>(p, upper_count, s, dry);
+        return launch_fixed_upto<V, N - 1>(p, cls, upper_count, s, dry);
     }
 }
 
 // Launch the kernel of one size class (cls) whose member count is at most upper_count.
 template <typename V>
 cudaError_t launch_class(const BatchParams& p, int cls, int upper_count, cudaStream_t s, bool dry) {
-    if (cls <= lane_max_n<V>()) return launch_lane_upto<V, lane_max_n<V>()>(p, cls, upper_count, s, dry);
+    if (cls <= kGroupMaxN) return launch_fixed_upto<V, kGroupMaxN>(p, cls, upper_count, s, dry);
     return launch_warp<V>(p, cls, upper_count, s, dry);
 }
 
