@@ -1,6 +1,7 @@
 // C-ABI of the cholinv library (declared in include/cholinv.h): host-side
 // argument validation, size-class bucketing, kernel dispatch, plans (CUDA
 // graphs) and the device error word.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -86,14 +87,80 @@ chol_status_t check_ws(int32_t batch, const int32_t* n, void* ws, size_t ws_byte
     return CHOL_OK;
 }
 
-cudaError_t launch_dtype(chol_dtype_t dt, const BatchParams& p, cudaStream_t s, bool dry) {
+cudaError_t launch_dtype_class(chol_dtype_t dt, const BatchParams& p, int cls, int upper, cudaStream_t s, bool dry) {
     switch (dt) {
-        case CHOL_F32: return launch_batched_f32(p, s, dry);
-        case CHOL_F64: return launch_batched_f64(p, s, dry);
-        case CHOL_C64: return launch_batched_c64(p, s, dry);
-        case CHOL_C128: return launch_batched_c128(p, s, dry);
+        case CHOL_F32: return launch_class_f32(p, cls, upper, s, dry);
+        case CHOL_F64: return launch_class_f64(p, cls, upper, s, dry);
+        case CHOL_C64: return launch_class_c64(p, cls, upper, s, dry);
+        case CHOL_C128: return launch_class_c128(p, cls, upper, s, dry);
     }
     return cudaErrorInvalidValue;
+}
+
+// Streams and events (per device) on which the size-class kernels of a batch
+// with per-matrix sizes run side by side: the caller's stream forks to them
+// after the bucketing and joins them before returning, so classes overlap
+// (and a class with no members costs only its launch), in eager calls and in
+// captured graphs alike.  Calls from several host threads serialise on them.
+constexpr int kForkStreams = 8;
+struct ForkPool {
+    bool init = false;
+    cudaStream_t st[kForkStreams];
+    cudaEvent_t fork;
+    cudaEvent_t join[kForkStreams];
+    std::mutex mu;
+};
+ForkPool g_fork[kMaxDevices];
+
+cudaError_t fork_pool(ForkPool** out) {
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return e;
+    if (d < 0 || d >= kMaxDevices) return cudaErrorInvalidDevice;
+    ForkPool& f = g_fork[d];
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (!f.init) {
+        for (int i = 0; i < kForkStreams; ++i) {
+            if ((e = cudaStreamCreateWithFlags(&f.st[i], cudaStreamNonBlocking)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&f.join[i], cudaEventDisableTiming)) != cudaSuccess) return e;
+        }
+        if ((e = cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+        f.init = true;
+    }
+    *out = &f;
+    return cudaSuccess;
+}
+
+cudaError_t launch_dtype(chol_dtype_t dt, const BatchParams& p, cudaStream_t s, bool dry) {
+    if (p.cls_count == nullptr) return launch_dtype_class(dt, p, p.max_n, p.batch, s, dry);
+    if (dry) {
+        ForkPool* fp0 = nullptr;
+        cudaError_t e0 = fork_pool(&fp0);  // create the streams outside any capture
+        if (e0 != cudaSuccess) return e0;
+        for (int c = p.max_n; c >= 1; --c) {
+            cudaError_t e = launch_dtype_class(dt, p, c, p.batch, s, true);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    ForkPool* fp = nullptr;
+    cudaError_t e = fork_pool(&fp);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(fp->mu);
+    if ((e = cudaEventRecord(fp->fork, s)) != cudaSuccess) return e;
+    const int used = std::min(kForkStreams, (int)p.max_n);
+    for (int i = 0; i < used; ++i)
+        if ((e = cudaStreamWaitEvent(fp->st[i], fp->fork, 0)) != cudaSuccess) return e;
+    // largest orders first: they take longest
+    for (int c = p.max_n, k = 0; c >= 1; --c, ++k) {
+        e = launch_dtype_class(dt, p, c, p.batch, fp->st[k % used], false);
+        if (e != cudaSuccess) return e;
+    }
+    for (int i = 0; i < used; ++i) {
+        if ((e = cudaEventRecord(fp->join[i], fp->st[i])) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, fp->join[i], 0)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Enqueue bucketing (if per-matrix sizes) and every class kernel.

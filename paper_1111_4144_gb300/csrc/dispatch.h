@@ -12,9 +12,12 @@ struct DeviceInfo {
 };
 DeviceInfo device_info();  // defined in api.cu
 
-cudaError_t launch_batched_f32(const BatchParams& p, cudaStream_t s, bool dry);
-cudaError_t launch_batched_f64(const BatchParams& p, cudaStream_t s, bool dry);
-cudaError_t launch_batched_c64(const BatchParams& p, cudaStream_t s, bool dry);
-cudaError_t launch_batched_c128(const BatchParams& p, cudaStream_t s, bool dry);
+// Launch the kernel of size class `cls` (matrices of order cls; at most
+// `upper` of them) on stream s.  dry = true only performs the kernel's
+// one-time set-up (before a stream capture) and launches nothing.
+cudaError_t launch_class_f32(const BatchParams& p, int cls, int upper, cudaStream_t s, bool dry);
+cudaError_t launch_class_f64(const BatchParams& p, int cls, int upper, cudaStream_t s, bool dry);
+cudaError_t launch_class_c64(const BatchParams& p, int cls, int upper, cudaStream_t s, bool dry);
+cudaError_t launch_class_c128(const BatchParams& p, int cls, int upper, cudaStream_t s, bool dry);
 
 }  // namespace cholinv

@@ -120,21 +120,55 @@ CHOL_D void group_store(const BatchParams& p, V* out, const unsigned char* mir, 
 // element (r, j) sits at row_base(r) + j.
 CHOL_HD constexpr int row_base(int n, int r) { return r * n - (r * (r - 1)) / 2 - r; }
 
-// Threads per matrix for order N: the smallest power of two (2..32) whose
-// per-thread share of the columns fits in about 112 32-bit registers; 0 if
-// none does (the one-matrix-per-warp kernel takes those orders).
+// Row r of the packed mirror, columns r..N-1, into out[r..N-1], using 16-byte
+// loads wherever a whole aligned unit lies inside the row.
+template <typename V, int N>
+CHOL_D void load_row(const V* M, int r, V (&out)[N]) {
+    constexpr int U = 16 / (int)sizeof(V);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        if (k >= r) {
+            const int e = row_base(N, r) + k;
+            // a unit may run past the row's end into the next row (or the
+            // mirror's padding); those extra elements are not used
+            const bool unit_start = (e % U) == 0;
+            const bool in_unit = (e % U) != 0 && k - (e % U) >= r;  // covered by an earlier unit load
+            if (unit_start) {
+                const uint4 w = *reinterpret_cast<const uint4*>(M + e);
+#pragma unroll
+                for (int z = 0; z < U; ++z)
+                    if (k + z < N) out[k + z] = reinterpret_cast<const V*>(&w)[z];
+            } else if (!in_unit) {
+                out[k] = M[e];
+            }
+        }
+    }
+}
+
+// Threads per matrix for order N (ALG 1): the smallest power of two
+// (2..32) whose share of the columns' upper parts fits in about 150 32-bit
+// registers; 0 if none does (the one-matrix-per-warp kernel takes those).
+// Fewer threads per matrix measured faster (less repeated mirror traffic)
+// even at lower occupancy: for 16 x 16 complex64, G = 2 / 4 / 8 / 16 took
+// 276 / 345 / 493 / 700 us per 349,525 matrices on one GB300.
 template <typename V, int N>
 constexpr int group_size() {
     for (int g = 2; g <= 32; g *= 2) {
         int words = 0;
         const int nc = (N + g - 1) / g;
         for (int c = 0; c < nc; ++c) words += (c * g + g < N ? c * g + g : N) * traits<V>::words;
-        if (words <= 112) return g;
+        if (words <= 150) return g;
     }
     return 0;
 }
 
-template <typename V, int N, int G>
+// ALG 1: left-looking Eq. 4 (column i of R read from the mirror at row i);
+//        inverse terms with k > j read row j of X from the mirror.
+// ALG 2: the same sums taken right-looking (row k of R broadcast from the
+//        mirror, each entry still receives its terms in ascending k); in the
+//        inverse every thread keeps its columns in full (the lower half
+//        mirrored in once per row), so the dot products run on registers.
+template <typename V, int N, int G, int ALG>
 __global__ void __launch_bounds__(GroupCfg<V, N, G>::THREADS)
 k_group(BatchParams p) {
     using C = GroupCfg<V, N, G>;
@@ -184,6 +218,7 @@ k_group(BatchParams p) {
         cp_async_wait<0>();
         __syncthreads();
 
+        if constexpr (ALG == 1) {
         const bool live = q < m;
         V* M = reinterpret_cast<V*>(mirs + (size_t)(live ? q : 0) * C::STRIDE);
         // own columns, upper parts, into registers
@@ -306,6 +341,131 @@ k_group(BatchParams p) {
             }
             __syncthreads();
             group_store<V, N, G>(p, Xo, mirs, s_off, s_info, s_i, s_j, m, vec, false, p.fill_lower != 0);
+        }
+        } else {
+        const bool live = q < m;
+        V* M = reinterpret_cast<V*>(mirs + (size_t)(live ? q : 0) * C::STRIDE);
+        // Own columns in registers.  col[c][r] holds row r of column j = c*G + h:
+        // rows r <= j first hold A, then R, then X (each in place); rows r > j
+        // receive the mirrored lower half of X, conj(x_jr), once row j of X is done.
+        V col[NC][N];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int j = c * G + h;
+            const int jj = min(j, N - 1);
+#pragma unroll
+            for (int r = 0; r < N; ++r) {
+                if (r <= c * G + G - 1) {
+                    const V v = M[row_base(N, r) + jj];
+                    col[c][r] = (r <= j && j < N) ? v : zero_v<V>();
+                }
+            }
+        }
+        int info = 0;
+        // ---------------- factor, Eqs. 3-4.  Entry (i, j) receives its terms
+        // conj(r_ki) r_kj in the order k = 0, 1, ..., i-1 (one per step k, as
+        // in Eq. 4's sum), then the scaling by 1/r_ii at step i.
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const int co = k / G, ho = k % G;
+            const R tt = __shfl_sync(0xffffffffu, re_of(col[co][k]), gbase + ho);  // Eq. 3 argument
+            if (info == 0 && !pivot_ok(tt)) info = k + 1;
+            const R rii = sqrt(tt);
+            const R inv = R(1) / rii;
+            // row k of R in the owned columns (Eq. 4's division), into the mirror
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                if (k <= c * G + G - 1) {
+                    const int j = c * G + h;
+                    if (j >= k && j < N) {
+                        const V r = (j == k) ? from_real<V>(rii) : scale_v(col[c][k], inv);
+                        col[c][k] = r;
+                        if (live) M[row_base(N, k) + j] = r;
+                    }
+                }
+            }
+            __syncwarp();
+            if (k + 1 < N) {
+                // row k of R (columns > k) for the updates of rows k+1..j
+                V rk[N];
+                load_row<V, N>(M, k, rk);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int j = c * G + h;
+#pragma unroll
+                    for (int i = 0; i < N; ++i) {
+                        if (i > k && i <= c * G + G - 1) {
+                            const V u = fnma_conj(rk[i], col[c][k], col[c][i]);
+                            if (i <= c * G) col[c][i] = u;          // i <= j for every h
+                            else col[c][i] = (i <= j) ? u : col[c][i];
+                        }
+                    }
+                }
+            }
+        }
+        if (live && h == 0) s_info[q] = info;
+        if (store_R || !p.want_inv) {
+            __syncthreads();
+            group_store<V, N, G>(p, Ro, mirs, s_off, s_info, s_i, s_j, m, vec, true, false);
+            __syncthreads();
+        }
+        if (p.want_inv) {
+            // ---------------- proposed inverse, Sec. IV.A, rows N..1.  At step i
+            // every row k > i of an owned column already holds x~_kj, so
+            //   x_ij = -(1/r_ii) sum_{k>i} r_ik col[c][k]
+            // is a dot product of row i of R (from the mirror) with registers.
+#pragma unroll
+            for (int i = N - 1; i >= 0; --i) {
+                V rr[N];  // row i of R, columns i..N-1
+                load_row<V, N>(M, i, rr);
+                const R inv = R(1) / re_of(rr[i]);
+                V xs[NC];
+                R sd = R(0);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    if (c * G + G - 1 > i) {
+                        const int j = c * G + h;
+                        V acc = zero_v<V>();
+#pragma unroll
+                        for (int k = 0; k < N; ++k)
+                            if (k > i) acc = fma_v(rr[k], col[c][k], acc);
+                        xs[c] = scale_v(acc, -inv);
+                        if (j > i && j < N) sd = fma_re_conjb(col[c][i], xs[c], sd);
+                    }
+                }
+                __syncwarp();  // row i of R has been read; it may be overwritten
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    if (c * G + G - 1 > i) {
+                        const int j = c * G + h;
+                        if (j > i && j < N) {
+                            col[c][i] = xs[c];
+                            if (live) M[row_base(N, i) + j] = xs[c];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int d = G / 2; d > 0; d >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, d);
+                const V xd = from_real<V>((inv - sd) * inv);
+                const int co = i / G, ho = i % G;
+                if (h == ho) {
+                    col[co][i] = xd;
+                    if (live) M[row_base(N, i) + i] = xd;
+                }
+                __syncwarp();
+                if (i > 0) {
+                    // row i of X is complete: its owner mirrors it into the
+                    // lower half of column i (rows k > i hold conj(x_ik))
+                    V xr[N];
+                    load_row<V, N>(M, i, xr);
+#pragma unroll
+                    for (int k = 0; k < N; ++k)
+                        if (k > i) col[co][k] = (h == ho) ? conj_v(xr[k]) : col[co][k];
+                }
+            }
+            __syncthreads();
+            group_store<V, N, G>(p, Xo, mirs, s_off, s_info, s_i, s_j, m, vec, false, p.fill_lower != 0);
+        }
         }
         if (p.info)
             for (int k = t; k < m; k += THREADS) p.info[member_index(p, N, chunk * MPC + k)] = s_info[k];

@@ -3,8 +3,8 @@
 
 namespace cholinv {
 
-cudaError_t launch_batched_c64(const BatchParams& p, cudaStream_t s, bool dry) {
-    return launch_batched<cpx<float>>(p, s, dry);
+cudaError_t launch_class_c64(const BatchParams& p, int cls, int upper, cudaStream_t s, bool dry) {
+    return launch_class<cpx<float>>(p, cls, upper, s, dry);
 }
 
 }  // namespace cholinv

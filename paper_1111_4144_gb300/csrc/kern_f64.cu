@@ -3,8 +3,8 @@
 
 namespace cholinv {
 
-cudaError_t launch_batched_f64(const BatchParams& p, cudaStream_t s, bool dry) {
-    return launch_batched<double>(p, s, dry);
+cudaError_t launch_class_f64(const BatchParams& p, int cls, int upper, cudaStream_t s, bool dry) {
+    return launch_class<double>(p, cls, upper, s, dry);
 }
 
 }  // namespace cholinv

@@ -65,23 +65,23 @@ static cudaError_t launch_warp(const BatchParams& p, int N, int upper_count, cud
     return cudaGetLastError();
 }
 
-template <typename V, int N, int G>
+template <typename V, int N, int G, int ALG>
 static cudaError_t launch_group(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
     using C = GroupCfg<V, N, G>;
     static std::once_flag once;
     static int per_sm = 1;
     static cudaError_t setup_err = cudaSuccess;
     std::call_once(once, [&] {
-        setup_err = cudaFuncSetAttribute(k_group<V, N, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        setup_err = cudaFuncSetAttribute(k_group<V, N, G, ALG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (setup_err == cudaSuccess)
-            setup_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group<V, N, G>, C::THREADS, C::SMEM);
+            setup_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group<V, N, G, ALG>, C::THREADS, C::SMEM);
         if (per_sm < 1) per_sm = 1;
     });
     if (setup_err != cudaSuccess || dry) return setup_err;
     const int chunks = (upper_count + C::MPC - 1) / C::MPC;
     if (chunks <= 0) return cudaSuccess;
     const int grid = std::min(chunks, device_info().sms * per_sm);
-    k_group<V, N, G><<<grid, C::THREADS, C::SMEM, s>>>(p);
+    k_group<V, N, G, ALG><<<grid, C::THREADS, C::SMEM, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -89,7 +89,7 @@ template <typename V, int N>
 static cudaError_t launch_fixed(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
     constexpr int kind = kernel_kind<V, N>();
     if constexpr (kind == 0) return launch_lane<V, N>(p, upper_count, s, dry);
-    else if constexpr (kind == 1) return launch_group<V, N, group_size<V, N>()>(p, upper_count, s, dry);
+    else if constexpr (kind == 1) return launch_group<V, N, group_size<V, N>(), 1>(p, upper_count, s, dry);
     else return launch_warp<V>(p, N, upper_count, s, dry);
 }
 
@@ -108,20 +108,6 @@ template <typename V>
 cudaError_t launch_class(const BatchParams& p, int cls, int upper_count, cudaStream_t s, bool dry) {
     if (cls <= kGroupMaxN) return launch_fixed_upto<V, kGroupMaxN>(p, cls, upper_count, s, dry);
     return launch_warp<V>(p, cls, upper_count, s, dry);
-}
-
-// Every size class of a batch: one class for uniform batches, otherwise
-// every class 1..max_n (a class kernel with no members exits at once).
-// dry = true only performs the one-time per-kernel set-up (used before a
-// stream capture) and launches nothing.
-template <typename V>
-cudaError_t launch_batched(const BatchParams& p, cudaStream_t s, bool dry) {
-    if (p.cls_count == nullptr) return launch_class<V>(p, p.max_n, p.batch, s, dry);
-    for (int c = p.max_n; c >= 1; --c) {
-        cudaError_t e = launch_class<V>(p, c, p.batch, s, dry);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
 }
 
 }  // namespace cholinv
