@@ -93,7 +93,9 @@ typedef enum {
 } chol_prec_t;
 
 /* opts->flags */
-#define CHOL_FLAG_PIVOT64 0x1   /* F32/C64: accumulate Eq. 3 (the pivot) in FP64 and take its sqrt in FP64 */
+#define CHOL_FLAG_PIVOT64 0x1     /* F32/C64: accumulate Eq. 3 (the pivot) in FP64 and take its sqrt in FP64 */
+#define CHOL_FLAG_GRAD_UPPER 0x2  /* chol_inv_backward: gradient with respect to the upper triangle taken as
+                                     the independent parameters (see chol_inv_backward) */
 
 typedef struct {
     int32_t prec;          /* chol_prec_t */
@@ -122,12 +124,15 @@ chol_status_t chol_factor_batched(chol_dtype_t dt, int32_t batch, const int32_t*
  * (Sec. II Eqs. 3-4 fused with Sec. IV.A Eqs. 20-24): the factor stays on
  * chip and the recurrence for X runs on it directly.
  *   A: input; R: optional output of the factor (NULL = not written);
- *   X: output.  With opts->prec = CHOL_PREC_FP32_REFINE the result is
- *   refined (refine_steps Newton-Schulz steps, residual I - A X accumulated
- *   in FP64); refine_steps = -1 applies one step to the matrices whose
- *   pivots show cancellation (min_i t_i / a_ii < 2^-12, t_i the argument of
- *   Eq. 3) and none to the rest.  Refinement needs A intact, so X == A is
- *   rejected (CHOL_ERR_ARG) when any step may run.
+ *   X: output.  With opts->prec = CHOL_PREC_FP32_REFINE (F32 / C64) the
+ *   result is refined by refine_steps Newton-Schulz steps
+ *   X <- X + X (I - A X), the residual accumulated in FP64 from exact
+ *   products of the FP32 operands.  refine_steps = -1 (automatic) refines a
+ *   matrix once when gamma = max_i a_ii x_ii > 4096; gamma lies in
+ *   [1, kappa_2(A)], so well-conditioned matrices are left as they are.
+ *   Refinement reads A again after X is formed, so X == A is rejected
+ *   (CHOL_ERR_ARG) when refine_steps != 0.  CHOL_FLAG_PIVOT64 accumulates
+ *   the sum of Eq. 3 in FP64 for F32 / C64 (pivots lost to cancellation).
  */
 chol_status_t chol_inv_batched(chol_dtype_t dt, int32_t batch, const int32_t* n, const int64_t* off,
                                int32_t max_n, const void* A, void* R, void* X, int32_t* info,
@@ -137,12 +142,18 @@ chol_status_t chol_inv_batched(chol_dtype_t dt, int32_t batch, const int32_t* n,
  * chol_inv_backward — adjoint of X = A^{-1} on Hermitian matrices:
  *   dA = -X S X,  S = (G + G^H) / 2
  * (not in the paper; it reuses the forward X and does no refactorisation).
- *   X: the forward result in the given layout (upper half is read; the
- *   lower half is taken as its conjugate mirror).  G: dense n*n gradient of
- *   the loss with respect to the full X.  dA: dense n*n output (full
- *   Hermitian).  G and dA always use the dense layout and the element
- *   offsets off[b] of a dense batch (off == NULL: b * max_n^2); X uses
- *   opts->layout with its own offsets: pass xoff (NULL = contiguous).
+ * For every Hermitian perturbation E, dL = Re<dA, E>_F: dA is the gradient
+ * on the Hermitian subspace, itself Hermitian.
+ *   X: the forward result in opts->layout, at element offsets xoff[b]
+ *   (NULL = contiguous); its upper half is read, the lower half is taken as
+ *   the conjugate mirror.  G: dense n*n gradient of the loss with respect
+ *   to the full X.  dA: dense n*n output.  G and dA use the element offsets
+ *   off[b] of a dense batch (off == NULL: b * max_n^2).
+ *   With CHOL_FLAG_GRAD_UPPER, dA is instead the gradient with respect to
+ *   the entries the forward call reads (the upper triangle, diagonal real
+ *   part): 2 dA_ij above the diagonal, Re(dA_ii) on it, 0 below.  This is
+ *   what an autograd system that perturbs entries one at a time expects.
+ *   dA may not alias X or G.
  */
 chol_status_t chol_inv_backward(chol_dtype_t dt, int32_t batch, const int32_t* n, const int64_t* off,
                                 const int64_t* xoff, int32_t max_n, const void* X, const void* G, void* dA,

@@ -24,6 +24,7 @@ CHOL_F32, CHOL_F64, CHOL_C64, CHOL_C128 = 0, 1, 2, 3
 CHOL_OK, CHOL_ERR_ARG, CHOL_ERR_CUDA, CHOL_ERR_UNSUPPORTED, CHOL_ERR_TIMEOUT, CHOL_ERR_WORKSPACE = 0, -1, -2, -3, -4, -5
 CHOL_PREC_NATIVE, CHOL_PREC_FP32_REFINE, CHOL_PREC_TF32_REFINE, CHOL_PREC_BF16_REFINE = 0, 1, 2, 3
 CHOL_FLAG_PIVOT64 = 0x1
+CHOL_FLAG_GRAD_UPPER = 0x2
 CHOL_CALL_FACTOR, CHOL_CALL_INV, CHOL_CALL_BACKWARD = 0, 1, 2
 CHOL_NOALLOC_MAX_BATCH = 1048576
 

@@ -113,6 +113,59 @@ def factor(A, n=None, off=None, max_n=None, *, layout=LAYOUT_DENSE, flags=0, R=N
     return R, info
 
 
+def backward(X, G, n=None, off=None, xoff=None, max_n=None, *, layout=LAYOUT_DENSE, upper_param=False, dA=None,
+             stream=None):
+    """dA = -X (G + G^H)/2 X for every matrix (chol_inv_backward).
+
+    X: forward result (upper half read) in `layout`; G: dense gradient with
+    respect to the full X.  Dense (batch, N, N) tensors need no sizes.
+    upper_param: return the gradient with respect to the upper triangle
+    (the entries the forward call reads) instead of the Hermitian gradient.
+    """
+    _need_cuda(X, G, dA)
+    dt = dtype_code(X)
+    if G.dtype != X.dtype:
+        raise ValueError("X and G must have the same dtype")
+    batch, max_n = _geometry(G, n, off, max_n, LAYOUT_DENSE)
+    if dA is None:
+        dA = torch.empty_like(G)
+    flags = L.CHOL_FLAG_GRAD_UPPER if upper_param else 0
+    o = L.opts(L.CHOL_PREC_NATIVE, 0, 0, layout, flags)
+    st = L.chol_inv_backward(dt, batch, _p(n), _p(off), _p(xoff), max_n, _p(X), _p(G), _p(dA), o, None, 0,
+                             _s(stream))
+    L.check(st, "chol_inv_backward")
+    return dA
+
+
+class CholInv(torch.autograd.Function):
+    """X = A^{-1} for a dense batch (batch, N, N) of Hermitian positive-definite
+    matrices, differentiable.  The forward pass reads the upper triangle of A
+    (Sec. II) and returns the full Hermitian X; the backward pass runs the
+    adjoint kernel on the saved X (no refactorisation) and returns the
+    gradient with respect to the entries the forward pass read."""
+
+    @staticmethod
+    def forward(ctx, A, prec=L.CHOL_PREC_NATIVE, refine_steps=0):
+        if A.dim() != 3:
+            raise ValueError("CholInv expects a (batch, N, N) tensor")
+        A = A.contiguous()
+        X, info = inv(A, layout=LAYOUT_DENSE, fill_lower=True, prec=prec, refine_steps=refine_steps)
+        ctx.save_for_backward(X)
+        ctx.mark_non_differentiable(info)
+        return X, info
+
+    @staticmethod
+    def backward(ctx, gX, ginfo=None):
+        (X,) = ctx.saved_tensors
+        dA = backward(X, gX.contiguous(), upper_param=True)
+        return dA, None, None
+
+
+def inv_autograd(A, prec=L.CHOL_PREC_NATIVE, refine_steps=0):
+    """Differentiable full inverse of a dense batch; returns (X, info)."""
+    return CholInv.apply(A, prec, refine_steps)
+
+
 def last_device_error(stream=None) -> int:
     return L.chol_last_device_error(_s(stream))
 

@@ -72,7 +72,7 @@ chol_status_t check_common(chol_dtype_t dt, int32_t batch, int32_t max_n, const 
     if (o.layout != 0 && o.layout != 1) return CHOL_ERR_ARG;
     if (o.prec < CHOL_PREC_NATIVE || o.prec > CHOL_PREC_BF16_REFINE) return CHOL_ERR_ARG;
     if (o.refine_steps < -1 || o.refine_steps > 2) return CHOL_ERR_ARG;
-    if (o.flags & ~CHOL_FLAG_PIVOT64) return CHOL_ERR_ARG;
+    if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER)) return CHOL_ERR_ARG;
     if (max_n > kBatchedMaxN) return CHOL_ERR_UNSUPPORTED;
     if (o.prec == CHOL_PREC_TF32_REFINE || o.prec == CHOL_PREC_BF16_REFINE) return CHOL_ERR_UNSUPPORTED;
     if (o.prec == CHOL_PREC_FP32_REFINE && !is_fp32(dt)) return CHOL_ERR_UNSUPPORTED;
@@ -197,8 +197,23 @@ chol_status_t inv_validate(chol_dtype_t dt, int32_t batch, const int32_t* n, int
     if (st != CHOL_OK) return st;
     if (batch == 0) return CHOL_OK;
     if (A == nullptr || X == nullptr) return CHOL_ERR_ARG;
-    if (o.prec == CHOL_PREC_FP32_REFINE && o.refine_steps != 0) return CHOL_ERR_UNSUPPORTED;
+    if (o.prec == CHOL_PREC_FP32_REFINE && o.refine_steps != 0 && X == A) return CHOL_ERR_ARG;
     return check_ws(batch, n, ws, ws_bytes);
+}
+
+// The inverse with its optional refinement pass.
+chol_status_t enqueue_inv(chol_dtype_t dt, BatchParams p, void* ws, cudaStream_t s, bool dry, const chol_opts_t& o) {
+    chol_status_t st = enqueue_batched(dt, p, ws, s, dry);
+    if (st != CHOL_OK) return st;
+    if (o.prec == CHOL_PREC_FP32_REFINE && o.refine_steps != 0) {
+        BatchParams q = p;
+        DevState* ds = nullptr;
+        if (dev_state(&ds) != cudaSuccess) return CHOL_ERR_CUDA;
+        q.err = ds->err;
+        const int steps = o.refine_steps > 0 ? o.refine_steps : 1;
+        if (launch_refine(dt, q, steps, o.refine_steps < 0, s, dry) != cudaSuccess) return CHOL_ERR_CUDA;
+    }
+    return CHOL_OK;
 }
 
 BatchParams make_params(int32_t batch, const int32_t* n, const int64_t* off, int32_t max_n, const void* A,
@@ -216,6 +231,7 @@ BatchParams make_params(int32_t batch, const int32_t* n, const int64_t* off, int
     p.R = R;
     p.X = X;
     p.info = info;
+    p.flags = o.flags;
     return p;
 }
 
@@ -261,15 +277,32 @@ chol_status_t chol_inv_batched(chol_dtype_t dt, int32_t batch, const int32_t* n,
     chol_status_t st = inv_validate(dt, batch, n, max_n, A, X, o, ws, ws_bytes);
     if (st != CHOL_OK || batch == 0) return st;
     BatchParams p = make_params(batch, n, off, max_n, A, (R == X) ? nullptr : R, X, info, o, 1);
-    return enqueue_batched(dt, p, ws, static_cast<cudaStream_t>(stream), false);
+    return enqueue_inv(dt, p, ws, static_cast<cudaStream_t>(stream), false, o);
 }
 
 chol_status_t chol_inv_backward(chol_dtype_t dt, int32_t batch, const int32_t* n, const int64_t* off,
                                 const int64_t* xoff, int32_t max_n, const void* X, const void* G, void* dA,
                                 const chol_opts_t* opts, void* ws, size_t ws_bytes, void* stream) {
-    (void)dt; (void)batch; (void)n; (void)off; (void)xoff; (void)max_n; (void)X; (void)G; (void)dA;
-    (void)opts; (void)ws; (void)ws_bytes; (void)stream;
-    return CHOL_ERR_UNSUPPORTED;
+    (void)ws; (void)ws_bytes;
+    const chol_opts_t o = opts_or_default(opts);
+    chol_status_t st = check_common(dt, batch, max_n, o);
+    if (st != CHOL_OK || batch == 0) return st;
+    if (X == nullptr || G == nullptr || dA == nullptr) return CHOL_ERR_ARG;
+    if (dA == X || dA == G) return CHOL_ERR_ARG;
+    BwdParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.batch = batch;
+    p.n = n;
+    p.off = off;
+    p.xoff = xoff;
+    p.max_n = max_n;
+    p.layout = o.layout;
+    p.X = X;
+    p.G = G;
+    p.dA = dA;
+    p.flags = o.flags;
+    if (launch_backward(dt, p, static_cast<cudaStream_t>(stream), false) != cudaSuccess) return CHOL_ERR_CUDA;
+    return CHOL_OK;
 }
 
 size_t chol_workspace_bytes(int32_t call, chol_dtype_t dt, int32_t batch, int32_t max_n, int32_t has_sizes,
@@ -368,14 +401,14 @@ chol_status_t chol_plan_inv_create(chol_plan_t** plan, chol_dtype_t dt, int32_t 
     if (st != CHOL_OK) return st;
     BatchParams p = make_params(batch, n, off, max_n, A, (R == X) ? nullptr : R, X, info, o, 1);
     // one-time kernel set-up outside the capture
-    st = enqueue_batched(dt, p, ws, nullptr, true);
+    st = enqueue_inv(dt, p, ws, nullptr, true, o);
     if (st != CHOL_OK) return st;
     cudaStream_t cs = nullptr;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return CHOL_ERR_CUDA;
     chol_plan* pl = new chol_plan();
     st = CHOL_OK;
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = CHOL_ERR_CUDA;
-    if (st == CHOL_OK && batch > 0) st = enqueue_batched(dt, p, ws, cs, false);
+    if (st == CHOL_OK && batch > 0) st = enqueue_inv(dt, p, ws, cs, false, o);
     cudaGraph_t g = nullptr;
     if (cudaStreamEndCapture(cs, &g) != cudaSuccess && st == CHOL_OK) st = CHOL_ERR_CUDA;
     pl->graph = g;

@@ -33,7 +33,31 @@ struct BatchParams {
     const int32_t* cls_start;  // per-class start in perm
     const int32_t* perm;       // matrix indices sorted by class
     int* err;                  // device error word
+    int32_t flags;             // CHOL_FLAG_*
 };
+
+// Arguments of the adjoint kernel.
+struct BwdParams {
+    int32_t batch;
+    const int32_t* n;          // per-matrix order (NULL: uniform max_n)
+    const int64_t* off;        // element offsets of G and dA (dense layout)
+    const int64_t* xoff;       // element offsets of X (its own layout)
+    int32_t max_n;
+    int32_t layout;            // layout of X
+    const void* X;
+    const void* G;
+    void* dA;
+    int32_t flags;             // CHOL_FLAG_GRAD_UPPER selects the upper-parameter form
+};
+
+// Eq. 3's argument with its sum accumulated in FP64 (the sum of |r_ki|^2 over
+// FP32 values is formed from exact FP64 products); used for FP32 value types
+// under CHOL_FLAG_PIVOT64 to avoid losing the pivot to cancellation.
+template <typename V>
+CHOL_D double pivot64_term(V v) {
+    if constexpr (traits<V>::cplx) return (double)v.re * (double)v.re + (double)v.im * (double)v.im;
+    else return (double)v * (double)v;
+}
 
 // Matrix index of the k-th member of class N, and its element offset.
 CHOL_D int64_t member_index(const BatchParams& p, int N, int k) {
@@ -56,7 +80,7 @@ CHOL_D int class_count(const BatchParams& p, int N) {
 // bounds that depend on an outer index the front end leaves a register array
 // in local memory.)
 template <typename V, int N, class Acc>
-CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 1]) {
+CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 1], bool pivot64 = false) {
     using R = typename traits<V>::real;
     int info = 0;
 #pragma unroll
@@ -67,12 +91,24 @@ CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 
             if (k < i) col[k] = m.at(pidx(N, k, i));
         // Eq. 3
         R t = re_of(m.at(pidx(N, i, i)));
+        R rii, inv;
+        if (sizeof(R) == 4 && pivot64) {
+            double td = (double)t;
 #pragma unroll
-        for (int k = 0; k < N; ++k)
-            if (k < i) t = fnma_abs2(col[k], t);
-        if (info == 0 && !pivot_ok(t)) info = i + 1;
-        R rii = sqrt(t);
-        R inv = R(1) / rii;
+            for (int k = 0; k < N; ++k)
+                if (k < i) td -= pivot64_term(col[k]);
+            t = (R)td;
+            rii = (R)sqrt(td);
+            inv = (R)(1.0 / sqrt(td));
+            if (info == 0 && !pivot_ok(td)) info = i + 1;
+        } else {
+#pragma unroll
+            for (int k = 0; k < N; ++k)
+                if (k < i) t = fnma_abs2(col[k], t);
+            if (info == 0 && !pivot_ok(t)) info = i + 1;
+            rii = sqrt(t);
+            inv = R(1) / rii;
+        }
         dinv[i] = inv;
         m.at(pidx(N, i, i)) = from_real<V>(rii);
         // Eq. 4
@@ -350,7 +386,7 @@ k_lane(BatchParams p) {
             int info = 0;
             R dinv[N];
             if (t < m) {
-                info = factor_unrolled<V, N>(r, dinv);
+                info = factor_unrolled<V, N>(r, dinv, p.flags & CHOL_FLAG_PIVOT64);
                 if (store_R) {
 #pragma unroll
                     for (int e = 0; e < TN; ++e) {
@@ -392,7 +428,7 @@ k_lane(BatchParams p) {
             int info = 0;
             R dinv[N];
             SmemMat<V, N> sm{buf, t};
-            if (t < m) info = factor_unrolled<V, N>(sm, dinv);
+            if (t < m) info = factor_unrolled<V, N>(sm, dinv, p.flags & CHOL_FLAG_PIVOT64);
             if (t < m) s_info[t] = info;
             if (store_R) {
                 __syncthreads();
@@ -460,9 +496,18 @@ __global__ void k_warp(BatchParams p, int N, int warps_per_cta) {
             // pivot: column i lives in lane i & 31, slot i >> 5
             R tsrc = re_of((i < 32) ? s0 : s1);
             R tt = __shfl_sync(0xffffffffu, tsrc, i & 31);
-            if (info == 0 && !pivot_ok(tt)) info = i + 1;
-            const R rii = sqrt(tt);
-            const R inv = R(1) / rii;
+            R rii, inv;
+            if (sizeof(R) == 4 && (p.flags & CHOL_FLAG_PIVOT64)) {
+                double td = (double)re_of(S[i * LD + i]);
+                for (int k = 0; k < i; ++k) td -= pivot64_term(S[k * LD + i]);
+                if (info == 0 && !pivot_ok(td)) info = i + 1;
+                rii = (R)sqrt(td);
+                inv = (R)(1.0 / sqrt(td));
+            } else {
+                if (info == 0 && !pivot_ok(tt)) info = i + 1;
+                rii = sqrt(tt);
+                inv = R(1) / rii;
+            }
             if (j0 > i && j0 < N) S[i * LD + j0] = scale_v(s0, inv);
             if (j1 > i && j1 < N) S[i * LD + j1] = scale_v(s1, inv);
             if (lane == (i & 31)) S[i * LD + i] = from_real<V>(rii);

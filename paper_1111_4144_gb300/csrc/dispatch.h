@@ -6,6 +6,7 @@
 namespace cholinv {
 
 struct BatchParams;
+struct BwdParams;
 
 struct DeviceInfo {
     int sms = 0;
@@ -19,5 +20,12 @@ cudaError_t launch_class_f32(const BatchParams& p, int cls, int upper, cudaStrea
 cudaError_t launch_class_f64(const BatchParams& p, int cls, int upper, cudaStream_t s, bool dry);
 cudaError_t launch_class_c64(const BatchParams& p, int cls, int upper, cudaStream_t s, bool dry);
 cudaError_t launch_class_c128(const BatchParams& p, int cls, int upper, cudaStream_t s, bool dry);
+
+// Refinement pass (refine.cu): FP32 / complex64 only.  steps Newton-Schulz
+// steps on every matrix, or (automatic) one step where max_i a_ii x_ii > 4096.
+cudaError_t launch_refine(int dtype, const BatchParams& p, int steps, int automatic, cudaStream_t s, bool dry);
+
+// Adjoint dA = -X (G + G^H)/2 X (adjoint.cu).
+cudaError_t launch_backward(int dtype, const BwdParams& p, cudaStream_t s, bool dry);
 
 }  // namespace cholinv

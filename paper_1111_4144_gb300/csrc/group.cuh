@@ -164,7 +164,8 @@ constexpr int group_size() {
 
 // ALG 1: left-looking Eq. 4 (column i of R read from the mirror at row i);
 //        inverse terms with k > j read row j of X from the mirror.
-// ALG 2: the same sums taken right-looking (row k of R broadcast from the
+// ALG 2 (an alternative kept for tuning; it ignores CHOL_FLAG_PIVOT64 and
+//        is not dispatched by default): the same sums taken right-looking (row k of R broadcast from the
 //        mirror, each entry still receives its terms in ascending k); in the
 //        inverse every thread keeps its columns in full (the lower half
 //        mirrored in once per row), so the dot products run on registers.
@@ -258,9 +259,21 @@ k_group(BatchParams p) {
             const int co = i / G, ho = i % G;
             const R tc = re_of(sv[co]);
             const R tt = __shfl_sync(0xffffffffu, tc, gbase + ho);
-            if (info == 0 && !pivot_ok(tt)) info = i + 1;
-            const R rii = sqrt(tt);
-            const R inv = R(1) / rii;
+            R rii, inv;
+            if (sizeof(R) == 4 && (p.flags & CHOL_FLAG_PIVOT64)) {
+                // Eq. 3 in FP64: a_ii (still in the mirror) minus |r_ki|^2 over column i
+                double td = (double)re_of(M[row_base(N, i) + i]);
+#pragma unroll
+                for (int k = 0; k < N; ++k)
+                    if (k < i) td -= pivot64_term(ci[k]);
+                if (info == 0 && !pivot_ok(td)) info = i + 1;
+                rii = (R)sqrt(td);
+                inv = (R)(1.0 / sqrt(td));
+            } else {
+                if (info == 0 && !pivot_ok(tt)) info = i + 1;
+                rii = sqrt(tt);
+                inv = R(1) / rii;
+            }
             dinv[i] = inv;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {

@@ -1,0 +1,135 @@
+// Iterative refinement of a single-precision inverse (FP32 / complex64):
+//   E  = I - A X        (residual: each product of two FP32 numbers is exact
+//                        in FP64, and the sums are accumulated in FP64)
+//   X <- X + X E        (Newton-Schulz correction, FP32, upper half of X)
+// The paper states the method's accuracy only for well-conditioned inputs
+// (Sec. II); refinement recovers what FP32 arithmetic loses on harder ones.
+//
+// One warp per matrix.  A and the current X are expanded to full Hermitian
+// squares in shared memory (global memory holds only their upper
+// triangles).  For each column j, lanes (one per row) form column j of E in
+// FP64 and park it in shared memory; then the lanes owning rows i <= j add
+// row i of X times that column and write the new x_ij to global memory.
+// The old X stays in shared memory until the step ends.
+#include <algorithm>
+#include <mutex>
+
+#include "batched.cuh"
+#include "dispatch.h"
+
+namespace cholinv {
+
+template <typename V>
+struct wide;  // the FP64 counterpart of a single-precision value type
+template <> struct wide<float> { using type = double; };
+template <> struct wide<cpx<float>> { using type = cpx<double>; };
+
+CHOL_D double widen(float v) { return (double)v; }
+CHOL_D cpx<double> widen(cpx<float> v) { return {(double)v.re, (double)v.im}; }
+CHOL_D float narrow(double v) { return (float)v; }
+CHOL_D cpx<float> narrow(cpx<double> v) { return {(float)v.re, (float)v.im}; }
+
+// gamma = max_i a_ii x_ii lies in [1, kappa_2(A)] for a Hermitian positive
+// definite A (a_ii <= lambda_max and x_ii <= 1/lambda_min).  The automatic
+// mode refines a matrix once when gamma exceeds this bound.
+constexpr double kAutoRefineGamma = 4096.0;
+
+template <typename V>
+CHOL_HD size_t refine_warp_bytes(int N) {
+    using W = typename wide<V>::type;
+    const size_t b = (size_t)2 * N * (N + 1) * sizeof(V) + (size_t)N * sizeof(W);
+    return (b + 15) / 16 * 16;
+}
+
+template <typename V>
+__global__ void k_refine(BatchParams p, int steps, int automatic) {
+    using W = typename wide<V>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = p.max_n;
+    const int LD = N + 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    unsigned char* base = smem_raw + (size_t)w * refine_warp_bytes<V>(N);
+    V* Af = reinterpret_cast<V*>(base);
+    V* Xf = Af + (size_t)N * LD;
+    W* ec = reinterpret_cast<W*>(Xf + (size_t)N * LD);
+    const V* A = static_cast<const V*>(p.A);
+    V* X = static_cast<V*>(p.X);
+
+    for (int b = blockIdx.x * wpc + w; b < p.batch; b += gridDim.x * wpc) {
+        const int n = p.n ? p.n[b] : N;
+        if (n <= 0 || n > N) continue;
+        if (p.info && p.info[b] != 0) continue;
+        const int64_t o = p.off ? p.off[b] : (int64_t)b * (p.layout ? tri64(N) : (int64_t)N * N);
+        auto gidx = [&](int i, int j) { return p.layout ? (int64_t)pidx(n, i, j) : (int64_t)i * n + j; };
+        for (int i = 0; i < n; ++i)
+            for (int j = i + lane; j < n; j += 32) {
+                V a = A[o + gidx(i, j)];
+                if (i == j) a = from_real<V>(re_of(a));
+                Af[i * LD + j] = a;
+                Af[j * LD + i] = conj_v(a);
+            }
+        int todo = steps;
+        for (int s = 0; s <= todo; ++s) {
+            // (re)load the current X
+            __syncwarp();
+            for (int i = 0; i < n; ++i)
+                for (int j = i + lane; j < n; j += 32) {
+                    V x = X[o + gidx(i, j)];
+                    if (i == j) x = from_real<V>(re_of(x));
+                    Xf[i * LD + j] = x;
+                    Xf[j * LD + i] = conj_v(x);
+                }
+            __syncwarp();
+            if (s == 0 && automatic) {
+                double g = 0.0;
+                for (int i = lane; i < n; i += 32)
+                    g = fmax(g, (double)re_of(Af[i * LD + i]) * (double)re_of(Xf[i * LD + i]));
+                for (int d = 16; d > 0; d >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, d));
+                todo = g > kAutoRefineGamma ? 1 : 0;
+            }
+            if (s == todo) break;
+            for (int j = 0; j < n; ++j) {
+                for (int i = lane; i < n; i += 32) {
+                    W acc = zero_v<W>();
+                    for (int k = 0; k < n; ++k) acc = fma_v(widen(Af[i * LD + k]), widen(Xf[k * LD + j]), acc);
+                    ec[i] = (i == j) ? from_real<W>(1.0) - acc : zero_v<W>() - acc;
+                }
+                __syncwarp();
+                for (int i = lane; i <= j; i += 32) {
+                    V acc = Xf[i * LD + j];
+                    for (int k = 0; k < n; ++k) acc = fma_v(Xf[i * LD + k], narrow(ec[k]), acc);
+                    if (i == j) acc = from_real<V>(re_of(acc));
+                    X[o + gidx(i, j)] = acc;
+                }
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <typename V>
+static cudaError_t launch_refine_t(const BatchParams& p, int steps, int automatic, cudaStream_t s, bool dry) {
+    static std::once_flag once;
+    static cudaError_t setup = cudaSuccess;
+    std::call_once(once, [&] {
+        setup = cudaFuncSetAttribute(k_refine<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
+    if (setup != cudaSuccess || dry) return setup;
+    const size_t per = refine_warp_bytes<V>(p.max_n);
+    const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, 98304 / per));
+    int per_sm = 1;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine<V>, 32 * warps, per * warps);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min((p.batch + warps - 1) / warps, device_info().sms * std::max(per_sm, 1)));
+    k_refine<V><<<grid, 32 * warps, per * warps, s>>>(p, steps, automatic);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine(int dtype, const BatchParams& p, int steps, int automatic, cudaStream_t s, bool dry) {
+    if (dtype == CHOL_F32) return launch_refine_t<float>(p, steps, automatic, s, dry);
+    if (dtype == CHOL_C64) return launch_refine_t<cpx<float>>(p, steps, automatic, s, dry);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace cholinv
