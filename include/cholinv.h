@@ -30,10 +30,17 @@
  *     (int64, in elements of the dtype) of A, R, X, G and dA.  n == NULL means
  *     every matrix has order max_n; off == NULL means matrix b starts at
  *     element b * (max_n*max_n) (dense) or b * max_n*(max_n+1)/2 (packed).
- *     max_n is a host int and must be >= every n[b]; 1 <= max_n <= 64 for the
- *     batched kernels.  n[b] == 0 is an empty matrix (info 0, nothing
- *     written).  n[b] < 0 or n[b] > max_n sets info[b] = -1 and the device
- *     error word (CHOL_ERR_ARG).
+ *     max_n is a host int and must be >= every n[b].  n[b] == 0 is an empty
+ *     matrix (info 0, nothing written).  n[b] < 0 or n[b] > max_n sets
+ *     info[b] = -1 and the device error word (CHOL_ERR_ARG).
+ *   Large orders.  max_n <= 64 runs the batched kernels (one matrix per
+ *     thread, thread group or warp).  max_n > 64 runs the blocked path
+ *     (factor and inverse by b x b blocks, products as tiled GEMMs): uniform
+ *     batches only (n == NULL, off == NULL), dense layout, CHOL_F32 or
+ *     CHOL_F64, one matrix after another.  There X is the working storage:
+ *     its lower half is always written (the full Hermitian inverse), X may
+ *     not alias A or R, and refine_steps = -1 means one step.  Other
+ *     combinations return CHOL_ERR_UNSUPPORTED.
  *   Layout (opts->layout).  0: dense row-major n*n; only the upper triangle
  *     (i <= j) of A is read (Sec. II: the lower part is never needed).
  *     1: upper triangle packed row by row (row i holds columns i..n-1),

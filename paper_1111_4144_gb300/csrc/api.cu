@@ -6,6 +6,7 @@
 #include <mutex>
 
 #include "batched.cuh"
+#include "blocked.h"
 #include "dispatch.h"
 
 // The per-device error word; kernels receive its address as an argument.
@@ -235,6 +236,30 @@ BatchParams make_params(int32_t batch, const int32_t* n, const int64_t* off, int
     return p;
 }
 
+// Orders above kBatchedMaxN take the blocked path: uniform batches of dense
+// real matrices (FP32, FP64), processed one matrix at a time.
+chol_status_t blocked_validate(chol_dtype_t dt, int32_t batch, const int32_t* n, const int64_t* off, int32_t max_n,
+                               const chol_opts_t& o, size_t need, void* ws, size_t ws_bytes) {
+    if (dt < CHOL_F32 || dt > CHOL_C128 || batch < 0) return CHOL_ERR_ARG;
+    if (o.layout != 0 && o.layout != 1) return CHOL_ERR_ARG;
+    if (o.prec < CHOL_PREC_NATIVE || o.prec > CHOL_PREC_BF16_REFINE) return CHOL_ERR_ARG;
+    if (o.refine_steps < -1 || o.refine_steps > 2) return CHOL_ERR_ARG;
+    if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER)) return CHOL_ERR_ARG;
+    if (n != nullptr || off != nullptr || o.layout != 0) return CHOL_ERR_UNSUPPORTED;
+    if (dt != CHOL_F32 && dt != CHOL_F64) return CHOL_ERR_UNSUPPORTED;
+    if (o.prec == CHOL_PREC_TF32_REFINE || o.prec == CHOL_PREC_BF16_REFINE) return CHOL_ERR_UNSUPPORTED;
+    if (o.prec == CHOL_PREC_FP32_REFINE && dt != CHOL_F32) return CHOL_ERR_UNSUPPORTED;
+    if (max_n > 1 << 16) return CHOL_ERR_UNSUPPORTED;
+    if (batch > 0 && (ws == nullptr || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256 != 0))
+        return CHOL_ERR_WORKSPACE;
+    return CHOL_OK;
+}
+
+int blocked_refine_steps(const chol_opts_t& o) {
+    if (o.prec != CHOL_PREC_FP32_REFINE) return 0;
+    return o.refine_steps < 0 ? 1 : o.refine_steps;
+}
+
 }  // namespace
 
 DeviceInfo device_info() {
@@ -260,6 +285,15 @@ chol_status_t chol_factor_batched(chol_dtype_t dt, int32_t batch, const int32_t*
                                   int32_t max_n, const void* A, void* R, int32_t* info,
                                   const chol_opts_t* opts, void* ws, size_t ws_bytes, void* stream) {
     const chol_opts_t o = opts_or_default(opts);
+    if (max_n > kBatchedMaxN) {
+        chol_status_t sb = blocked_validate(dt, batch, n, off, max_n, o,
+                                            blocked_workspace_bytes(dt, max_n, 0), ws, ws_bytes);
+        if (sb != CHOL_OK || batch == 0) return sb;
+        if (A == nullptr || R == nullptr) return CHOL_ERR_ARG;
+        // the factor is formed in R itself (R is the working storage)
+        return blocked_run(dt, batch, max_n, A, nullptr, R, info, o.flags & CHOL_FLAG_PIVOT64, 0, 0, ws,
+                           static_cast<cudaStream_t>(stream));
+    }
     chol_status_t st = check_common(dt, batch, max_n, o);
     if (st != CHOL_OK) return st;
     if (batch == 0) return CHOL_OK;
@@ -274,6 +308,16 @@ chol_status_t chol_inv_batched(chol_dtype_t dt, int32_t batch, const int32_t* n,
                                int32_t max_n, const void* A, void* R, void* X, int32_t* info,
                                const chol_opts_t* opts, void* ws, size_t ws_bytes, void* stream) {
     const chol_opts_t o = opts_or_default(opts);
+    if (max_n > kBatchedMaxN) {
+        const int rs = blocked_refine_steps(o);
+        chol_status_t sb = blocked_validate(dt, batch, n, off, max_n, o, blocked_workspace_bytes(dt, max_n, rs), ws,
+                                            ws_bytes);
+        if (sb != CHOL_OK || batch == 0) return sb;
+        if (A == nullptr || X == nullptr) return CHOL_ERR_ARG;
+        if (X == A || (R != nullptr && (R == A || R == X))) return CHOL_ERR_ARG;
+        return blocked_run(dt, batch, max_n, A, R, X, info, o.flags & CHOL_FLAG_PIVOT64, rs, 1, ws,
+                           static_cast<cudaStream_t>(stream));
+    }
     chol_status_t st = inv_validate(dt, batch, n, max_n, A, X, o, ws, ws_bytes);
     if (st != CHOL_OK || batch == 0) return st;
     BatchParams p = make_params(batch, n, off, max_n, A, (R == X) ? nullptr : R, X, info, o, 1);
@@ -307,7 +351,9 @@ chol_status_t chol_inv_backward(chol_dtype_t dt, int32_t batch, const int32_t* n
 
 size_t chol_workspace_bytes(int32_t call, chol_dtype_t dt, int32_t batch, int32_t max_n, int32_t has_sizes,
                             const chol_opts_t* opts) {
-    (void)dt; (void)max_n; (void)opts;
+    const chol_opts_t o = opts_or_default(opts);
+    if (max_n > kBatchedMaxN && (call == CHOL_CALL_FACTOR || call == CHOL_CALL_INV))
+        return blocked_workspace_bytes(dt, max_n, call == CHOL_CALL_INV ? blocked_refine_steps(o) : 0);
     if (call == CHOL_CALL_FACTOR || call == CHOL_CALL_INV) return ws_need_batched(batch, has_sizes);
     return 0;
 }

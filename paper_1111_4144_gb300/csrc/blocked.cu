@@ -1,0 +1,506 @@
+// Blocked path for large matrices (order > 64): the paper's factorisation
+// (Eqs. 3-4) and inverse recurrence (Sec. IV.A) taken block by block.
+//
+// Factor, right-looking, panel K of b rows:
+//   R_KK      = chol(A_KK)                    Eqs. 3-4 on the diagonal block (one CTA)
+//   R_K,>K    = R_KK^{-T} A_K,>K              Eq. 4 for the block row (a GEMM with the
+//                                            inverted b x b diagonal block)
+//   A_>K,>K  -= R_K,>K^T R_K,>K               the k < i terms of Eqs. 3-4 (upper tiles only)
+// Inverse, block rows I = last..first (R X = S, S = diag(1/r_ii)):
+//   X_I,>I    = -R_II^{-1} (R_I,>I X_>I,>I)   off-diagonal blocks (x_ij = -(1/r_ii) sum_{k>i} r_ik x~_kj)
+//   Z         = R_I,>I X_I,>I^T               the k beyond the block part of the diagonal sums
+//   X_II      : the recurrence inside the block with s_ij replaced by s_ij - z_ij
+// X is kept full (each new block row is mirrored into its block column) so
+// that every product reads plain dense operands.  The matrix lives in X
+// (dense row-major, in place); A is only read.
+//
+// The products run through one tiled GEMM (`k_gemm`); the small triangular
+// pieces through single-CTA kernels.  Real element types (FP32, FP64).
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "batched.cuh"
+#include "blocked.h"
+#include "dispatch.h"
+
+namespace cholinv {
+
+// ---------------------------------------------------------------------------
+// Tiled GEMM:  C = alpha * op(A) op(B) + beta * C   (or, with `partial`, the
+// raw product of one K-slice into partial[z]).  op(A) is M x K: A stored
+// row-major M x K (TA = false) or K x M (TA = true); op(B) is K x N: stored
+// K x N (TB = false) or N x K (TB = true).  upper != 0 computes only the
+// entries with row <= col (tiles wholly below the diagonal are skipped).
+// 128 x 128 tiles, BK = 8, 256 threads, 8 x 8 outputs per thread.
+// ---------------------------------------------------------------------------
+constexpr int GB_M = 128, GB_N = 128, GB_K = 8, GB_THREADS = 256;
+
+template <typename Tin, typename Tacc, typename Tout, bool TA, bool TB>
+__global__ void __launch_bounds__(GB_THREADS)
+k_gemm(int M, int N, int K, Tacc alpha, const Tin* __restrict__ A, int64_t lda, const Tin* __restrict__ B,
+       int64_t ldb, Tacc beta, Tout* C, int64_t ldc, int upper, int kchunk, Tacc* partial) {
+    __shared__ Tin As[2][GB_K][GB_M + 4];
+    __shared__ Tin Bs[2][GB_K][GB_N + 4];
+    const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
+    if (upper && m0 > n0 + GB_N - 1) return;
+    const int kb = blockIdx.z * kchunk;
+    const int ke = min(K, kb + kchunk);
+    const int t = threadIdx.x;
+    const int tm = (t / 16) * 8, tn = (t % 16) * 8;
+    Tacc acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = Tacc(0);
+
+    auto load = [&](int buf, int k0) {
+        // 128 x 8 elements of each operand, 4 per thread
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int f = t + r * GB_THREADS;
+            int mm, kk;
+            if (TA) { kk = f / GB_M; mm = f % GB_M; } else { mm = f / GB_K; kk = f % GB_K; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            Tin v = Tin(0);
+            if (gm < M && gk < ke) v = TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
+            As[buf][kk][mm] = v;
+            int nn, k2;
+            if (TB) { nn = f / GB_K; k2 = f % GB_K; } else { k2 = f / GB_N; nn = f % GB_N; }
+            const int gn = n0 + nn, gk2 = k0 + k2;
+            Tin w = Tin(0);
+            if (gn < N && gk2 < ke) w = TB ? B[(int64_t)gn * ldb + gk2] : B[(int64_t)gk2 * ldb + gn];
+            Bs[buf][k2][nn] = w;
+        }
+    };
+    int buf = 0;
+    if (kb < ke) load(0, kb);
+    __syncthreads();
+    for (int k0 = kb; k0 < ke; k0 += GB_K) {
+        if (k0 + GB_K < ke) load(buf ^ 1, k0 + GB_K);
+#pragma unroll
+        for (int kk = 0; kk < GB_K; ++kk) {
+            Tacc a[8], b[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = (Tacc)As[buf][kk][tm + i];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) b[j] = (Tacc)Bs[buf][kk][tn + j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int gm = m0 + tm + i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int gn = n0 + tn + j;
+            if (gn >= N || (upper && gm > gn)) continue;
+            if (partial) {
+                partial[((int64_t)blockIdx.z * M + gm) * N + gn] = acc[i][j];
+            } else {
+                Tacc c = alpha * acc[i][j];
+                if (beta != Tacc(0)) c = fma(beta, (Tacc)C[(int64_t)gm * ldc + gn], c);
+                C[(int64_t)gm * ldc + gn] = (Tout)c;
+            }
+        }
+    }
+}
+
+// C = alpha * sum_z partial[z] + beta * C, z ascending (deterministic split-K).
+template <typename Tacc, typename Tout>
+__global__ void k_splitk_reduce(int M, int N, int splits, Tacc alpha, const Tacc* partial, Tacc beta, Tout* C,
+                                int64_t ldc, int upper) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < (int64_t)M * N;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        const int gm = (int)(f / N), gn = (int)(f % N);
+        if (upper && gm > gn) continue;
+        Tacc s = Tacc(0);
+        for (int z = 0; z < splits; ++z) s += partial[(int64_t)z * M * N + f];
+        Tacc c = alpha * s;
+        if (beta != Tacc(0)) c = fma(beta, (Tacc)C[(int64_t)gm * ldc + gn], c);
+        C[(int64_t)gm * ldc + gn] = (Tout)c;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal block: Eqs. 3-4 on the b x b block at (k0, k0) of X (in place),
+// then the inverse of the triangular factor (R_KK^{-1}, upper) into Rinv.
+// One CTA of 256 threads; the block sits in shared memory.  A pivot <= 0 or
+// non-finite sets *failed and info (1-based global row).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_blk_potrf(T* X, int64_t ldx, int n0, int k0, int b, T* Rinv, int* failed, int32_t* info,
+                            int pivot64) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* S = reinterpret_cast<T*>(smem_raw);  // [b][b+1]
+    const int LD = b + 1;
+    const int t = threadIdx.x;
+    if (*failed) return;
+    for (int f = t; f < b * b; f += blockDim.x) {
+        const int i = f / b, j = f % b;
+        S[i * LD + j] = (i <= j) ? X[(int64_t)(k0 + i) * ldx + k0 + j] : T(0);
+    }
+    __syncthreads();
+    __shared__ int bad;
+    if (t == 0) bad = 0;
+    __syncthreads();
+    for (int i = 0; i < b; ++i) {
+        // row i: s_j = a_ij - sum_{k<i} r_ki r_kj, j >= i (left-looking, Eq. 4's order)
+        T sj = T(0);
+        const int j = t;
+        if (j >= i && j < b) {
+            sj = S[i * LD + j];
+            for (int k = 0; k < i; ++k) sj = fma(-S[k * LD + i], S[k * LD + j], sj);
+        }
+        __syncthreads();
+        if (j == i) {
+            double td = (double)sj;
+            if (pivot64 && sizeof(T) == 4) {
+                td = (double)S[i * LD + i];
+                for (int k = 0; k < i; ++k) td -= (double)S[k * LD + i] * (double)S[k * LD + i];
+            }
+            if (!(td > 0.0) || !isfinite(td)) {
+                if (atomicCAS(failed, 0, 1) == 0 && info) *info = k0 + i + 1;
+                bad = 1;
+            }
+            S[i * LD + i] = (T)sqrt(td);
+        }
+        __syncthreads();
+        if (j > i && j < b) S[i * LD + j] = sj / S[i * LD + i];
+        __syncthreads();
+    }
+    if (bad) return;
+    // R_KK back to X (upper part)
+    for (int f = t; f < b * b; f += blockDim.x) {
+        const int i = f / b, j = f % b;
+        if (i <= j) X[(int64_t)(k0 + i) * ldx + k0 + j] = S[i * LD + j];
+    }
+    // Rinv = R_KK^{-1}: column j by back substitution, one thread per column
+    for (int j = t; j < b; j += blockDim.x) {
+        for (int i = b - 1; i >= 0; --i) {
+            if (i > j) { Rinv[(int64_t)i * b + j] = T(0); continue; }
+            T s = (i == j) ? T(1) : T(0);
+            for (int k = i + 1; k <= j; ++k) s = fma(-S[i * LD + k], Rinv[(int64_t)k * b + j], s);
+            Rinv[(int64_t)i * b + j] = s / S[i * LD + i];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Diagonal block of X (Sec. IV.A inside the block): with Z = R_I,>I X_I,>I^T,
+//   x_ij = ((delta_ij / r_ii - z_ij) - sum_{k>i, k in block} r_ik x~_kj) / r_ii,  i <= j,
+// rows from the last to the first; written to both triangles of the block.
+// One CTA; R_II (from X) and the block of X in shared memory.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_blk_diag(T* X, int64_t ldx, int i0, int b, const T* Z, const int* failed) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* Rs = reinterpret_cast<T*>(smem_raw);  // [b][b+1] R_II
+    T* Xs = Rs + (size_t)b * (b + 1);         // [b][b+1] X_II (full)
+    const int LD = b + 1;
+    const int t = threadIdx.x;
+    if (*failed) return;
+    for (int f = t; f < b * b; f += blockDim.x) {
+        const int i = f / b, j = f % b;
+        Rs[i * LD + j] = (i <= j) ? X[(int64_t)(i0 + i) * ldx + i0 + j] : T(0);
+    }
+    __syncthreads();
+    for (int i = b - 1; i >= 0; --i) {
+        const T inv = T(1) / Rs[i * LD + i];
+        const int j = t;
+        T x = T(0);
+        if (j > i && j < b) {
+            T s = Z ? Z[(int64_t)i * b + j] : T(0);
+            for (int k = i + 1; k < b; ++k) s = fma(Rs[i * LD + k], (k <= j) ? Xs[k * LD + j] : Xs[j * LD + k], s);
+            x = -s * inv;
+        }
+        __syncthreads();
+        if (j > i && j < b) { Xs[i * LD + j] = x; Xs[j * LD + i] = x; }
+        __syncthreads();
+        if (t == 0) {
+            T s = Z ? Z[(int64_t)i * b + i] : T(0);
+            for (int k = i + 1; k < b; ++k) s = fma(Rs[i * LD + k], Xs[i * LD + k], s);
+            Xs[i * LD + i] = (inv - s) * inv;
+        }
+        __syncthreads();
+    }
+    for (int f = t; f < b * b; f += blockDim.x) {
+        const int i = f / b, j = f % b;
+        X[(int64_t)(i0 + i) * ldx + i0 + j] = Xs[i * LD + j];
+    }
+}
+
+// Copy a b x m panel P into X at (r0, c0) and its transpose at (c0, r0).
+template <typename T>
+__global__ void k_put_panel(T* X, int64_t ldx, int r0, int c0, int b, int m, const T* P, int mirror, const int* failed) {
+    if (*failed) return;
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < (int64_t)b * m;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(f / m), j = (int)(f % m);
+        const T v = P[f];
+        X[(int64_t)(r0 + i) * ldx + c0 + j] = v;
+        if (mirror) X[(int64_t)(c0 + j) * ldx + r0 + i] = v;
+    }
+}
+
+// X (n x n) <- upper triangle of A (layout dense, ld n); lower part cleared.
+template <typename T>
+__global__ void k_load_upper(T* X, const T* A, int n) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < (int64_t)n * n;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(f / n), j = (int)(f % n);
+        X[f] = (i <= j) ? A[f] : T(0);
+    }
+}
+
+// Full symmetric copy of A from its upper triangle (for the refinement residual).
+template <typename T>
+__global__ void k_sym_full(T* F, const T* A, int n) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < (int64_t)n * n;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(f / n), j = (int)(f % n);
+        F[f] = (i <= j) ? A[f] : A[(int64_t)j * n + i];
+    }
+}
+
+template <typename T>
+__global__ void k_identity(T* E, int n) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < (int64_t)n * n;
+         f += (int64_t)gridDim.x * blockDim.x)
+        E[f] = ((f / n) == (f % n)) ? T(1) : T(0);
+}
+
+// Fill X with NaN when the factorisation failed.
+template <typename T>
+__global__ void k_nan_if_failed(T* X, int64_t count, const int* failed) {
+    if (!*failed) return;
+    const T q = T(__int_as_float(0x7fffffff));
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < count; f += (int64_t)gridDim.x * blockDim.x)
+        X[f] = q;
+}
+
+// X += C elementwise.
+__global__ void k_axpy(float* X, const float* C, int64_t count) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < count; f += (int64_t)gridDim.x * blockDim.x)
+        X[f] += C[f];
+}
+
+// R <- upper triangle of X, lower part zero (the factor, before the inverse overwrites it).
+template <typename T>
+__global__ void k_copy_upper(T* R, const T* X, int n, const int* failed) {
+    const T q = T(__int_as_float(0x7fffffff));
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < (int64_t)n * n;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(f / n), j = (int)(f % n);
+        R[f] = *failed ? q : ((i <= j) ? X[f] : T(0));
+    }
+}
+
+// Convert the FP64 residual to the working precision.
+__global__ void k_narrow(float* dst, const double* src, int64_t count) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < count; f += (int64_t)gridDim.x * blockDim.x)
+        dst[f] = (float)src[f];
+}
+
+// ---------------------------------------------------------------------------
+// Host driver
+// ---------------------------------------------------------------------------
+namespace {
+
+// Panel width b: 128 for FP32, 64 for FP64 (the diagonal-block kernels hold
+// two b x b blocks in shared memory).
+constexpr int kblk(int dtype) { return dtype == CHOL_F64 ? 64 : 128; }
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+struct BlkWs {
+    char* base;
+    size_t off = 0;
+    template <typename U>
+    U* take(size_t count) {
+        U* p = reinterpret_cast<U*>(base + off);
+        off += align256(count * sizeof(U));
+        return p;
+    }
+};
+
+template <typename Tin, typename Tacc, typename Tout, bool TA, bool TB>
+cudaError_t gemm(int M, int N, int K, Tacc alpha, const Tin* A, int64_t lda, const Tin* B, int64_t ldb, Tacc beta,
+                 Tout* C, int64_t ldc, int upper, Tacc* partial, size_t partial_elems, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const int sms = device_info().sms;
+    dim3 grid((N + GB_N - 1) / GB_N, (M + GB_M - 1) / GB_M, 1);
+    int splits = 1;
+    if (partial && K > 0) {
+        const int tiles = grid.x * grid.y;
+        while (splits < 32 && tiles * splits * 2 <= 2 * sms && K / (splits * 2) >= 256 &&
+               (size_t)M * N * splits * 2 <= partial_elems)
+            splits *= 2;
+    }
+    if (splits == 1) {
+        k_gemm<Tin, Tacc, Tout, TA, TB><<<grid, GB_THREADS, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                                                                   upper, K > 0 ? K : 1, nullptr);
+        return cudaGetLastError();
+    }
+    int kchunk = (K + splits - 1) / splits;
+    kchunk = (kchunk + GB_K - 1) / GB_K * GB_K;
+    grid.z = splits;
+    k_gemm<Tin, Tacc, Tacc, TA, TB><<<grid, GB_THREADS, 0, s>>>(M, N, K, Tacc(1), A, lda, B, ldb, Tacc(0),
+                                                               partial, N, upper, kchunk, partial);
+    const int64_t total = (int64_t)M * N;
+    const int rgrid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sms * 8);
+    k_splitk_reduce<Tacc, Tout><<<rgrid, 256, 0, s>>>(M, N, splits, alpha, partial, beta, C, ldc, upper);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t blocked_workspace_bytes(int dtype, int n, int refine) {
+    if (n <= 0) return 0;
+    const size_t es = (dtype == CHOL_F64) ? 8 : 4;
+    const int kBlk = kblk(dtype);
+    const int nb = (n + kBlk - 1) / kBlk;
+    size_t bytes = 256;                                       // failed flag
+    bytes += align256((size_t)nb * kBlk * kBlk * es);         // Rinv blocks
+    bytes += 2 * align256((size_t)kBlk * n * es);             // panels
+    bytes += align256((size_t)kBlk * kBlk * es);              // Z
+    bytes += align256((size_t)32 * kBlk * n * (dtype == CHOL_F64 ? 8 : 4));  // split-K partials
+    if (refine) {
+        bytes += align256((size_t)n * n * 4);   // full A (FP32)
+        bytes += align256((size_t)n * n * 8);   // residual (FP64)
+        bytes += align256((size_t)n * n * 4);   // residual (FP32) / correction
+        bytes += align256((size_t)32 * std::max<size_t>((size_t)n * n, 1) * 0);  // (no extra partials)
+    }
+    return bytes;
+}
+
+template <typename T>
+static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, int pivot64, int refine_steps,
+                                 int want_inv, char* ws, cudaStream_t s) {
+    using Tacc = T;
+    const int b = kblk(sizeof(T) == 8 ? CHOL_F64 : CHOL_F32);
+    const int nb = (n + b - 1) / b;
+    BlkWs w{ws};
+    int* failed = w.take<int>(64);
+    T* Rinv = w.take<T>((size_t)nb * b * b);
+    T* P = w.take<T>((size_t)b * n);
+    T* P2 = w.take<T>((size_t)b * n);
+    T* Z = w.take<T>((size_t)b * b);
+    const size_t part_elems = (size_t)32 * b * n;
+    Tacc* part = w.take<Tacc>(part_elems);
+    const int sms = device_info().sms;
+    const int g1 = sms * 4;
+    static std::once_flag once;
+    static cudaError_t setup = cudaSuccess;
+    const size_t potrf_smem = (size_t)b * (b + 1) * sizeof(T);
+    const size_t diag_smem = 2 * (size_t)b * (b + 1) * sizeof(T);
+    std::call_once(once, [&] {
+        setup = cudaFuncSetAttribute(k_blk_potrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem);
+        if (setup == cudaSuccess)
+            setup = cudaFuncSetAttribute(k_blk_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem);
+    });
+    if (setup != cudaSuccess) return CHOL_ERR_CUDA;
+    if (cudaMemsetAsync(failed, 0, sizeof(int), s) != cudaSuccess) return CHOL_ERR_CUDA;
+    if (info && cudaMemsetAsync(info, 0, sizeof(int32_t), s) != cudaSuccess) return CHOL_ERR_CUDA;
+    k_load_upper<T><<<g1, 256, 0, s>>>(X, A, n);
+    // ---------------- factor
+    for (int kb = 0; kb < nb; ++kb) {
+        const int k0 = kb * b;
+        const int bk = std::min(b, n - k0);
+        const int m = n - k0 - bk;  // columns right of the panel
+        T* RinvK = Rinv + (size_t)kb * b * b;
+        k_blk_potrf<T><<<1, 256, potrf_smem, s>>>(X, n, n, k0, bk, RinvK, failed, info, pivot64);
+        if (m <= 0) break;
+        // R_K,>K = R_KK^{-T} A_K,>K  (into P), then back into X
+        cudaError_t e = gemm<T, Tacc, T, true, false>(bk, m, bk, Tacc(1), RinvK, bk, X + (int64_t)k0 * n + k0 + bk,
+                                                      n, Tacc(0), P, m, 0, part, part_elems, s);
+        if (e != cudaSuccess) return CHOL_ERR_CUDA;
+        k_put_panel<T><<<g1, 256, 0, s>>>(X, n, k0, k0 + bk, bk, m, P, 0, failed);
+        // A_>K,>K -= R_K,>K^T R_K,>K (upper part)
+        T* Ct = X + (int64_t)(k0 + bk) * n + k0 + bk;
+        e = gemm<T, Tacc, T, true, false>(m, m, bk, Tacc(-1), P, m, P, m, Tacc(1), Ct, n, 1, part, part_elems, s);
+        if (e != cudaSuccess) return CHOL_ERR_CUDA;
+    }
+    if (R) k_copy_upper<T><<<g1, 256, 0, s>>>(R, X, n, failed);
+    if (!want_inv) return cudaGetLastError() == cudaSuccess ? CHOL_OK : CHOL_ERR_CUDA;
+    // ---------------- inverse, block rows last..first
+    for (int ib = nb - 1; ib >= 0; --ib) {
+        const int i0 = ib * b;
+        const int bi = std::min(b, n - i0);
+        const int m = n - i0 - bi;
+        const T* RinvI = Rinv + (size_t)ib * b * b;
+        if (m > 0) {
+            const T* RIr = X + (int64_t)i0 * n + i0 + bi;          // R_I,>I   (bi x m, ld n)
+            const T* Xrr = X + (int64_t)(i0 + bi) * n + i0 + bi;  // X_>I,>I  (m x m, ld n, full)
+            // P = R_I,>I X_>I,>I
+            cudaError_t e = gemm<T, Tacc, T, false, false>(bi, m, m, Tacc(1), RIr, n, Xrr, n, Tacc(0), P, m, 0, part,
+                                                           part_elems, s);
+            if (e != cudaSuccess) return CHOL_ERR_CUDA;
+            // P2 = -R_II^{-1} P   (X_I,>I)
+            e = gemm<T, Tacc, T, false, false>(bi, m, bi, Tacc(-1), RinvI, bi, P, m, Tacc(0), P2, m, 0, part,
+                                              part_elems, s);
+            if (e != cudaSuccess) return CHOL_ERR_CUDA;
+            // Z = R_I,>I X_I,>I^T
+            e = gemm<T, Tacc, T, false, true>(bi, bi, m, Tacc(1), RIr, n, P2, m, Tacc(0), Z, bi, 0, part, part_elems,
+                                             s);
+            if (e != cudaSuccess) return CHOL_ERR_CUDA;
+            k_put_panel<T><<<g1, 256, 0, s>>>(X, n, i0, i0 + bi, bi, m, P2, 1, failed);
+        }
+        k_blk_diag<T><<<1, 256, diag_smem, s>>>(X, n, i0, bi, m > 0 ? Z : nullptr, failed);
+    }
+    k_nan_if_failed<T><<<g1, 256, 0, s>>>(X, (int64_t)n * n, failed);
+    if (cudaGetLastError() != cudaSuccess) return CHOL_ERR_CUDA;
+
+    // ---------------- refinement (FP32 only): E = I - A X in FP64, X += X E
+    if (refine_steps > 0 && sizeof(T) == 4) {
+        float* Af = w.take<float>((size_t)n * n);
+        double* E = w.take<double>((size_t)n * n);
+        float* E32 = w.take<float>((size_t)n * n);
+        const float* A32 = reinterpret_cast<const float*>(A);
+        float* X32 = reinterpret_cast<float*>(X);
+        k_sym_full<float><<<g1, 256, 0, s>>>(Af, A32, n);
+        for (int st = 0; st < refine_steps; ++st) {
+            k_identity<double><<<g1, 256, 0, s>>>(E, n);
+            cudaError_t e = gemm<float, double, double, false, false>(n, n, n, -1.0, Af, n, X32, n, 1.0, E, n, 0,
+                                                                     nullptr, 0, s);
+            if (e != cudaSuccess) return CHOL_ERR_CUDA;
+            k_narrow<<<g1, 256, 0, s>>>(E32, E, (int64_t)n * n);
+            // the correction X E goes to a separate buffer (the FP64 one, now free): the
+            // product reads X while it runs
+            float* Cx = reinterpret_cast<float*>(E);
+            e = gemm<float, float, float, false, false>(n, n, n, 1.0f, X32, n, E32, n, 0.0f, Cx, n, 0, nullptr, 0, s);
+            if (e != cudaSuccess) return CHOL_ERR_CUDA;
+            k_axpy<<<g1, 256, 0, s>>>(X32, Cx, (int64_t)n * n);
+        }
+        if (cudaGetLastError() != cudaSuccess) return CHOL_ERR_CUDA;
+    }
+    return CHOL_OK;
+}
+
+chol_status_t blocked_run(int dtype, int32_t batch, int32_t n, const void* A, void* R, void* X, int32_t* info,
+                          int pivot64, int refine_steps, int want_inv, void* ws, cudaStream_t s) {
+    for (int32_t bi = 0; bi < batch; ++bi) {
+        const int64_t o = (int64_t)bi * n * n;
+        chol_status_t st;
+        if (dtype == CHOL_F32)
+            st = blocked_one<float>(static_cast<const float*>(A) + o, R ? static_cast<float*>(R) + o : nullptr,
+                                    static_cast<float*>(X) + o, n, info ? info + bi : nullptr, pivot64,
+                                    refine_steps, want_inv, static_cast<char*>(ws), s);
+        else if (dtype == CHOL_F64)
+            st = blocked_one<double>(static_cast<const double*>(A) + o, R ? static_cast<double*>(R) + o : nullptr,
+                                     static_cast<double*>(X) + o, n, info ? info + bi : nullptr, 0, 0, want_inv,
+                                     static_cast<char*>(ws), s);
+        else
+            return CHOL_ERR_UNSUPPORTED;
+        if (st != CHOL_OK) return st;
+    }
+    return CHOL_OK;
+}
+
+}  // namespace cholinv

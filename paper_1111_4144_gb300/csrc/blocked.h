@@ -1,0 +1,21 @@
+// Blocked large-order path (blocked.cu), called by api.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/cholinv.h"
+
+namespace cholinv {
+
+// Device workspace of one blocked call (matrices are processed one at a time).
+size_t blocked_workspace_bytes(int dtype, int n, int refine);
+
+// Factor (and, if want_inv, invert) `batch` dense n x n matrices stored back
+// to back.  X is the working storage and receives the full Hermitian
+// inverse; R (optional) receives the factor.  Real types only.
+chol_status_t blocked_run(int dtype, int32_t batch, int32_t n, const void* A, void* R, void* X, int32_t* info,
+                          int pivot64, int refine_steps, int want_inv, void* ws, cudaStream_t s);
+
+}  // namespace cholinv

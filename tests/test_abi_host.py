@@ -57,7 +57,10 @@ FAKE = 0x100000  # a non-null pointer value; never dereferenced because validati
     (dict(dt=9), "ARG"),
     (dict(batch=-1), "ARG"),
     (dict(max_n=0), "ARG"),
-    (dict(max_n=65), "UNSUPPORTED"),
+    (dict(max_n=65), "WORKSPACE"),          # blocked path: needs its workspace
+    (dict(max_n=65, n=FAKE), "UNSUPPORTED"),  # blocked path: uniform batches only
+    (dict(max_n=65, dt=2), "UNSUPPORTED"),    # blocked path: real types only
+    (dict(max_n=65, layout=1), "UNSUPPORTED"),
     (dict(A=None), "ARG"),
     (dict(X=None), "ARG"),
     (dict(layout=2), "ARG"),

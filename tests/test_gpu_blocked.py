@@ -1,0 +1,130 @@
+"""GPU parity of the blocked large-order path (orders > 64) against the oracle."""
+import numpy as np
+import pytest
+
+from paper_1111_4144_gb300 import workloads as wl
+
+from gpu_helpers import TOL64, U32, tol32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1111_4144_gb300 import _lib
+    _lib.load()
+
+
+def _run(A_np, **kw):
+    import torch
+    from paper_1111_4144_gb300 import api
+    A = torch.from_numpy(A_np).cuda()
+    out = api.inv(A, **kw)
+    torch.cuda.synchronize()
+    return [o.cpu().numpy() for o in out]
+
+
+def _oracle(orc, M):
+    R, info = orc.chol(M)
+    X = orc.inv_rows(R) if info == 0 else None
+    return R, X, info
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("N", [65, 128, 200, 300, 513])
+def test_blocked_fp64_parity(orc, N):
+    b = wl.log_spaced(N, decades=4.0, seed=1004 + N)
+    A = b.A.reshape(1, N, N)
+    X, info, R = _run(A, want_R=True)
+    Ro, Xo, info_o = _oracle(orc, A[0])
+    assert info[0] == 0 and info_o == 0
+    # X is written in full (Hermitian); compare the upper triangle, check the mirror
+    assert _rel(np.triu(X[0]), np.triu(Xo)) <= TOL64
+    assert np.array_equal(np.tril(X[0], -1), np.triu(X[0], 1).T)
+    assert _rel(R[0], Ro) <= TOL64 and np.all(np.tril(R[0], -1) == 0)
+
+
+@pytest.mark.parametrize("N", [100, 257, 600])
+def test_blocked_fp32_parity(orc, N):
+    b = wl.qr_spectrum(2, lambda rng, m: np.full(m, N), lambda rng, m, NN: 10.0 ** rng.uniform(0, 3, size=(m, NN)),
+                       seed=77 + N)
+    A = b.A.reshape(2, N, N).astype(np.float32)
+    X, info = _run(A)
+    for k in range(2):
+        _, Xo, _ = _oracle(orc, A[k].astype(np.float64))
+        Aw = A[k].astype(np.float64)
+        kap = np.linalg.cond(np.triu(Aw) + np.triu(Aw, 1).T)
+        assert info[k] == 0
+        assert _rel(np.triu(X[k]), np.triu(Xo)) <= tol32(kap)
+
+
+@pytest.mark.parametrize("N", [160, 400])
+def test_blocked_fp32_refined(orc, N):
+    from paper_1111_4144_gb300 import _lib as L
+    b = wl.log_spaced(N, decades=4.0, seed=5 + N)
+    A = b.A.reshape(1, N, N).astype(np.float32)
+    _, Xo, _ = _oracle(orc, A[0].astype(np.float64))
+    X0, _ = _run(A)
+    X2, info = _run(A, prec=L.CHOL_PREC_FP32_REFINE, refine_steps=2)
+    e0 = _rel(np.triu(X0[0]), np.triu(Xo))
+    e2 = _rel(np.triu(X2[0]), np.triu(Xo))
+    assert info[0] == 0
+    assert e2 <= 64 * U32 and e2 < e0 / 10, (e0, e2)
+
+
+def test_blocked_non_pd_info(orc):
+    N = 300
+    b = wl.log_spaced(N, decades=2.0, seed=3)
+    A = b.A.reshape(1, N, N).copy()
+    A[0, 200, 200] = -5.0
+    X, info = _run(A)
+    _, _, info_o = _oracle(orc, A[0])
+    assert info[0] == info_o == 201
+    assert np.all(np.isnan(X[0]))
+
+
+def test_blocked_factor_only(orc):
+    import torch
+    from paper_1111_4144_gb300 import api
+    N = 257
+    b = wl.log_spaced(N, decades=3.0, seed=11)
+    A = torch.from_numpy(b.A.reshape(1, N, N)).cuda()
+    R, info = api.factor(A)
+    torch.cuda.synchronize()
+    Ro, _, _ = _oracle(orc, b.A.reshape(N, N))
+    R = R.cpu().numpy()[0]
+    assert info.item() == 0
+    assert _rel(np.triu(R), Ro) <= TOL64
+
+
+def test_blocked_fp64_2048_against_oracle(orc):
+    N = 2048
+    b = wl.log_spaced(N, decades=4.0, seed=2048)
+    A = b.A.reshape(1, N, N)
+    X, info = _run(A)
+    _, Xo, _ = _oracle(orc, A[0])
+    assert info[0] == 0 and _rel(np.triu(X[0]), np.triu(Xo)) <= TOL64
+
+
+def test_blocked_fp32_4096_residual():
+    """The large workload size: the residual property holds at any size."""
+    from paper_1111_4144_gb300 import _lib as L
+    N = 4096
+    b = wl.log_spaced(N, decades=4.0, seed=1004)
+    A = b.A.reshape(1, N, N).astype(np.float32)
+    X, info = _run(A, prec=L.CHOL_PREC_FP32_REFINE, refine_steps=2)
+    assert info[0] == 0
+    Aw = A[0].astype(np.float64)
+    Aw = np.triu(Aw) + np.triu(Aw, 1).T
+    Xw = X[0].astype(np.float64)
+    res = np.linalg.norm(Aw @ Xw - np.eye(N)) / (np.linalg.norm(Aw) * np.linalg.norm(Xw))
+    assert res <= 64 * U32, res
+    # against the FP64 solution of the same (rounded) matrix
+    Xref = np.linalg.inv(Aw)
+    assert _rel(np.triu(Xw), np.triu(Xref)) <= 1e-5
