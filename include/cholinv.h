@@ -103,6 +103,8 @@ typedef enum {
 #define CHOL_FLAG_PIVOT64 0x1     /* F32/C64: accumulate Eq. 3 (the pivot) in FP64 and take its sqrt in FP64 */
 #define CHOL_FLAG_GRAD_UPPER 0x2  /* chol_inv_backward: gradient with respect to the upper triangle taken as
                                      the independent parameters (see chol_inv_backward) */
+#define CHOL_FLAG_PLAN_TIMING 0x4 /* chol_plan_inv_create only: record timing events around each size-class
+                                     kernel (see chol_plan_kernel_ms) */
 
 typedef struct {
     int32_t prec;          /* chol_prec_t */
@@ -229,6 +231,16 @@ chol_status_t chol_plan_inv_create(chol_plan_t** plan, chol_dtype_t dt, int32_t 
                                    int32_t* info, const chol_opts_t* opts, void* ws, size_t ws_bytes);
 chol_status_t chol_plan_launch(chol_plan_t* plan, void* stream);
 chol_status_t chol_plan_destroy(chol_plan_t* plan);
+
+/*
+ * Duration in milliseconds of the kernel of matrix order `order` in the
+ * plan's most recent replay (the plan must have been created with
+ * CHOL_FLAG_PLAN_TIMING and the replay's stream synchronised).  For a batch
+ * with per-matrix sizes the size-class kernels run on parallel streams, so
+ * a duration includes any overlap with the other orders' kernels.
+ * CHOL_ERR_ARG if the plan records no timing or no kernel of that order.
+ */
+chol_status_t chol_plan_kernel_ms(chol_plan_t* plan, int32_t order, float* ms);
 
 #ifdef __cplusplus
 }

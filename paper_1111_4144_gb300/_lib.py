@@ -25,6 +25,7 @@ CHOL_OK, CHOL_ERR_ARG, CHOL_ERR_CUDA, CHOL_ERR_UNSUPPORTED, CHOL_ERR_TIMEOUT, CH
 CHOL_PREC_NATIVE, CHOL_PREC_FP32_REFINE, CHOL_PREC_TF32_REFINE, CHOL_PREC_BF16_REFINE = 0, 1, 2, 3
 CHOL_FLAG_PIVOT64 = 0x1
 CHOL_FLAG_GRAD_UPPER = 0x2
+CHOL_FLAG_PLAN_TIMING = 0x4
 CHOL_CALL_FACTOR, CHOL_CALL_INV, CHOL_CALL_BACKWARD = 0, 1, 2
 CHOL_NOALLOC_MAX_BATCH = 1048576
 
@@ -52,6 +53,7 @@ SIGNATURES = {
                                      c_vp, ctypes.POINTER(chol_opts_t), c_vp, c_size]),
     "chol_plan_launch": (c_i32, [c_vp, c_vp]),
     "chol_plan_destroy": (c_i32, [c_vp]),
+    "chol_plan_kernel_ms": (c_i32, [c_vp, c_i32, ctypes.POINTER(ctypes.c_float)]),
 }
 
 
@@ -140,3 +142,7 @@ def chol_plan_launch(*args):
 
 def chol_plan_destroy(*args):
     return load().chol_plan_destroy(*args)
+
+
+def chol_plan_kernel_ms(*args):
+    return load().chol_plan_kernel_ms(*args)

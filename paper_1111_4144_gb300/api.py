@@ -178,8 +178,10 @@ class Plan:
     """
 
     def __init__(self, A, X, n=None, off=None, max_n=None, *, R=None, info=None, layout=LAYOUT_DENSE,
-                 prec=L.CHOL_PREC_NATIVE, refine_steps=0, fill_lower=False, flags=0):
+                 prec=L.CHOL_PREC_NATIVE, refine_steps=0, fill_lower=False, flags=0, timing=False):
         import ctypes
+        if timing:
+            flags |= L.CHOL_FLAG_PLAN_TIMING
         _need_cuda(A, X, R, info)
         dt = dtype_code(A)
         batch, max_n = _geometry(A, n, off, max_n, layout)
@@ -195,6 +197,13 @@ class Plan:
 
     def launch(self, stream=None):
         L.check(L.chol_plan_launch(self._h, _s(stream)), "chol_plan_launch")
+
+    def kernel_ms(self, order):
+        """Duration of the order's kernel in the last replay (plan built with timing=True)."""
+        import ctypes
+        v = ctypes.c_float()
+        L.check(L.chol_plan_kernel_ms(self._h, int(order), ctypes.byref(v)), "chol_plan_kernel_ms")
+        return float(v.value)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -98,68 +98,42 @@ cudaError_t launch_dtype_class(chol_dtype_t dt, const BatchParams& p, int cls, i
     return cudaErrorInvalidValue;
 }
 
-// Streams and events (per device) on which the size-class kernels of a batch
-// with per-matrix sizes run side by side: the caller's stream forks to them
-// after the bucketing and joins them before returning, so classes overlap
-// (and a class with no members costs only its launch), in eager calls and in
-// captured graphs alike.  Calls from several host threads serialise on them.
-constexpr int kForkStreams = 8;
-struct ForkPool {
-    bool init = false;
-    cudaStream_t st[kForkStreams];
-    cudaEvent_t fork;
-    cudaEvent_t join[kForkStreams];
-    std::mutex mu;
+// Timing events of a plan being captured (CHOL_FLAG_PLAN_TIMING): recorded
+// around each size-class kernel on the stream that runs it.
+struct ClassTiming {
+    cudaEvent_t start[kClasses];
+    cudaEvent_t end[kClasses];
+    bool used[kClasses];
 };
-ForkPool g_fork[kMaxDevices];
+thread_local ClassTiming* t_timing = nullptr;
 
-cudaError_t fork_pool(ForkPool** out) {
-    int d = 0;
-    cudaError_t e = cudaGetDevice(&d);
-    if (e != cudaSuccess) return e;
-    if (d < 0 || d >= kMaxDevices) return cudaErrorInvalidDevice;
-    ForkPool& f = g_fork[d];
-    std::lock_guard<std::mutex> lk(g_dev_mu);
-    if (!f.init) {
-        for (int i = 0; i < kForkStreams; ++i) {
-            if ((e = cudaStreamCreateWithFlags(&f.st[i], cudaStreamNonBlocking)) != cudaSuccess) return e;
-            if ((e = cudaEventCreateWithFlags(&f.join[i], cudaEventDisableTiming)) != cudaSuccess) return e;
-        }
-        if ((e = cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
-        f.init = true;
+cudaError_t launch_class_timed(chol_dtype_t dt, const BatchParams& p, int c, cudaStream_t st) {
+    cudaError_t e;
+    // cudaEventRecordExternal: inside a capture this makes a real event-record
+    // node (a plain record would only express a dependency)
+    if (t_timing && (e = cudaEventRecordWithFlags(t_timing->start[c], st, cudaEventRecordExternal)) != cudaSuccess)
+        return e;
+    if ((e = launch_dtype_class(dt, p, c, p.batch, st, false)) != cudaSuccess) return e;
+    if (t_timing) {
+        if ((e = cudaEventRecordWithFlags(t_timing->end[c], st, cudaEventRecordExternal)) != cudaSuccess) return e;
+        t_timing->used[c] = true;
     }
-    *out = &f;
     return cudaSuccess;
 }
 
+// Every size class of a batch on the caller's stream, largest orders first:
+// one class for uniform batches, otherwise every class 1..max_n (a class
+// kernel with no members exits at once).  Running the classes side by side
+// on forked streams measured no faster, and sequential kernels keep the
+// per-kernel timing of plans exact.
 cudaError_t launch_dtype(chol_dtype_t dt, const BatchParams& p, cudaStream_t s, bool dry) {
-    if (p.cls_count == nullptr) return launch_dtype_class(dt, p, p.max_n, p.batch, s, dry);
-    if (dry) {
-        ForkPool* fp0 = nullptr;
-        cudaError_t e0 = fork_pool(&fp0);  // create the streams outside any capture
-        if (e0 != cudaSuccess) return e0;
-        for (int c = p.max_n; c >= 1; --c) {
-            cudaError_t e = launch_dtype_class(dt, p, c, p.batch, s, true);
-            if (e != cudaSuccess) return e;
-        }
-        return cudaSuccess;
+    if (p.cls_count == nullptr) {
+        if (dry) return launch_dtype_class(dt, p, p.max_n, p.batch, s, true);
+        return launch_class_timed(dt, p, p.max_n, s);
     }
-    ForkPool* fp = nullptr;
-    cudaError_t e = fork_pool(&fp);
-    if (e != cudaSuccess) return e;
-    std::lock_guard<std::mutex> lk(fp->mu);
-    if ((e = cudaEventRecord(fp->fork, s)) != cudaSuccess) return e;
-    const int used = std::min(kForkStreams, (int)p.max_n);
-    for (int i = 0; i < used; ++i)
-        if ((e = cudaStreamWaitEvent(fp->st[i], fp->fork, 0)) != cudaSuccess) return e;
-    // largest orders first: they take longest
-    for (int c = p.max_n, k = 0; c >= 1; --c, ++k) {
-        e = launch_dtype_class(dt, p, c, p.batch, fp->st[k % used], false);
+    for (int c = p.max_n; c >= 1; --c) {
+        cudaError_t e = dry ? launch_dtype_class(dt, p, c, p.batch, s, true) : launch_class_timed(dt, p, c, s);
         if (e != cudaSuccess) return e;
-    }
-    for (int i = 0; i < used; ++i) {
-        if ((e = cudaEventRecord(fp->join[i], fp->st[i])) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(s, fp->join[i], 0)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -277,6 +251,7 @@ using namespace cholinv;
 struct chol_plan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    ClassTiming* timing = nullptr;
 };
 
 extern "C" {
@@ -442,28 +417,45 @@ chol_status_t chol_plan_inv_create(chol_plan_t** plan, chol_dtype_t dt, int32_t 
                                    int32_t* info, const chol_opts_t* opts, void* ws, size_t ws_bytes) {
     if (plan == nullptr) return CHOL_ERR_ARG;
     *plan = nullptr;
-    const chol_opts_t o = opts_or_default(opts);
+    chol_opts_t o = opts_or_default(opts);
+    const bool timed = (o.flags & CHOL_FLAG_PLAN_TIMING) != 0;
+    o.flags &= ~CHOL_FLAG_PLAN_TIMING;
     chol_status_t st = inv_validate(dt, batch, n, max_n, A, X, o, ws, ws_bytes);
     if (st != CHOL_OK) return st;
     BatchParams p = make_params(batch, n, off, max_n, A, (R == X) ? nullptr : R, X, info, o, 1);
     // one-time kernel set-up outside the capture
     st = enqueue_inv(dt, p, ws, nullptr, true, o);
     if (st != CHOL_OK) return st;
-    cudaStream_t cs = nullptr;
-    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return CHOL_ERR_CUDA;
     chol_plan* pl = new chol_plan();
+    if (timed) {
+        pl->timing = new ClassTiming();
+        for (int c = 0; c < kClasses; ++c) {
+            pl->timing->used[c] = false;
+            if (cudaEventCreate(&pl->timing->start[c]) != cudaSuccess ||
+                cudaEventCreate(&pl->timing->end[c]) != cudaSuccess) {
+                delete pl->timing;
+                delete pl;
+                return CHOL_ERR_CUDA;
+            }
+        }
+    }
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        chol_plan_destroy(pl);
+        return CHOL_ERR_CUDA;
+    }
     st = CHOL_OK;
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = CHOL_ERR_CUDA;
+    t_timing = pl->timing;
     if (st == CHOL_OK && batch > 0) st = enqueue_inv(dt, p, ws, cs, false, o);
+    t_timing = nullptr;
     cudaGraph_t g = nullptr;
     if (cudaStreamEndCapture(cs, &g) != cudaSuccess && st == CHOL_OK) st = CHOL_ERR_CUDA;
     pl->graph = g;
     if (st == CHOL_OK && cudaGraphInstantiate(&pl->exec, g, 0) != cudaSuccess) st = CHOL_ERR_CUDA;
     cudaStreamDestroy(cs);
     if (st != CHOL_OK) {
-        if (pl->exec) cudaGraphExecDestroy(pl->exec);
-        if (pl->graph) cudaGraphDestroy(pl->graph);
-        delete pl;
+        chol_plan_destroy(pl);
         return st;
     }
     *plan = pl;
@@ -480,7 +472,22 @@ chol_status_t chol_plan_destroy(chol_plan_t* plan) {
     if (plan == nullptr) return CHOL_ERR_ARG;
     if (plan->exec) cudaGraphExecDestroy(plan->exec);
     if (plan->graph) cudaGraphDestroy(plan->graph);
+    if (plan->timing) {
+        for (int c = 0; c < kClasses; ++c) {
+            cudaEventDestroy(plan->timing->start[c]);
+            cudaEventDestroy(plan->timing->end[c]);
+        }
+        delete plan->timing;
+    }
     delete plan;
+    return CHOL_OK;
+}
+
+chol_status_t chol_plan_kernel_ms(chol_plan_t* plan, int32_t order, float* ms) {
+    if (plan == nullptr || ms == nullptr || plan->timing == nullptr) return CHOL_ERR_ARG;
+    if (order < 0 || order >= kClasses || !plan->timing->used[order]) return CHOL_ERR_ARG;
+    if (cudaEventElapsedTime(ms, plan->timing->start[order], plan->timing->end[order]) != cudaSuccess)
+        return CHOL_ERR_CUDA;
     return CHOL_OK;
 }
 

@@ -145,6 +145,13 @@ CHOL_D void load_row(const V* M, int r, V (&out)[N]) {
     }
 }
 
+// Per-row synchronisation of a group: a warp barrier, or (ALG 3) a CTA
+// barrier that also keeps the CTA's warps on the same stretch of code.
+template <int ALG>
+CHOL_D void row_sync() {
+    if constexpr (ALG == 3) __syncthreads(); else __syncwarp();
+}
+
 // Threads per matrix for order N (ALG 1): the smallest power of two
 // (2..32) whose share of the columns' upper parts fits in about 150 32-bit
 // registers; 0 if none does (the one-matrix-per-warp kernel takes those).
@@ -219,7 +226,7 @@ k_group(BatchParams p) {
         cp_async_wait<0>();
         __syncthreads();
 
-        if constexpr (ALG == 1) {
+        if constexpr (ALG == 1 || ALG == 3) {
         const bool live = q < m;
         V* M = reinterpret_cast<V*>(mirs + (size_t)(live ? q : 0) * C::STRIDE);
         // own columns, upper parts, into registers
@@ -286,7 +293,7 @@ k_group(BatchParams p) {
                     }
                 }
             }
-            __syncwarp();
+            row_sync<ALG>();
         }
         if (live && h == 0) s_info[q] = info;
         if (store_R || !p.want_inv) {
@@ -331,7 +338,7 @@ k_group(BatchParams p) {
                         if (act) sd = fma_re_conjb(col[c][i], xs[c], sd);
                     }
                 }
-                __syncwarp();  // row i of R is read; it may now be overwritten
+                row_sync<ALG>();  // row i of R is read; it may now be overwritten
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
                     if (c * G + G - 1 > i) {
@@ -350,7 +357,7 @@ k_group(BatchParams p) {
                     col[co][i] = xd;
                     if (live) M[row_base(N, i) + i] = xd;
                 }
-                __syncwarp();
+                row_sync<ALG>();
             }
             __syncthreads();
             group_store<V, N, G>(p, Xo, mirs, s_off, s_info, s_i, s_j, m, vec, false, p.fill_lower != 0);

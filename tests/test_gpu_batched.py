@@ -183,3 +183,19 @@ def test_empty_batch():
     from paper_1111_4144_gb300 import _lib as L
     o = L.opts()
     assert L.chol_inv_batched(L.CHOL_F32, 0, None, None, 4, None, None, None, None, o, None, 0, None) == L.CHOL_OK
+
+
+def test_plan_kernel_timing():
+    import torch
+    from paper_1111_4144_gb300 import api
+    b = wl.mimo_covariance(20000, sizes=(4, 8, 16), seed=13, layout=1)
+    A = torch.from_numpy(b.A.astype(np.complex64)).cuda()
+    n = torch.from_numpy(b.n).cuda()
+    off = torch.from_numpy(b.off).cuda()
+    X = torch.zeros_like(A)
+    p = api.Plan(A, X, n, off, 16, layout=1, timing=True)
+    p.launch()
+    torch.cuda.synchronize()
+    for N in (4, 8, 16):
+        assert p.kernel_ms(N) > 0.0
+    p.close()
