@@ -222,6 +222,9 @@ def run_ours(args, rank, world, local_rank):
     off = torch.from_numpy(b.off).to(dev)
     X = torch.zeros_like(A)
     stream = torch.cuda.Stream(device=dev)
+    # pick the fastest kernel variant of each order on this GPU (set-up, untimed)
+    tuned = api.autotune(torch.complex64, max(sizes), layout=api.LAYOUT_PACKED, batch=65536, stream=stream)
+    torch.cuda.synchronize()
     if args.uniform:
         plan = api.Plan(A, X, None, None, sizes[0], layout=api.LAYOUT_PACKED, timing=True)
         kernels_per_step = 1
@@ -351,6 +354,7 @@ def run_ours(args, rank, world, local_rank):
                 "vs_baseline": None, "dtype": "c64 (fp32 arithmetic)", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "batch_per_gpu": b.batch, "sizes": list(SIZES), "sigma2": SIGMA2,
                            "layout": "packed_upper", "launch": "cuda_graph",
+                           "autotuned_variants": {str(k): v for k, v in tuned.items()},
                            "l2": "inputs larger than L2 (509 MB in, 509 MB out per step)"},
                 "roofline": {"bound": "hbm", "achieved": dom_gbs, "peak": peaks.get("hbm_gbs", FALLBACK_HBM_GBS),
                              "unit": "GB/s", "frac": dom_gbs / peaks.get("hbm_gbs", FALLBACK_HBM_GBS),

@@ -214,6 +214,27 @@ const char* chol_status_string(chol_status_t status);
  * current device (CHOL_OK if no kernel reported an error). */
 chol_status_t chol_last_device_error(void* stream);
 
+/*
+ * Autotuning (not in the paper).  Orders up to 32 have more than one
+ * compiled kernel variant (one matrix per thread vs. G threads per matrix,
+ * or G vs. 2G threads); which is fastest depends on the GPU.
+ * chol_autotune times every variant of every order 1..max_n for dtype dt and
+ * layout on a synthetic batch of `batch` matrices on `stream` and keeps the
+ * fastest in a per-process table that all later calls use (plans capture
+ * the variant current at creation).  It allocates and frees device memory
+ * and synchronises the stream, so it is a set-up call, not for the hot path
+ * or a stream capture.  cache_path (may be NULL) receives the choices as a
+ * small text file keyed by GPU name; chol_tune_load reads such a file back.
+ * chol_tune_variants / chol_tune_get / chol_tune_set inspect or pin the
+ * table (variant 0 is the compiled-in default).
+ */
+chol_status_t chol_autotune(chol_dtype_t dt, int32_t max_n, int32_t layout, int32_t batch, const char* cache_path,
+                            void* stream);
+chol_status_t chol_tune_load(const char* cache_path);
+int32_t chol_tune_variants(chol_dtype_t dt, int32_t order);
+int32_t chol_tune_get(chol_dtype_t dt, int32_t order);
+chol_status_t chol_tune_set(chol_dtype_t dt, int32_t order, int32_t variant);
+
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int32_t chol_version(void);
 

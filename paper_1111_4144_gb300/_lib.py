@@ -54,6 +54,11 @@ SIGNATURES = {
     "chol_plan_launch": (c_i32, [c_vp, c_vp]),
     "chol_plan_destroy": (c_i32, [c_vp]),
     "chol_plan_kernel_ms": (c_i32, [c_vp, c_i32, ctypes.POINTER(ctypes.c_float)]),
+    "chol_autotune": (c_i32, [c_i32, c_i32, c_i32, c_i32, ctypes.c_char_p, c_vp]),
+    "chol_tune_load": (c_i32, [ctypes.c_char_p]),
+    "chol_tune_variants": (c_i32, [c_i32, c_i32]),
+    "chol_tune_get": (c_i32, [c_i32, c_i32]),
+    "chol_tune_set": (c_i32, [c_i32, c_i32, c_i32]),
 }
 
 
@@ -146,3 +151,23 @@ def chol_plan_destroy(*args):
 
 def chol_plan_kernel_ms(*args):
     return load().chol_plan_kernel_ms(*args)
+
+
+def chol_autotune(*args):
+    return load().chol_autotune(*args)
+
+
+def chol_tune_load(*args):
+    return load().chol_tune_load(*args)
+
+
+def chol_tune_variants(*args):
+    return load().chol_tune_variants(*args)
+
+
+def chol_tune_get(*args):
+    return load().chol_tune_get(*args)
+
+
+def chol_tune_set(*args):
+    return load().chol_tune_set(*args)

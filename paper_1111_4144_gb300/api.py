@@ -166,6 +166,16 @@ def inv_autograd(A, prec=L.CHOL_PREC_NATIVE, refine_steps=0):
     return CholInv.apply(A, prec, refine_steps)
 
 
+def autotune(dtype, max_n, *, layout=LAYOUT_PACKED, batch=65536, cache_path=None, stream=None):
+    """Time every kernel variant of orders 1..max_n on this GPU and keep the
+    fastest (chol_autotune).  Returns {order: chosen variant} for the orders
+    that have a choice."""
+    dt = _DT[dtype]
+    path = cache_path.encode() if cache_path else None
+    L.check(L.chol_autotune(dt, int(max_n), int(layout), int(batch), path, _s(stream)), "chol_autotune")
+    return {n: L.chol_tune_get(dt, n) for n in range(1, int(max_n) + 1) if L.chol_tune_variants(dt, n) > 1}
+
+
 def last_device_error(stream=None) -> int:
     return L.chol_last_device_error(_s(stream))
 

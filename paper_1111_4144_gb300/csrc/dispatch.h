@@ -21,6 +21,15 @@ cudaError_t launch_class_f64(const BatchParams& p, int cls, int upper, cudaStrea
 cudaError_t launch_class_c64(const BatchParams& p, int cls, int upper, cudaStream_t s, bool dry);
 cudaError_t launch_class_c128(const BatchParams& p, int cls, int upper, cudaStream_t s, bool dry);
 
+// Number of kernel variants of an order (for the autotuner).
+int class_variants_f32(int cls);
+int class_variants_f64(int cls);
+int class_variants_c64(int cls);
+int class_variants_c128(int cls);
+
+// The tuning table (tune.cu): the variant to launch for (dtype, order); 0 by default.
+int variant_of(int dtype, int order);
+
 // Refinement pass (refine.cu): FP32 / complex64 only.  steps Newton-Schulz
 // steps on every matrix, or (automatic) one step where max_i a_ii x_ii > 4096.
 cudaError_t launch_refine(int dtype, const BatchParams& p, int steps, int automatic, cudaStream_t s, bool dry);

@@ -1,0 +1,12 @@
+// Batched kernels for element type cpx<double>, matrix orders 1..14.
+#include "launch.cuh"
+
+namespace cholinv {
+
+cudaError_t launch_class_c128_lo(const BatchParams& p, int cls, int upper, cudaStream_t s, bool dry) {
+    return launch_class_half<cpx<double>, true>(p, cls, upper, s, dry);
+}
+
+int class_variants_c128_lo(int cls) { return class_variants_half<cpx<double>, true>(cls); }
+
+}  // namespace cholinv

@@ -85,29 +85,86 @@ static cudaError_t launch_group(const BatchParams& p, int upper_count, cudaStrea
     return cudaGetLastError();
 }
 
+// Kernel variants of one order, chosen at run time by the autotuner
+// (tune.cu) through variant_of(); variant 0 is the compiled-in default.
+//   lane orders  : 0 lane; 1 group G=2 (orders >= 8 only)
+//   group orders : 0 group G0; 1 group 2*G0 (when 2*G0 <= 32)
+//   warp orders  : 0 warp
 template <typename V, int N>
-static cudaError_t launch_fixed(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
+constexpr int num_variants() {
     constexpr int kind = kernel_kind<V, N>();
-    if constexpr (kind == 0) return launch_lane<V, N>(p, upper_count, s, dry);
-    else if constexpr (kind == 1) return launch_group<V, N, group_size<V, N>(), 1>(p, upper_count, s, dry);
-    else return launch_warp<V>(p, N, upper_count, s, dry);
+    if constexpr (kind == 0) return (N >= 8 && N <= kGroupMaxN && group_size<V, N>() == 2) ? 2 : 1;
+    else if constexpr (kind == 1) return group_size<V, N>() * 2 <= 32 ? 2 : 1;
+    else return 1;
 }
 
 template <typename V, int N>
-static cudaError_t launch_fixed_upto(const BatchParams& p, int cls, int upper_count, cudaStream_t s, bool dry) {
-    if constexpr (N == 0) {
-        return cudaErrorInvalidValue;
+static cudaError_t launch_fixed(const BatchParams& p, int variant, int upper_count, cudaStream_t s, bool dry) {
+    constexpr int kind = kernel_kind<V, N>();
+    if constexpr (kind == 0) {
+        if constexpr (num_variants<V, N>() > 1)
+            if (variant == 1) return launch_group<V, N, 2, 1>(p, upper_count, s, dry);
+        return launch_lane<V, N>(p, upper_count, s, dry);
+    } else if constexpr (kind == 1) {
+        constexpr int G0 = group_size<V, N>();
+        if constexpr (num_variants<V, N>() > 1)
+            if (variant == 1) return launch_group<V, N, (G0 * 2 <= 32 ? G0 * 2 : G0), 1>(p, upper_count, s, dry);
+        return launch_group<V, N, G0, 1>(p, upper_count, s, dry);
     } else {
-        if (cls == N) return launch_fixed<V, N>(p, upper_count, s, dry);
-        return launch_fixed_upto<V, N - 1>(p, cls, upper_count, s, dry);
+        return launch_warp<V>(p, N, upper_count, s, dry);
     }
 }
 
-// Launch the kernel of one size class (cls) whose member count is at most upper_count.
-template <typename V>
-cudaError_t launch_class(const BatchParams& p, int cls, int upper_count, cudaStream_t s, bool dry) {
-    if (cls <= kGroupMaxN) return launch_fixed_upto<V, kGroupMaxN>(p, cls, upper_count, s, dry);
-    return launch_warp<V>(p, cls, upper_count, s, dry);
+// Launch class `cls` if it lies in [LO, N] (compile-time recursion).
+template <typename V, int LO, int N>
+static cudaError_t launch_fixed_range(const BatchParams& p, int cls, int variant, int upper_count, cudaStream_t s,
+                                      bool dry) {
+    if constexpr (N < LO) {
+        return cudaErrorInvalidValue;
+    } else {
+        if (cls == N) return launch_fixed<V, N>(p, variant, upper_count, s, dry);
+        return launch_fixed_range<V, LO, N - 1>(p, cls, variant, upper_count, s, dry);
+    }
+}
+
+template <typename V, int LO, int N>
+static int variants_range(int cls) {
+    if constexpr (N < LO) {
+        return 1;
+    } else {
+        if (cls == N) return num_variants<V, N>();
+        return variants_range<V, LO, N - 1>(cls);
+    }
+}
+
+template <typename V> constexpr int dtype_code();
+template <> constexpr int dtype_code<float>() { return CHOL_F32; }
+template <> constexpr int dtype_code<double>() { return CHOL_F64; }
+template <> constexpr int dtype_code<cpx<float>>() { return CHOL_C64; }
+template <> constexpr int dtype_code<cpx<double>>() { return CHOL_C128; }
+
+// Orders are split over two translation units per element type (compiled
+// in parallel): [1, kSplitN] and (kSplitN, kGroupMaxN] plus the warp kernel.
+constexpr int kSplitN = 14;
+
+// Launch the kernel of one size class (cls) whose member count is at most
+// upper_count, in the variant the tuning table holds for it; LOW selects
+// which half of the orders this translation unit instantiates.
+template <typename V, bool LOW>
+cudaError_t launch_class_half(const BatchParams& p, int cls, int upper_count, cudaStream_t s, bool dry) {
+    const int v = variant_of(dtype_code<V>(), cls);
+    if constexpr (LOW) {
+        return launch_fixed_range<V, 1, kSplitN>(p, cls, v, upper_count, s, dry);
+    } else {
+        if (cls <= kGroupMaxN) return launch_fixed_range<V, kSplitN + 1, kGroupMaxN>(p, cls, v, upper_count, s, dry);
+        return launch_warp<V>(p, cls, upper_count, s, dry);
+    }
+}
+
+template <typename V, bool LOW>
+int class_variants_half(int cls) {
+    if constexpr (LOW) return variants_range<V, 1, kSplitN>(cls);
+    else return cls <= kGroupMaxN ? variants_range<V, kSplitN + 1, kGroupMaxN>(cls) : 1;
 }
 
 }  // namespace cholinv

@@ -1,0 +1,225 @@
+// Autotuner: for every order with more than one compiled kernel variant
+// (one matrix per thread vs. G threads per matrix, or G vs. 2G), time each
+// variant on a synthetic batch on this GPU and keep the fastest in a table
+// that the batched launcher consults.  The table can be written to and read
+// from a small text file so that a later process skips the timing.
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "batched.cuh"
+#include "dispatch.h"
+
+namespace cholinv {
+
+namespace {
+std::atomic<int> g_variant[4][kClasses];  // zero-initialised: the compiled-in default
+std::mutex g_tune_mu;
+
+int variants(int dt, int n) {
+    switch (dt) {
+        case CHOL_F32: return class_variants_f32(n);
+        case CHOL_F64: return class_variants_f64(n);
+        case CHOL_C64: return class_variants_c64(n);
+        case CHOL_C128: return class_variants_c128(n);
+    }
+    return 1;
+}
+
+cudaError_t launch_one(int dt, const BatchParams& p, int n, cudaStream_t s) {
+    switch (dt) {
+        case CHOL_F32: return launch_class_f32(p, n, p.batch, s, false);
+        case CHOL_F64: return launch_class_f64(p, n, p.batch, s, false);
+        case CHOL_C64: return launch_class_c64(p, n, p.batch, s, false);
+        case CHOL_C128: return launch_class_c128(p, n, p.batch, s, false);
+    }
+    return cudaErrorInvalidValue;
+}
+
+size_t elem_bytes(int dt) { return dt == CHOL_F32 ? 4 : dt == CHOL_C128 ? 16 : 8; }
+
+// Synthetic Hermitian positive-definite matrices for timing only:
+// a_ii = n + 1, off-diagonal entries hashed into [-0.5, 0.5) (diagonally dominant).
+template <typename V>
+__global__ void k_tune_gen_t(V* A, int64_t count, int n, int layout) {
+    const int T = layout ? n * (n + 1) / 2 : n * n;
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < count; f += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(f % T);
+        int i, j;
+        if (layout) {
+            i = 0;
+            while (pidx(n, i + 1, i + 1) <= e && i + 1 < n) ++i;
+            j = e - pidx(n, i, i) + i;
+        } else {
+            i = e / n;
+            j = e % n;
+        }
+        unsigned h = (unsigned)(f * 2654435761u) ^ 0x9e3779b9u;
+        h ^= h >> 15; h *= 0x2c1b3c6du; h ^= h >> 12;
+        using R = typename traits<V>::real;
+        const R re = (i == j) ? R(n + 1) : R((h & 0xffff) / 65536.f - 0.5f);
+        const R im = (i == j) ? R(0) : R((h >> 16) / 65536.f - 0.5f);
+        if constexpr (traits<V>::cplx) A[f] = V{re, im}; else A[f] = re;
+    }
+}
+
+cudaError_t gen(int dt, void* A, int64_t count, int n, int layout, cudaStream_t s) {
+    const int grid = 1024, th = 256;
+    switch (dt) {
+        case CHOL_F32: k_tune_gen_t<float><<<grid, th, 0, s>>>(static_cast<float*>(A), count, n, layout); break;
+        case CHOL_F64: k_tune_gen_t<double><<<grid, th, 0, s>>>(static_cast<double*>(A), count, n, layout); break;
+        case CHOL_C64: k_tune_gen_t<cpx<float>><<<grid, th, 0, s>>>(static_cast<cpx<float>*>(A), count, n, layout); break;
+        case CHOL_C128: k_tune_gen_t<cpx<double>><<<grid, th, 0, s>>>(static_cast<cpx<double>*>(A), count, n, layout); break;
+    }
+    return cudaGetLastError();
+}
+
+std::string device_tag() {
+    int d = 0;
+    cudaGetDevice(&d);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, d) != cudaSuccess) return "unknown";
+    std::string s = prop.name;
+    for (auto& c : s)
+        if (c == ' ') c = '_';
+    return s + "_sm" + std::to_string(prop.multiProcessorCount);
+}
+
+}  // namespace
+
+int variant_of(int dtype, int order) {
+    if (dtype < 0 || dtype > 3 || order < 0 || order >= kClasses) return 0;
+    return g_variant[dtype][order].load(std::memory_order_relaxed);
+}
+
+}  // namespace cholinv
+
+using namespace cholinv;
+
+extern "C" {
+
+int32_t chol_tune_variants(chol_dtype_t dt, int32_t order) {
+    if (dt < CHOL_F32 || dt > CHOL_C128 || order < 1 || order >= kClasses) return 0;
+    return variants(dt, order);
+}
+
+int32_t chol_tune_get(chol_dtype_t dt, int32_t order) { return variant_of(dt, order); }
+
+chol_status_t chol_tune_set(chol_dtype_t dt, int32_t order, int32_t variant) {
+    if (dt < CHOL_F32 || dt > CHOL_C128 || order < 1 || order >= kClasses) return CHOL_ERR_ARG;
+    if (variant < 0 || variant >= variants(dt, order)) return CHOL_ERR_ARG;
+    g_variant[dt][order].store(variant, std::memory_order_relaxed);
+    return CHOL_OK;
+}
+
+chol_status_t chol_autotune(chol_dtype_t dt, int32_t max_n, int32_t layout, int32_t batch, const char* cache_path,
+                            void* stream) {
+    if (dt < CHOL_F32 || dt > CHOL_C128 || max_n < 1 || batch < 1 || (layout != 0 && layout != 1))
+        return CHOL_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int top = std::min<int>(max_n, kClasses - 1);
+    const size_t es = elem_bytes(dt);
+    const int64_t per = layout ? (int64_t)top * (top + 1) / 2 : (int64_t)top * top;
+    void *A = nullptr, *X = nullptr;
+    if (cudaMalloc(&A, (size_t)batch * per * es) != cudaSuccess) return CHOL_ERR_CUDA;
+    if (cudaMalloc(&X, (size_t)batch * per * es) != cudaSuccess) { cudaFree(A); return CHOL_ERR_CUDA; }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    chol_status_t st = CHOL_OK;
+    std::vector<std::string> lines;
+    for (int n = 1; n <= top && st == CHOL_OK; ++n) {
+        const int nv = variants(dt, n);
+        if (nv <= 1) continue;
+        const int64_t count = (int64_t)batch * (layout ? (int64_t)n * (n + 1) / 2 : (int64_t)n * n);
+        if (gen(dt, A, count, n, layout, s) != cudaSuccess) { st = CHOL_ERR_CUDA; break; }
+        BatchParams p;
+        std::memset(&p, 0, sizeof(p));
+        p.batch = batch;
+        p.max_n = n;
+        p.layout = layout;
+        p.want_inv = 1;
+        p.A = A;
+        p.X = X;
+        float best_ms = 1e30f;
+        int best = 0;
+        std::string times;
+        for (int v = 0; v < nv; ++v) {
+            g_variant[dt][n].store(v);
+            for (int w = 0; w < 2; ++w)
+                if (launch_one(dt, p, n, s) != cudaSuccess) st = CHOL_ERR_CUDA;
+            cudaEventRecord(e0, s);
+            const int reps = 5;
+            for (int r = 0; r < reps; ++r)
+                if (launch_one(dt, p, n, s) != cudaSuccess) st = CHOL_ERR_CUDA;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = CHOL_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            times += " " + std::to_string(ms * 1000.f);
+            if (ms < best_ms) { best_ms = ms; best = v; }
+        }
+        g_variant[dt][n].store(best);
+        lines.push_back(std::to_string((int)dt) + " " + std::to_string(n) + " " + std::to_string(best) + times);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(A);
+    cudaFree(X);
+    if (st == CHOL_OK && cache_path && cache_path[0]) {
+        // keep other devices' / dtypes' entries already in the file
+        std::vector<std::string> keep;
+        const std::string tag = device_tag();
+        if (FILE* f = std::fopen(cache_path, "r")) {
+            char buf[512];
+            std::string cur;
+            while (std::fgets(buf, sizeof(buf), f)) {
+                std::string l(buf);
+                if (!l.empty() && l.back() == '\n') l.pop_back();
+                if (l.rfind("device ", 0) == 0) { cur = l.substr(7); keep.push_back(l); continue; }
+                int d = -1;
+                if (cur == tag && std::sscanf(l.c_str(), "%d", &d) == 1 && d == (int)dt) continue;
+                keep.push_back(l);
+            }
+            std::fclose(f);
+        }
+        if (FILE* f = std::fopen(cache_path, "w")) {
+            for (auto& l : keep) std::fprintf(f, "%s\n", l.c_str());
+            std::fprintf(f, "device %s\n", tag.c_str());
+            for (auto& l : lines) std::fprintf(f, "%s\n", l.c_str());
+            std::fclose(f);
+        } else {
+            st = CHOL_ERR_ARG;
+        }
+    }
+    return st;
+}
+
+chol_status_t chol_tune_load(const char* cache_path) {
+    if (!cache_path) return CHOL_ERR_ARG;
+    FILE* f = std::fopen(cache_path, "r");
+    if (!f) return CHOL_ERR_ARG;
+    const std::string tag = device_tag();
+    char buf[512];
+    std::string cur;
+    int loaded = 0;
+    while (std::fgets(buf, sizeof(buf), f)) {
+        std::string l(buf);
+        if (!l.empty() && l.back() == '\n') l.pop_back();
+        if (l.rfind("device ", 0) == 0) { cur = l.substr(7); continue; }
+        int d, n, v;
+        if (cur == tag && std::sscanf(l.c_str(), "%d %d %d", &d, &n, &v) == 3 &&
+            chol_tune_set(static_cast<chol_dtype_t>(d), n, v) == CHOL_OK)
+            ++loaded;
+    }
+    std::fclose(f);
+    return loaded > 0 ? CHOL_OK : CHOL_ERR_ARG;
+}
+
+}  // extern "C"

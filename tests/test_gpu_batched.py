@@ -199,3 +199,42 @@ def test_plan_kernel_timing():
     for N in (4, 8, 16):
         assert p.kernel_ms(N) > 0.0
     p.close()
+
+
+@pytest.mark.parametrize("tag", ["c64", "f32", "c128"])
+def test_every_kernel_variant_matches_oracle(orc, tag):
+    """Each compiled variant of an order (lane / group G / group 2G) gives results
+    within tolerance; the tuning table is restored afterwards."""
+    from paper_1111_4144_gb300 import _lib as L
+    dt = {"f32": L.CHOL_F32, "c64": L.CHOL_C64, "c128": L.CHOL_C128}[tag]
+    try:
+        for N in (8, 9, 12, 16, 20, 32):
+            nv = L.chol_tune_variants(dt, N)
+            assert nv >= 1
+            b = make_batch(tag, N, 150, 1, seed=300 + N)
+            Ro, Xo, info_o, A_wide = oracle_inv(orc, b, tag)
+            for v in range(nv):
+                assert L.chol_tune_set(dt, N, v) == L.CHOL_OK
+                X, info, _ = run_inv(b, tag, mixed=False)
+                assert np.array_equal(info, info_o)
+                check_errors(tag, b, A_wide, upper_errors(b, X, Xo), f"X (N={N}, variant {v})")
+            assert L.chol_tune_set(dt, N, nv) == L.CHOL_ERR_ARG
+    finally:
+        for N in range(1, 65):
+            L.chol_tune_set(dt, N, 0)
+
+
+def test_autotune_and_cache(tmp_path):
+    from paper_1111_4144_gb300 import _lib as L, api
+    import torch
+    path = str(tmp_path / "tune.txt")
+    chosen = api.autotune(torch.complex64, 16, layout=1, batch=4096, cache_path=path)
+    assert set(chosen) == {n for n in range(1, 17) if L.chol_tune_variants(L.CHOL_C64, n) > 1}
+    text = open(path).read()
+    assert text.startswith("device ")
+    for n in chosen:
+        L.chol_tune_set(L.CHOL_C64, n, 0)
+    assert L.chol_tune_load(path.encode()) == L.CHOL_OK
+    assert {n: L.chol_tune_get(L.CHOL_C64, n) for n in chosen} == chosen
+    for n in chosen:
+        L.chol_tune_set(L.CHOL_C64, n, 0)
