@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--sizes", default=",".join(map(str, SIZES)), help="matrix orders, equal shares")
     ap.add_argument("--uniform", action="store_true",
                     help="profiling case: one order only (first of --sizes), no per-matrix sizes")
+    ap.add_argument("--blocked", type=int, default=0,
+                    help="time the blocked path instead: one FP32 matrix of this order, lambda log-spaced over "
+                         "[1, 1e4], tensor-core products (prints one JSON line)")
+    ap.add_argument("--blocked-prec", default="tf32", choices=["tf32", "fp32", "fp64"])
     return ap.parse_args()
 
 
@@ -202,6 +206,46 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t_start}
     print(json.dumps(line), flush=True)
+
+
+def run_blocked(args, local_rank):
+    """One large matrix through the blocked path (the large-order workload)."""
+    import torch
+    from paper_1111_4144_gb300 import _lib as L, api
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    N = args.blocked
+    dt = torch.float64 if args.blocked_prec == "fp64" else torch.float32
+    # A = Q diag(lambda) Q^T with Q from a Householder QR of a Gaussian, lambda log-spaced over [1, 1e4]
+    if N <= 8192:
+        from paper_1111_4144_gb300 import workloads as wl
+        A = torch.from_numpy(wl.log_spaced(N, decades=4.0, seed=1004).A.reshape(1, N, N)).to(dev).to(dt)
+    else:
+        g = torch.Generator(device=dev).manual_seed(1004)
+        Q, _ = torch.linalg.qr(torch.randn(N, N, dtype=torch.float64, device=dev, generator=g))
+        lam = 10.0 ** (4.0 * torch.arange(N, dtype=torch.float64, device=dev) / max(N - 1, 1))
+        A64 = (Q * lam) @ Q.T
+        A = ((A64 + A64.T) / 2).to(dt).reshape(1, N, N)
+        del Q, A64
+    A = A.contiguous()
+    kw = {}
+    if args.blocked_prec == "tf32":
+        kw = dict(prec=L.CHOL_PREC_TF32_REFINE, refine_steps=0)
+    X, info = api.inv(A, **kw)
+    torch.cuda.synchronize()
+    for _ in range(max(args.warmup - 1, 0)):
+        api.inv(A, X=X, info=info, **kw)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        api.inv(A, X=X, info=info, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"blocked_order": N, "prec": args.blocked_prec, "ms_per_inverse": ms,
+                      "alg_tflops": N ** 3 / (ms / 1e3) / 1e12, "info": int(info.item()),
+                      "device_error": L.chol_last_device_error(None)}), flush=True)
 
 
 def run_ours(args, rank, world, local_rank):
@@ -383,6 +427,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.blocked:
+        run_blocked(args, local_rank)
         return
     if world > 1:
         import torch

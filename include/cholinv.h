@@ -95,7 +95,10 @@ typedef enum {
     CHOL_PREC_NATIVE = 0,       /* all arithmetic in the dtype's precision */
     CHOL_PREC_FP32_REFINE = 1,  /* F32/C64: FP32 body, then refine_steps Newton-Schulz steps
                                    X <- X + X (I - A X) with the residual accumulated in FP64 */
-    CHOL_PREC_TF32_REFINE = 2,  /* blocked large-N path: TF32 tensor-core products */
+    CHOL_PREC_TF32_REFINE = 2,  /* blocked large-N path (F32): the trailing updates and the inverse-assembly
+                                   products on tcgen05 tensor cores as error-corrected TF32 (three TF32
+                                   products per FP32 product, FP32-level accuracy), then refine_steps
+                                   refinement steps as for CHOL_PREC_FP32_REFINE */
     CHOL_PREC_BF16_REFINE = 3   /* blocked large-N path: BF16 tensor-core products */
 } chol_prec_t;
 
@@ -105,6 +108,8 @@ typedef enum {
                                      the independent parameters (see chol_inv_backward) */
 #define CHOL_FLAG_PLAN_TIMING 0x4 /* chol_plan_inv_create only: record timing events around each size-class
                                      kernel (see chol_plan_kernel_ms) */
+#define CHOL_FLAG_TF32_SINGLE 0x8 /* CHOL_PREC_TF32_REFINE: single-pass TF32 products (11 significant bits)
+                                     instead of the three-product split; only for kappa * 2^-11 << 1 */
 
 typedef struct {
     int32_t prec;          /* chol_prec_t */

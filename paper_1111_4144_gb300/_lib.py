@@ -26,6 +26,7 @@ CHOL_PREC_NATIVE, CHOL_PREC_FP32_REFINE, CHOL_PREC_TF32_REFINE, CHOL_PREC_BF16_R
 CHOL_FLAG_PIVOT64 = 0x1
 CHOL_FLAG_GRAD_UPPER = 0x2
 CHOL_FLAG_PLAN_TIMING = 0x4
+CHOL_FLAG_TF32_SINGLE = 0x8
 CHOL_CALL_FACTOR, CHOL_CALL_INV, CHOL_CALL_BACKWARD = 0, 1, 2
 CHOL_NOALLOC_MAX_BATCH = 1048576
 

@@ -82,6 +82,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.replace(tmp, LIB)
     with open(stamp, "w") as f:
         f.write(dig)
+    shutil.rmtree(objdir, ignore_errors=True)  # objects are not needed once linked
     return LIB
 
 

@@ -218,11 +218,12 @@ chol_status_t blocked_validate(chol_dtype_t dt, int32_t batch, const int32_t* n,
     if (o.layout != 0 && o.layout != 1) return CHOL_ERR_ARG;
     if (o.prec < CHOL_PREC_NATIVE || o.prec > CHOL_PREC_BF16_REFINE) return CHOL_ERR_ARG;
     if (o.refine_steps < -1 || o.refine_steps > 2) return CHOL_ERR_ARG;
-    if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER)) return CHOL_ERR_ARG;
+    if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER | CHOL_FLAG_TF32_SINGLE)) return CHOL_ERR_ARG;
     if (n != nullptr || off != nullptr || o.layout != 0) return CHOL_ERR_UNSUPPORTED;
     if (dt != CHOL_F32 && dt != CHOL_F64) return CHOL_ERR_UNSUPPORTED;
-    if (o.prec == CHOL_PREC_TF32_REFINE || o.prec == CHOL_PREC_BF16_REFINE) return CHOL_ERR_UNSUPPORTED;
-    if (o.prec == CHOL_PREC_FP32_REFINE && dt != CHOL_F32) return CHOL_ERR_UNSUPPORTED;
+    if (o.prec == CHOL_PREC_BF16_REFINE) return CHOL_ERR_UNSUPPORTED;
+    if ((o.prec == CHOL_PREC_FP32_REFINE || o.prec == CHOL_PREC_TF32_REFINE) && dt != CHOL_F32)
+        return CHOL_ERR_UNSUPPORTED;
     if (max_n > 1 << 16) return CHOL_ERR_UNSUPPORTED;
     if (batch > 0 && (ws == nullptr || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256 != 0))
         return CHOL_ERR_WORKSPACE;
@@ -230,8 +231,19 @@ chol_status_t blocked_validate(chol_dtype_t dt, int32_t batch, const int32_t* n,
 }
 
 int blocked_refine_steps(const chol_opts_t& o) {
-    if (o.prec != CHOL_PREC_FP32_REFINE) return 0;
+    if (o.prec != CHOL_PREC_FP32_REFINE && o.prec != CHOL_PREC_TF32_REFINE) return 0;
     return o.refine_steps < 0 ? 1 : o.refine_steps;
+}
+
+// Tensor-core mode of the blocked products (see blocked_run).
+int blocked_tc(const chol_opts_t& o) {
+    if (o.prec != CHOL_PREC_TF32_REFINE) return 0;
+    return (o.flags & CHOL_FLAG_TF32_SINGLE) ? 1 : 2;
+}
+
+int* device_error_word() {
+    DevState* ds = nullptr;
+    return dev_state(&ds) == cudaSuccess ? ds->err : nullptr;
 }
 
 }  // namespace
@@ -266,8 +278,8 @@ chol_status_t chol_factor_batched(chol_dtype_t dt, int32_t batch, const int32_t*
         if (sb != CHOL_OK || batch == 0) return sb;
         if (A == nullptr || R == nullptr) return CHOL_ERR_ARG;
         // the factor is formed in R itself (R is the working storage)
-        return blocked_run(dt, batch, max_n, A, nullptr, R, info, o.flags & CHOL_FLAG_PIVOT64, 0, 0, ws,
-                           static_cast<cudaStream_t>(stream));
+        return blocked_run(dt, batch, max_n, A, nullptr, R, info, o.flags & CHOL_FLAG_PIVOT64, 0, 0, blocked_tc(o),
+                           device_error_word(), ws, static_cast<cudaStream_t>(stream));
     }
     chol_status_t st = check_common(dt, batch, max_n, o);
     if (st != CHOL_OK) return st;
@@ -290,8 +302,8 @@ chol_status_t chol_inv_batched(chol_dtype_t dt, int32_t batch, const int32_t* n,
         if (sb != CHOL_OK || batch == 0) return sb;
         if (A == nullptr || X == nullptr) return CHOL_ERR_ARG;
         if (X == A || (R != nullptr && (R == A || R == X))) return CHOL_ERR_ARG;
-        return blocked_run(dt, batch, max_n, A, R, X, info, o.flags & CHOL_FLAG_PIVOT64, rs, 1, ws,
-                           static_cast<cudaStream_t>(stream));
+        return blocked_run(dt, batch, max_n, A, R, X, info, o.flags & CHOL_FLAG_PIVOT64, rs, 1, blocked_tc(o),
+                           device_error_word(), ws, static_cast<cudaStream_t>(stream));
     }
     chol_status_t st = inv_validate(dt, batch, n, max_n, A, X, o, ws, ws_bytes);
     if (st != CHOL_OK || batch == 0) return st;

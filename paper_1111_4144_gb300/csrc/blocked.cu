@@ -23,6 +23,7 @@
 #include "batched.cuh"
 #include "blocked.h"
 #include "dispatch.h"
+#include "umma.cuh"
 
 namespace cholinv {
 
@@ -249,6 +250,24 @@ __global__ void k_put_panel(T* X, int64_t ldx, int r0, int c0, int b, int m, con
     }
 }
 
+// Copy the transpose of an m x b panel Pt into X at (r0, c0) (X[r0+i][c0+j] = Pt[j][i]).
+__global__ void k_put_panel_t(float* X, int64_t ldx, int r0, int c0, int b, int m, const float* Pt, const int* failed) {
+    if (*failed) return;
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < (int64_t)b * m;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(f / m), j = (int)(f % m);
+        X[(int64_t)(r0 + i) * ldx + c0 + j] = Pt[(int64_t)j * b + i];
+    }
+}
+
+// A tensor-core GEMM gave up waiting: report it, and make the result NaN.
+__global__ void k_report_umma(const int* umma_err, int* failed, int* err_word) {
+    if (*umma_err) {
+        atomicCAS(err_word, 0, CHOL_ERR_TIMEOUT);
+        *failed = 1;
+    }
+}
+
 // X (n x n) <- upper triangle of A (layout dense, ld n); lower part cleared.
 template <typename T>
 __global__ void k_load_upper(T* X, const T* A, int n) {
@@ -361,6 +380,98 @@ cudaError_t gemm(int M, int N, int K, Tacc alpha, const Tin* A, int64_t lda, con
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Tensor-core GEMM host side: TMA tensor maps and launches.
+// ---------------------------------------------------------------------------
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// Row-major FP32 matrix (rows x cols, leading dimension ld elements) as a 2-D
+// tensor map with 32 x 128 boxes and the 128-byte swizzle; entries outside
+// the matrix read as zero.
+bool make_map(CUtensorMap* m, const float* base, int64_t rows, int64_t cols, int64_t ld) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) || (ld * 4) % 16) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+    cuuint32_t box[2] = {(cuuint32_t)umma::BK, (cuuint32_t)umma::BM};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int STAGES, int SPLIT3>
+cudaError_t umma_setup() {
+    static std::once_flag once;
+    static cudaError_t e = cudaSuccess;
+    std::call_once(once, [] {
+        e = cudaFuncSetAttribute(umma::k_umma_gemm<STAGES, SPLIT3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)umma::smem_bytes<STAGES, SPLIT3>());
+    });
+    return e;
+}
+
+// C = alpha A B^T + beta C on the tensor cores (A: M x K at map coordinates
+// (ax, ay); B: N x K at (bx, by)); split-K through `partial` when the tile
+// grid alone would leave most of the GPU idle.
+cudaError_t umma_gemm(int M, int N, int K, float alpha, const CUtensorMap& ma, int ax, int ay, const CUtensorMap& mb,
+                      int bx, int by, float beta, float* C, int64_t ldc, int upper, float* partial, size_t partial_elems,
+                      int split3, int* err, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    cudaError_t e = split3 ? umma_setup<3, 1>() : umma_setup<4, 0>();
+    if (e != cudaSuccess) return e;
+    const int sms = device_info().sms;
+    dim3 grid((N + umma::BN - 1) / umma::BN, (M + umma::BM - 1) / umma::BM, 1);
+    int splits = 1;
+    const int tiles = grid.x * grid.y;
+    while (partial && splits < 32 && tiles * splits * 2 <= sms && K / (splits * 2) >= 4 * umma::BK &&
+           (size_t)M * N * splits * 2 <= partial_elems)
+        splits *= 2;
+    umma::GemmArgs g;
+    g.M = M; g.N = N; g.K = K;
+    g.ax = ax; g.ay = ay; g.bx = bx; g.by = by;
+    g.alpha = alpha; g.beta = beta; g.C = C; g.ldc = ldc; g.upper = upper;
+    int kchunk = (K + splits - 1) / splits;
+    kchunk = (kchunk + umma::BK - 1) / umma::BK * umma::BK;
+    g.kchunk = kchunk;
+    g.partial = splits > 1 ? partial : nullptr;
+    g.split3 = split3;
+    g.err = err;
+    grid.z = splits;
+    if (split3)
+        umma::k_umma_gemm<3, 1><<<grid, umma::THREADS, umma::smem_bytes<3, 1>(), s>>>(ma, mb, g);
+    else
+        umma::k_umma_gemm<4, 0><<<grid, umma::THREADS, umma::smem_bytes<4, 0>(), s>>>(ma, mb, g);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (splits > 1) {
+        const int64_t total = (int64_t)M * N;
+        const int rgrid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sms * 8);
+        k_splitk_reduce<float, float><<<rgrid, 256, 0, s>>>(M, N, splits, alpha, partial, beta, C, ldc, upper);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace
+
 size_t blocked_workspace_bytes(int dtype, int n, int refine) {
     if (n <= 0) return 0;
     const size_t es = (dtype == CHOL_F64) ? 8 : 4;
@@ -371,6 +482,7 @@ size_t blocked_workspace_bytes(int dtype, int n, int refine) {
     bytes += 2 * align256((size_t)kBlk * n * es);             // panels
     bytes += align256((size_t)kBlk * kBlk * es);              // Z
     bytes += align256((size_t)32 * kBlk * n * (dtype == CHOL_F64 ? 8 : 4));  // split-K partials
+    bytes += 256;                                                             // tensor-core error flag
     if (refine) {
         bytes += align256((size_t)n * n * 4);   // full A (FP32)
         bytes += align256((size_t)n * n * 8);   // residual (FP64)
@@ -382,7 +494,7 @@ size_t blocked_workspace_bytes(int dtype, int n, int refine) {
 
 template <typename T>
 static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, int pivot64, int refine_steps,
-                                 int want_inv, char* ws, cudaStream_t s) {
+                                 int want_inv, int tc, int* err_word, char* ws, cudaStream_t s) {
     using Tacc = T;
     const int b = kblk(sizeof(T) == 8 ? CHOL_F64 : CHOL_F32);
     const int nb = (n + b - 1) / b;
@@ -394,7 +506,16 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
     T* Z = w.take<T>((size_t)b * b);
     const size_t part_elems = (size_t)32 * b * n;
     Tacc* part = w.take<Tacc>(part_elems);
+    int* umma_err = w.take<int>(64);
     const int sms = device_info().sms;
+    // tensor cores for the two large products (trailing update, inverse
+    // assembly): FP32 only, and the tensor maps need 16-byte rows
+    CUtensorMap mapX, mapPt;
+    bool use_tc = tc != 0 && sizeof(T) == 4 && n % 4 == 0 && b % 4 == 0;
+    if (use_tc)
+        use_tc = make_map(&mapX, reinterpret_cast<const float*>(X), n, n, n) &&
+                 make_map(&mapPt, reinterpret_cast<const float*>(P2), n, b, b);
+    const int split3 = tc == 2 ? 1 : 0;
     const int g1 = sms * 4;
     static std::once_flag once;
     static cudaError_t setup = cudaSuccess;
@@ -407,6 +528,7 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
     });
     if (setup != cudaSuccess) return CHOL_ERR_CUDA;
     if (cudaMemsetAsync(failed, 0, sizeof(int), s) != cudaSuccess) return CHOL_ERR_CUDA;
+    if (cudaMemsetAsync(umma_err, 0, sizeof(int), s) != cudaSuccess) return CHOL_ERR_CUDA;
     if (info && cudaMemsetAsync(info, 0, sizeof(int32_t), s) != cudaSuccess) return CHOL_ERR_CUDA;
     k_load_upper<T><<<g1, 256, 0, s>>>(X, A, n);
     // ---------------- factor
@@ -417,13 +539,28 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
         T* RinvK = Rinv + (size_t)kb * b * b;
         k_blk_potrf<T><<<1, 256, potrf_smem, s>>>(X, n, n, k0, bk, RinvK, failed, info, pivot64);
         if (m <= 0) break;
+        T* Ct = X + (int64_t)(k0 + bk) * n + k0 + bk;
+        if constexpr (sizeof(T) == 4) {
+            if (use_tc) {
+                // Pt = A_K,>K^T R_KK^{-1} = (R_K,>K)^T (m x bk, K-major for the tensor cores)
+                float* Pt = reinterpret_cast<float*>(P2);
+                cudaError_t e = gemm<T, Tacc, T, true, false>(m, bk, bk, Tacc(1), X + (int64_t)k0 * n + k0 + bk, n,
+                                                              RinvK, bk, Tacc(0), Pt, bk, 0, part, part_elems, s);
+                if (e != cudaSuccess) return CHOL_ERR_CUDA;
+                k_put_panel_t<<<g1, 256, 0, s>>>(X, n, k0, k0 + bk, bk, m, Pt, failed);
+                // A_>K,>K -= R_K,>K^T R_K,>K = Pt Pt^T (upper part), tensor cores
+                e = umma_gemm(m, m, bk, -1.f, mapPt, 0, 0, mapPt, 0, 0, 1.f, Ct, n, 1, nullptr, 0, split3, umma_err,
+                              s);
+                if (e != cudaSuccess) return CHOL_ERR_CUDA;
+                continue;
+            }
+        }
         // R_K,>K = R_KK^{-T} A_K,>K  (into P), then back into X
         cudaError_t e = gemm<T, Tacc, T, true, false>(bk, m, bk, Tacc(1), RinvK, bk, X + (int64_t)k0 * n + k0 + bk,
                                                       n, Tacc(0), P, m, 0, part, part_elems, s);
         if (e != cudaSuccess) return CHOL_ERR_CUDA;
         k_put_panel<T><<<g1, 256, 0, s>>>(X, n, k0, k0 + bk, bk, m, P, 0, failed);
         // A_>K,>K -= R_K,>K^T R_K,>K (upper part)
-        T* Ct = X + (int64_t)(k0 + bk) * n + k0 + bk;
         e = gemm<T, Tacc, T, true, false>(m, m, bk, Tacc(-1), P, m, P, m, Tacc(1), Ct, n, 1, part, part_elems, s);
         if (e != cudaSuccess) return CHOL_ERR_CUDA;
     }
@@ -438,9 +575,16 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
         if (m > 0) {
             const T* RIr = X + (int64_t)i0 * n + i0 + bi;          // R_I,>I   (bi x m, ld n)
             const T* Xrr = X + (int64_t)(i0 + bi) * n + i0 + bi;  // X_>I,>I  (m x m, ld n, full)
-            // P = R_I,>I X_>I,>I
-            cudaError_t e = gemm<T, Tacc, T, false, false>(bi, m, m, Tacc(1), RIr, n, Xrr, n, Tacc(0), P, m, 0, part,
-                                                           part_elems, s);
+            // P = R_I,>I X_>I,>I  (X is symmetric, so X_>I,>I read by rows is K-major)
+            cudaError_t e;
+            if (use_tc && bi == b) {
+                e = umma_gemm(bi, m, m, 1.f, mapX, i0 + bi, i0, mapX, i0 + bi, i0 + bi, 0.f,
+                              reinterpret_cast<float*>(P), m, 0, reinterpret_cast<float*>(part), part_elems, split3,
+                              umma_err, s);
+            } else {
+                e = gemm<T, Tacc, T, false, false>(bi, m, m, Tacc(1), RIr, n, Xrr, n, Tacc(0), P, m, 0, part,
+                                                   part_elems, s);
+            }
             if (e != cudaSuccess) return CHOL_ERR_CUDA;
             // P2 = -R_II^{-1} P   (X_I,>I)
             e = gemm<T, Tacc, T, false, false>(bi, m, bi, Tacc(-1), RinvI, bi, P, m, Tacc(0), P2, m, 0, part,
@@ -454,6 +598,7 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
         }
         k_blk_diag<T><<<1, 256, diag_smem, s>>>(X, n, i0, bi, m > 0 ? Z : nullptr, failed);
     }
+    if (use_tc) k_report_umma<<<1, 1, 0, s>>>(umma_err, failed, err_word);
     k_nan_if_failed<T><<<g1, 256, 0, s>>>(X, (int64_t)n * n, failed);
     if (cudaGetLastError() != cudaSuccess) return CHOL_ERR_CUDA;
 
@@ -484,18 +629,19 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
 }
 
 chol_status_t blocked_run(int dtype, int32_t batch, int32_t n, const void* A, void* R, void* X, int32_t* info,
-                          int pivot64, int refine_steps, int want_inv, void* ws, cudaStream_t s) {
+                          int pivot64, int refine_steps, int want_inv, int tc, int* err_word, void* ws,
+                          cudaStream_t s) {
     for (int32_t bi = 0; bi < batch; ++bi) {
         const int64_t o = (int64_t)bi * n * n;
         chol_status_t st;
         if (dtype == CHOL_F32)
             st = blocked_one<float>(static_cast<const float*>(A) + o, R ? static_cast<float*>(R) + o : nullptr,
                                     static_cast<float*>(X) + o, n, info ? info + bi : nullptr, pivot64,
-                                    refine_steps, want_inv, static_cast<char*>(ws), s);
+                                    refine_steps, want_inv, tc, err_word, static_cast<char*>(ws), s);
         else if (dtype == CHOL_F64)
             st = blocked_one<double>(static_cast<const double*>(A) + o, R ? static_cast<double*>(R) + o : nullptr,
                                      static_cast<double*>(X) + o, n, info ? info + bi : nullptr, 0, 0, want_inv,
-                                     static_cast<char*>(ws), s);
+                                     0, err_word, static_cast<char*>(ws), s);
         else
             return CHOL_ERR_UNSUPPORTED;
         if (st != CHOL_OK) return st;

@@ -128,3 +128,50 @@ def test_blocked_fp32_4096_residual():
     # against the FP64 solution of the same (rounded) matrix
     Xref = np.linalg.inv(Aw)
     assert _rel(np.triu(Xw), np.triu(Xref)) <= 1e-5
+
+
+@pytest.mark.parametrize("N", [256, 640, 2048])
+def test_blocked_tensor_core_split_tf32(orc, N):
+    """Trailing updates and inverse-assembly products on tcgen05 tensor cores,
+    error-corrected TF32 (three products): FP32-level accuracy."""
+    from paper_1111_4144_gb300 import _lib as L
+    b = wl.log_spaced(N, decades=3.0, seed=900 + N)
+    A = b.A.reshape(1, N, N).astype(np.float32)
+    X, info = _run(A, prec=L.CHOL_PREC_TF32_REFINE, refine_steps=0)
+    _, Xo, _ = _oracle(orc, A[0].astype(np.float64))
+    assert info[0] == 0
+    Aw = A[0].astype(np.float64)
+    kap = np.linalg.cond(np.triu(Aw) + np.triu(Aw, 1).T)
+    e = _rel(np.triu(X[0]), np.triu(Xo))
+    assert e <= tol32(kap), (e, tol32(kap))
+    assert np.array_equal(np.tril(X[0], -1), np.triu(X[0], 1).T)
+
+
+def test_blocked_tensor_core_single_tf32(orc):
+    """Single-pass TF32 products (flag): the raw tensor-core result, within 1e-2
+    on a well-conditioned matrix."""
+    from paper_1111_4144_gb300 import _lib as L
+    N = 512
+    b = wl.log_spaced(N, decades=1.0, seed=31)
+    A = b.A.reshape(1, N, N).astype(np.float32)
+    X, info = _run(A, prec=L.CHOL_PREC_TF32_REFINE, refine_steps=0, flags=L.CHOL_FLAG_TF32_SINGLE)
+    _, Xo, _ = _oracle(orc, A[0].astype(np.float64))
+    assert info[0] == 0
+    e = _rel(np.triu(X[0]), np.triu(Xo))
+    assert e <= 1e-2, e
+
+
+def test_blocked_tensor_core_4096_kappa_1e4():
+    """The large workload: N = 4096, lambda log-spaced over [1, 1e4], split TF32
+    on the tensor cores, against the FP64 inverse of the same rounded matrix."""
+    from paper_1111_4144_gb300 import _lib as L
+    N = 4096
+    b = wl.log_spaced(N, decades=4.0, seed=1004)
+    A = b.A.reshape(1, N, N).astype(np.float32)
+    X, info = _run(A, prec=L.CHOL_PREC_TF32_REFINE, refine_steps=0)
+    assert info[0] == 0
+    Aw = A[0].astype(np.float64)
+    Aw = np.triu(Aw) + np.triu(Aw, 1).T
+    Xref = np.linalg.inv(Aw)
+    kap = np.linalg.cond(Aw)
+    assert _rel(np.triu(X[0].astype(np.float64)), np.triu(Xref)) <= tol32(kap)
