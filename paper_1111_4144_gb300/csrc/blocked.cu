@@ -132,108 +132,236 @@ __global__ void k_splitk_reduce(int M, int N, int splits, Tacc alpha, const Tacc
 // ---------------------------------------------------------------------------
 // Diagonal block: Eqs. 3-4 on the b x b block at (k0, k0) of X (in place),
 // then the inverse of the triangular factor (R_KK^{-1}, upper) into Rinv.
-// One CTA of 256 threads; the block sits in shared memory.  A pivot <= 0 or
-// non-finite sets *failed and info (1-based global row).
+// One CTA of kDiagThreads threads.
+//
+// Factor, right-looking with the block in registers: thread t holds the
+// TR x TC tile at rows (t / 16) TR.., columns (t % 16) TC.. of a 32 TR x
+// 16 TC grid.  At step i every entry (r, c), r > i, receives its Eq. 4 term
+// -r_ir r_ic, so each entry still collects its terms in the order k = 0, 1,
+// ..., r-1 (the left-looking sum's order) before it is scaled by 1/r_rr.
+// The owners of row i+1 publish it (double-buffered) right after their
+// update, and the owner of entry (i+1, i+1) forms the next pivot (Eq. 3),
+// so a step needs one barrier.  R_KK^{-1} is formed the same way (right-
+// looking back substitution, rows from the last to the first).  A pivot
+// <= 0 or non-finite sets *failed and info (1-based global row).
 // ---------------------------------------------------------------------------
+constexpr int kDiagThreads = 512;
+
+template <typename T> struct DiagTile;
+template <> struct DiagTile<float>  { static constexpr int TR = 4, TC = 8; };  // b <= 128
+template <> struct DiagTile<double> { static constexpr int TR = 2, TC = 4; };  // b <= 64
+
 template <typename T>
-__global__ void k_blk_potrf(T* X, int64_t ldx, int n0, int k0, int b, T* Rinv, int* failed, int32_t* info,
-                            int pivot64) {
+__global__ void __launch_bounds__(kDiagThreads)
+k_blk_potrf(T* X, int64_t ldx, int n0, int k0, int b, T* Rinv, int* failed, int32_t* info, int pivot64) {
+    constexpr int TR = DiagTile<T>::TR, TC = DiagTile<T>::TC;
+    constexpr int BMAX = 16 * TC;  // = 32 * TR
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* S = reinterpret_cast<T*>(smem_raw);  // [b][b+1]
     const int LD = b + 1;
+    T* Ro = reinterpret_cast<T*>(smem_raw);  // [b][LD]   R_KK (upper, zeros below)
+    T* Pb = Ro + (size_t)b * LD;             // [2][BMAX]  pivot row (unscaled), double-buffered
+    T* dv = Pb + 2 * BMAX;                   // [b]        1 / r_ii
+    T* d0 = dv + b;                          // [b]        a_ii (FP64 pivots)
+    __shared__ T s_piv[2][2];                // per parity: r_ii, 1 / r_ii
+    __shared__ int s_bad[2];
     const int t = threadIdx.x;
     if (*failed) return;
-    for (int f = t; f < b * b; f += blockDim.x) {
-        const int i = f / b, j = f % b;
-        S[i * LD + j] = (i <= j) ? X[(int64_t)(k0 + i) * ldx + k0 + j] : T(0);
+    const int r0 = (t / 16) * TR, c0 = (t % 16) * TC;
+    for (int f = t; f < 2 * BMAX; f += blockDim.x) Pb[f] = T(0);  // entries past b stay zero
+    T a[TR][TC];
+#pragma unroll
+    for (int u = 0; u < TR; ++u)
+#pragma unroll
+        for (int v = 0; v < TC; ++v) {
+            const int r = r0 + u, c = c0 + v;
+            a[u][v] = (r <= c && c < b) ? X[(int64_t)(k0 + r) * ldx + k0 + c] : T(0);
+            if (r == c && c < b) d0[r] = a[u][v];
+        }
+    // pivot of row `r` from its Schur value s (Eq. 3), into slot r & 1
+    auto set_pivot = [&](int r, T s) {
+        const bool bad = !(s > T(0)) || !isfinite(s);
+        const T rii = sqrt(s);
+        s_bad[r & 1] = bad;
+        s_piv[r & 1][0] = rii;
+        s_piv[r & 1][1] = T(1) / rii;
+    };
+    // FP64 form of Eq. 3 for row r: a_rr minus the exact squares of column r of R (warp 0)
+    auto set_pivot64 = [&](int r) {
+        double part = 0.0;
+        for (int k = t; k < r; k += 32) part += (double)Ro[k * LD + r] * (double)Ro[k * LD + r];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+        if (t == 0) {
+            const double td = (double)d0[r] - part;
+            s_bad[r & 1] = !(td > 0.0) || !isfinite(td);
+            s_piv[r & 1][0] = (T)sqrt(td);
+            s_piv[r & 1][1] = (T)(1.0 / sqrt(td));
+        }
+    };
+    const bool p64 = pivot64 && sizeof(T) == 4;
+    __syncthreads();
+    // row 0 published, its pivot formed
+    if (r0 == 0) {
+#pragma unroll
+        for (int v = 0; v < TC; ++v)
+            if (c0 + v < b) Pb[c0 + v] = a[0][v];
+        if (c0 == 0 && !p64) set_pivot(0, a[0][0]);
     }
     __syncthreads();
-    __shared__ int bad;
-    if (t == 0) bad = 0;
-    __syncthreads();
+    if (p64 && t < 32) set_pivot64(0);
+    if (p64) __syncthreads();
+    // ---------------- factor, Eqs. 3-4
     for (int i = 0; i < b; ++i) {
-        // row i: s_j = a_ij - sum_{k<i} r_ki r_kj, j >= i (left-looking, Eq. 4's order)
-        T sj = T(0);
-        const int j = t;
-        if (j >= i && j < b) {
-            sj = S[i * LD + j];
-            for (int k = 0; k < i; ++k) sj = fma(-S[k * LD + i], S[k * LD + j], sj);
+        const T* P = Pb + (i & 1) * BMAX;
+        if (s_bad[i & 1]) {
+            // every thread reads the same flag, so all of them leave here
+            if (t == 0 && atomicCAS(failed, 0, 1) == 0 && info) *info = k0 + i + 1;
+            return;
+        }
+        const T rii = s_piv[i & 1][0], inv = s_piv[i & 1][1];
+        if (t < b) Ro[i * LD + t] = (t > i) ? P[t] * inv : (t == i ? rii : T(0));  // row i of R (Eq. 4)
+        if (t == 0) dv[i] = inv;
+        if (r0 + TR - 1 > i) {  // the tile has rows below the pivot row
+            // Entries (r, c) with r <= i (rows already published) or c <= i
+            // (below the diagonal of the rows still open) are never read
+            // again, so the update runs over the whole tile unguarded; the
+            // buffer's entries at and past b are zero, which keeps the tile's
+            // columns past b at zero.
+            T pr[TR], pc[TC];
+#pragma unroll
+            for (int u = 0; u < TR; ++u) pr[u] = P[r0 + u] * inv;
+#pragma unroll
+            for (int v = 0; v < TC; ++v) pc[v] = P[c0 + v] * inv;
+#pragma unroll
+            for (int u = 0; u < TR; ++u)
+#pragma unroll
+                for (int v = 0; v < TC; ++v) a[u][v] = fma(-pr[u], pc[v], a[u][v]);
+            // publish row i+1 (final in the columns >= i+1) and form its pivot
+            T* Pn = Pb + ((i + 1) & 1) * BMAX;
+#pragma unroll
+            for (int u = 0; u < TR; ++u) {
+                if (r0 + u == i + 1) {
+#pragma unroll
+                    for (int v = 0; v < TC; ++v) Pn[c0 + v] = a[u][v];
+                    if (!p64 && c0 <= i + 1 && i + 1 < c0 + TC) {
+#pragma unroll
+                        for (int v = 0; v < TC; ++v)
+                            if (c0 + v == i + 1) set_pivot(i + 1, a[u][v]);
+                    }
+                }
+            }
         }
         __syncthreads();
-        if (j == i) {
-            double td = (double)sj;
-            if (pivot64 && sizeof(T) == 4) {
-                td = (double)S[i * LD + i];
-                for (int k = 0; k < i; ++k) td -= (double)S[k * LD + i] * (double)S[k * LD + i];
-            }
-            if (!(td > 0.0) || !isfinite(td)) {
-                if (atomicCAS(failed, 0, 1) == 0 && info) *info = k0 + i + 1;
-                bad = 1;
-            }
-            S[i * LD + i] = (T)sqrt(td);
+        if (p64 && i + 1 < b) {
+            if (t < 32) set_pivot64(i + 1);
+            __syncthreads();
         }
-        __syncthreads();
-        if (j > i && j < b) S[i * LD + j] = sj / S[i * LD + i];
-        __syncthreads();
     }
-    if (bad) return;
     // R_KK back to X (upper part)
     for (int f = t; f < b * b; f += blockDim.x) {
         const int i = f / b, j = f % b;
-        if (i <= j) X[(int64_t)(k0 + i) * ldx + k0 + j] = S[i * LD + j];
+        if (i <= j) X[(int64_t)(k0 + i) * ldx + k0 + j] = Ro[i * LD + j];
     }
-    // Rinv = R_KK^{-1}: column j by back substitution, one thread per column
-    for (int j = t; j < b; j += blockDim.x) {
-        for (int i = b - 1; i >= 0; --i) {
-            if (i > j) { Rinv[(int64_t)i * b + j] = T(0); continue; }
-            T s = (i == j) ? T(1) : T(0);
-            for (int k = i + 1; k <= j; ++k) s = fma(-S[i * LD + k], Rinv[(int64_t)k * b + j], s);
-            Rinv[(int64_t)i * b + j] = s / S[i * LD + i];
+    // ---------------- R_KK W = I, rows from the last to the first; the tile
+    // holds B (W before each row's scaling by 1/r_kk)
+#pragma unroll
+    for (int u = 0; u < TR; ++u)
+#pragma unroll
+        for (int v = 0; v < TC; ++v) a[u][v] = (r0 + u == c0 + v) ? T(1) : T(0);
+    __syncthreads();  // the factor's last reads of the buffer are done
+#pragma unroll
+    for (int u = 0; u < TR; ++u)
+        if (r0 + u == b - 1) {
+#pragma unroll
+            for (int v = 0; v < TC; ++v) Pb[((b - 1) & 1) * BMAX + c0 + v] = a[u][v];
         }
+    __syncthreads();
+    for (int k = b - 1; k >= 0; --k) {
+        const T* P = Pb + (k & 1) * BMAX;
+        if (r0 < k) {  // the tile has rows above row k
+            const T dk = dv[k];
+            // rows >= k keep their values (row k is final); the published row
+            // is exactly zero left of its diagonal and past b
+            T rk[TR], wk[TC];
+#pragma unroll
+            for (int u = 0; u < TR; ++u) rk[u] = (r0 + u < k) ? Ro[(r0 + u) * LD + k] : T(0);
+#pragma unroll
+            for (int v = 0; v < TC; ++v) wk[v] = P[c0 + v] * dk;
+#pragma unroll
+            for (int u = 0; u < TR; ++u)
+#pragma unroll
+                for (int v = 0; v < TC; ++v) a[u][v] = fma(-rk[u], wk[v], a[u][v]);
+            T* Pn = Pb + ((k - 1) & 1) * BMAX;
+#pragma unroll
+            for (int u = 0; u < TR; ++u)
+                if (r0 + u == k - 1) {
+#pragma unroll
+                    for (int v = 0; v < TC; ++v) Pn[c0 + v] = a[u][v];
+                }
+        }
+        __syncthreads();
     }
+#pragma unroll
+    for (int u = 0; u < TR; ++u)
+#pragma unroll
+        for (int v = 0; v < TC; ++v) {
+            const int r = r0 + u, c = c0 + v;
+            if (r < b && c < b) Rinv[(int64_t)r * b + c] = (r <= c) ? a[u][v] * dv[r] : T(0);
+        }
 }
 
 // ---------------------------------------------------------------------------
-// Diagonal block of X (Sec. IV.A inside the block): with Z = R_I,>I X_I,>I^T,
-//   x_ij = ((delta_ij / r_ii - z_ij) - sum_{k>i, k in block} r_ik x~_kj) / r_ii,  i <= j,
-// rows from the last to the first; written to both triangles of the block.
-// One CTA; R_II (from X) and the block of X in shared memory.
+// Diagonal block of X, Sec. IV.A in block form.  Row block I of R X = S
+// (S lower triangular with diagonal 1/r_ii; its diagonal block is R_II^{-T})
+// gives, with W = R_II^{-1} and Z = R_I,>I X_>I,I (= R_I,>I X_I,>I^T):
+//   X_II = W (W^T - Z),
+// the block counterpart of x_ii = (1/r_ii)(1/r_ii - sum_{k>i} r_ik x_ik) and
+// x_ij = -(1/r_ii) sum_{k>i} r_ik x~_kj.  One CTA per 32 x 32 tile on or above
+// the block's diagonal; each result is written to both triangles (on a
+// diagonal tile only the entries with i <= j are written, and mirrored).
 // ---------------------------------------------------------------------------
+constexpr int kXdT = 32;
+
 template <typename T>
-__global__ void k_blk_diag(T* X, int64_t ldx, int i0, int b, const T* Z, const int* failed) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* Rs = reinterpret_cast<T*>(smem_raw);  // [b][b+1] R_II
-    T* Xs = Rs + (size_t)b * (b + 1);         // [b][b+1] X_II (full)
-    const int LD = b + 1;
+__global__ void __launch_bounds__(256)
+k_blk_xdiag(T* X, int64_t ldx, int i0, int b, const T* W, const T* Z, const int* failed) {
+    __shared__ T Ws[kXdT][kXdT + 1];  // W[i][k]
+    __shared__ T Ys[kXdT][kXdT + 1];  // W[j][k] - Z[k][j]
+    const int ti = blockIdx.y, tj = blockIdx.x;
+    if (ti > tj || *failed) return;
     const int t = threadIdx.x;
-    if (*failed) return;
-    for (int f = t; f < b * b; f += blockDim.x) {
-        const int i = f / b, j = f % b;
-        Rs[i * LD + j] = (i <= j) ? X[(int64_t)(i0 + i) * ldx + i0 + j] : T(0);
-    }
-    __syncthreads();
-    for (int i = b - 1; i >= 0; --i) {
-        const T inv = T(1) / Rs[i * LD + i];
-        const int j = t;
-        T x = T(0);
-        if (j > i && j < b) {
-            T s = Z ? Z[(int64_t)i * b + j] : T(0);
-            for (int k = i + 1; k < b; ++k) s = fma(Rs[i * LD + k], (k <= j) ? Xs[k * LD + j] : Xs[j * LD + k], s);
-            x = -s * inv;
+    const int ri = t / 8, cj = (t % 8) * 4;  // one row, four columns of the tile
+    const int ib = ti * kXdT, jb = tj * kXdT;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int kb = ib; kb < b; kb += kXdT) {  // W[i][k] = 0 for k < i
+        for (int f = t; f < kXdT * kXdT; f += 256) {
+            const int x = f / kXdT, y = f % kXdT;
+            const int i = ib + x, k = kb + y;
+            Ws[x][y] = (i < b && k < b && k >= i) ? W[(int64_t)i * b + k] : T(0);
+            const int kk = kb + x, j = jb + y;
+            T yv = T(0);
+            if (kk < b && j < b) {
+                yv = (kk >= j) ? W[(int64_t)j * b + kk] : T(0);
+                if (Z) yv -= Z[(int64_t)kk * b + j];
+            }
+            Ys[x][y] = yv;
         }
         __syncthreads();
-        if (j > i && j < b) { Xs[i * LD + j] = x; Xs[j * LD + i] = x; }
-        __syncthreads();
-        if (t == 0) {
-            T s = Z ? Z[(int64_t)i * b + i] : T(0);
-            for (int k = i + 1; k < b; ++k) s = fma(Rs[i * LD + k], Xs[i * LD + k], s);
-            Xs[i * LD + i] = (inv - s) * inv;
+#pragma unroll 8
+        for (int k = 0; k < kXdT; ++k) {
+            const T w = Ws[ri][k];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[c] = fma(w, Ys[k][cj + c], acc[c]);
         }
         __syncthreads();
     }
-    for (int f = t; f < b * b; f += blockDim.x) {
-        const int i = f / b, j = f % b;
-        X[(int64_t)(i0 + i) * ldx + i0 + j] = Xs[i * LD + j];
+    const int i = ib + ri;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int j = jb + cj + c;
+        if (i >= b || j >= b || (ti == tj && i > j)) continue;
+        X[(int64_t)(i0 + i) * ldx + i0 + j] = acc[c];
+        if (i != j) X[(int64_t)(i0 + j) * ldx + i0 + i] = acc[c];
     }
 }
 
@@ -519,12 +647,9 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
     const int g1 = sms * 4;
     static std::once_flag once;
     static cudaError_t setup = cudaSuccess;
-    const size_t potrf_smem = (size_t)b * (b + 1) * sizeof(T);
-    const size_t diag_smem = 2 * (size_t)b * (b + 1) * sizeof(T);
+    const size_t potrf_smem = ((size_t)b * (b + 1) + 2 * (size_t)16 * DiagTile<T>::TC + 2 * (size_t)b) * sizeof(T);
     std::call_once(once, [&] {
         setup = cudaFuncSetAttribute(k_blk_potrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem);
-        if (setup == cudaSuccess)
-            setup = cudaFuncSetAttribute(k_blk_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_smem);
     });
     if (setup != cudaSuccess) return CHOL_ERR_CUDA;
     if (cudaMemsetAsync(failed, 0, sizeof(int), s) != cudaSuccess) return CHOL_ERR_CUDA;
@@ -537,7 +662,7 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
         const int bk = std::min(b, n - k0);
         const int m = n - k0 - bk;  // columns right of the panel
         T* RinvK = Rinv + (size_t)kb * b * b;
-        k_blk_potrf<T><<<1, 256, potrf_smem, s>>>(X, n, n, k0, bk, RinvK, failed, info, pivot64);
+        k_blk_potrf<T><<<1, kDiagThreads, potrf_smem, s>>>(X, n, n, k0, bk, RinvK, failed, info, pivot64);
         if (m <= 0) break;
         T* Ct = X + (int64_t)(k0 + bk) * n + k0 + bk;
         if constexpr (sizeof(T) == 4) {
@@ -596,7 +721,8 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
             if (e != cudaSuccess) return CHOL_ERR_CUDA;
             k_put_panel<T><<<g1, 256, 0, s>>>(X, n, i0, i0 + bi, bi, m, P2, 1, failed);
         }
-        k_blk_diag<T><<<1, 256, diag_smem, s>>>(X, n, i0, bi, m > 0 ? Z : nullptr, failed);
+        const int xt = (bi + kXdT - 1) / kXdT;
+        k_blk_xdiag<T><<<dim3(xt, xt), 256, 0, s>>>(X, n, i0, bi, RinvI, m > 0 ? Z : nullptr, failed);
     }
     if (use_tc) k_report_umma<<<1, 1, 0, s>>>(umma_err, failed, err_word);
     k_nan_if_failed<T><<<g1, 256, 0, s>>>(X, (int64_t)n * n, failed);

@@ -19,13 +19,14 @@
 
 namespace cholinv {
 
-template <typename V, int N, int G>
+template <typename V, int N, int G, int W = 4>
 struct GroupCfg {
     static_assert(G >= 2 && G <= 32 && (G & (G - 1)) == 0, "G must be a power of two in [2, 32]");
+    static_assert(W % 4 == 0, "whole warps per SM sub-partition");
     static constexpr int TN = tri(N);
     static constexpr int NC = (N + G - 1) / G;   // columns per thread
     static constexpr int MPW = 32 / G;           // matrices per warp
-    static constexpr int WARPS = 4;
+    static constexpr int WARPS = W;
     static constexpr int THREADS = 32 * WARPS;
     static constexpr int MPC = MPW * WARPS;       // matrices per CTA chunk
     // bytes of one matrix's mirror: whole 16-byte units, an odd number of them
@@ -39,10 +40,10 @@ struct GroupCfg {
 };
 
 // Copy the chunk's matrices into the mirrors (cp.async, not waited on).
-template <typename V, int N, int G>
+// C supplies THREADS, TN, U (elements per 16-byte unit) and STRIDE.
+template <typename V, int N, class C>
 CHOL_D void group_stage(const BatchParams& p, const V* A, unsigned char* mir, const int64_t* s_off,
                         const uint8_t* s_i, const uint8_t* s_j, int m, bool vec) {
-    using C = GroupCfg<V, N, G>;
     const int t = threadIdx.x;
     if (vec) {
         constexpr int FULL = C::TN / C::U;  // whole units per matrix
@@ -69,11 +70,10 @@ CHOL_D void group_stage(const BatchParams& p, const V* A, unsigned char* mir, co
 }
 
 // Store the mirrors (X, or R when factoring) to global memory.
-template <typename V, int N, int G>
+template <typename V, int N, class C>
 CHOL_D void group_store(const BatchParams& p, V* out, const unsigned char* mir, const int64_t* s_off,
                         const int* s_info, const uint8_t* s_i, const uint8_t* s_j, int m, bool vec, bool is_factor,
                         bool fill_lower) {
-    using C = GroupCfg<V, N, G>;
     const int t = threadIdx.x;
     if (vec) {
         constexpr int FULL = C::TN / C::U;
@@ -176,10 +176,10 @@ constexpr int group_size() {
 //        mirror, each entry still receives its terms in ascending k); in the
 //        inverse every thread keeps its columns in full (the lower half
 //        mirrored in once per row), so the dot products run on registers.
-template <typename V, int N, int G, int ALG>
-__global__ void __launch_bounds__(GroupCfg<V, N, G>::THREADS)
+template <typename V, int N, int G, int ALG, int W = 4>
+__global__ void __launch_bounds__(GroupCfg<V, N, G, W>::THREADS)
 k_group(BatchParams p) {
-    using C = GroupCfg<V, N, G>;
+    using C = GroupCfg<V, N, G, W>;
     using R = typename traits<V>::real;
     constexpr int NC = C::NC;
     constexpr int TN = C::TN;
@@ -222,7 +222,7 @@ k_group(BatchParams p) {
             ok = (o % C::U) == 0;
         }
         const bool vec = (__syncthreads_and(ok) != 0) && p.layout == 1;
-        group_stage<V, N, G>(p, A, mirs, s_off, s_i, s_j, m, vec);
+        group_stage<V, N, C>(p, A, mirs, s_off, s_i, s_j, m, vec);
         cp_async_wait<0>();
         __syncthreads();
 
@@ -298,7 +298,7 @@ k_group(BatchParams p) {
         if (live && h == 0) s_info[q] = info;
         if (store_R || !p.want_inv) {
             __syncthreads();
-            group_store<V, N, G>(p, Ro, mirs, s_off, s_info, s_i, s_j, m, vec, true, false);
+            group_store<V, N, C>(p, Ro, mirs, s_off, s_info, s_i, s_j, m, vec, true, false);
             __syncthreads();
         }
         if (p.want_inv) {
@@ -360,7 +360,7 @@ k_group(BatchParams p) {
                 row_sync<ALG>();
             }
             __syncthreads();
-            group_store<V, N, G>(p, Xo, mirs, s_off, s_info, s_i, s_j, m, vec, false, p.fill_lower != 0);
+            group_store<V, N, C>(p, Xo, mirs, s_off, s_info, s_i, s_j, m, vec, false, p.fill_lower != 0);
         }
         } else {
         const bool live = q < m;
@@ -426,7 +426,7 @@ k_group(BatchParams p) {
         if (live && h == 0) s_info[q] = info;
         if (store_R || !p.want_inv) {
             __syncthreads();
-            group_store<V, N, G>(p, Ro, mirs, s_off, s_info, s_i, s_j, m, vec, true, false);
+            group_store<V, N, C>(p, Ro, mirs, s_off, s_info, s_i, s_j, m, vec, true, false);
             __syncthreads();
         }
         if (p.want_inv) {
@@ -484,7 +484,7 @@ k_group(BatchParams p) {
                 }
             }
             __syncthreads();
-            group_store<V, N, G>(p, Xo, mirs, s_off, s_info, s_i, s_j, m, vec, false, p.fill_lower != 0);
+            group_store<V, N, C>(p, Xo, mirs, s_off, s_info, s_i, s_j, m, vec, false, p.fill_lower != 0);
         }
         }
         if (p.info)
