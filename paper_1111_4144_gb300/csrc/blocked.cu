@@ -486,7 +486,8 @@ cudaError_t gemm(int M, int N, int K, Tacc alpha, const Tin* A, int64_t lda, con
     int splits = 1;
     if (partial && K > 0) {
         const int tiles = grid.x * grid.y;
-        while (splits < 32 && tiles * splits * 2 <= 2 * sms && K / (splits * 2) >= 256 &&
+        // split K until the grid covers the SMs twice, keeping >= 32 of K per slice
+        while (splits < 32 && tiles * splits * 2 <= 2 * sms && K / (splits * 2) >= 32 &&
                (size_t)M * N * splits * 2 <= partial_elems)
             splits *= 2;
     }
@@ -600,6 +601,35 @@ cudaError_t umma_gemm(int M, int N, int K, float alpha, const CUtensorMap& ma, i
 
 }  // namespace
 
+namespace {
+// A side stream (per device) for the factor's lookahead, with the two events
+// that fork it from and join it to the caller's stream.  Enqueueing holds
+// the mutex, so concurrent calls on one device take turns at it.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ready = nullptr, done = nullptr;
+    std::mutex mu;
+};
+SideStream* side_stream() {
+    static std::mutex init_mu;
+    static SideStream* per_dev[64] = {};
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(init_mu);
+    if (!per_dev[d]) {
+        SideStream* ss = new SideStream();
+        if (cudaStreamCreateWithFlags(&ss->s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ss->ready, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ss->done, cudaEventDisableTiming) != cudaSuccess) {
+            delete ss;
+            return nullptr;
+        }
+        per_dev[d] = ss;
+    }
+    return per_dev[d];
+}
+}  // namespace
+
 size_t blocked_workspace_bytes(int dtype, int n, int refine) {
     if (n <= 0) return 0;
     const size_t es = (dtype == CHOL_F64) ? 8 : 4;
@@ -607,9 +637,10 @@ size_t blocked_workspace_bytes(int dtype, int n, int refine) {
     const int nb = (n + kBlk - 1) / kBlk;
     size_t bytes = 256;                                       // failed flag
     bytes += align256((size_t)nb * kBlk * kBlk * es);         // Rinv blocks
-    bytes += 2 * align256((size_t)kBlk * n * es);             // panels
+    bytes += 3 * align256((size_t)kBlk * n * es);             // panels (one double-buffered)
     bytes += align256((size_t)kBlk * kBlk * es);              // Z
     bytes += align256((size_t)32 * kBlk * n * (dtype == CHOL_F64 ? 8 : 4));  // split-K partials
+    bytes += align256((size_t)8 * kBlk * n * (dtype == CHOL_F64 ? 8 : 4));   // side stream's partials
     bytes += 256;                                                             // tensor-core error flag
     if (refine) {
         bytes += align256((size_t)n * n * 4);   // full A (FP32)
@@ -631,18 +662,22 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
     T* Rinv = w.take<T>((size_t)nb * b * b);
     T* P = w.take<T>((size_t)b * n);
     T* P2 = w.take<T>((size_t)b * n);
+    T* P3 = w.take<T>((size_t)b * n);
     T* Z = w.take<T>((size_t)b * b);
     const size_t part_elems = (size_t)32 * b * n;
     Tacc* part = w.take<Tacc>(part_elems);
+    const size_t part2_elems = (size_t)8 * b * n;
+    Tacc* part2 = w.take<Tacc>(part2_elems);
     int* umma_err = w.take<int>(64);
     const int sms = device_info().sms;
     // tensor cores for the two large products (trailing update, inverse
     // assembly): FP32 only, and the tensor maps need 16-byte rows
-    CUtensorMap mapX, mapPt;
+    CUtensorMap mapX, mapPt[2];
     bool use_tc = tc != 0 && sizeof(T) == 4 && n % 4 == 0 && b % 4 == 0;
     if (use_tc)
         use_tc = make_map(&mapX, reinterpret_cast<const float*>(X), n, n, n) &&
-                 make_map(&mapPt, reinterpret_cast<const float*>(P2), n, b, b);
+                 make_map(&mapPt[0], reinterpret_cast<const float*>(P2), n, b, b) &&
+                 make_map(&mapPt[1], reinterpret_cast<const float*>(P3), n, b, b);
     const int split3 = tc == 2 ? 1 : 0;
     const int g1 = sms * 4;
     static std::once_flag once;
@@ -656,38 +691,69 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
     if (cudaMemsetAsync(umma_err, 0, sizeof(int), s) != cudaSuccess) return CHOL_ERR_CUDA;
     if (info && cudaMemsetAsync(info, 0, sizeof(int32_t), s) != cudaSuccess) return CHOL_ERR_CUDA;
     k_load_upper<T><<<g1, 256, 0, s>>>(X, A, n);
-    // ---------------- factor
-    for (int kb = 0; kb < nb; ++kb) {
+    // ---------------- factor, with one block of lookahead: once the trailing
+    // update has reached block row K+1, that block's diagonal factor and
+    // panel (the critical path) run on a side stream while the main stream
+    // updates the remaining rows.  Panels alternate between two buffers.
+    T* pbuf[2] = {use_tc ? P2 : P, P3};
+    // R_KK and R_K,>K of block kb into X; the panel, in the layout the
+    // trailing update reads, into pbuf[kb & 1]
+    auto panel = [&](int kb, cudaStream_t st, Tacc* pw, size_t pw_elems) -> cudaError_t {
         const int k0 = kb * b;
         const int bk = std::min(b, n - k0);
-        const int m = n - k0 - bk;  // columns right of the panel
+        const int m = n - k0 - bk;
         T* RinvK = Rinv + (size_t)kb * b * b;
-        k_blk_potrf<T><<<1, kDiagThreads, potrf_smem, s>>>(X, n, n, k0, bk, RinvK, failed, info, pivot64);
-        if (m <= 0) break;
-        T* Ct = X + (int64_t)(k0 + bk) * n + k0 + bk;
-        if constexpr (sizeof(T) == 4) {
-            if (use_tc) {
-                // Pt = A_K,>K^T R_KK^{-1} = (R_K,>K)^T (m x bk, K-major for the tensor cores)
-                float* Pt = reinterpret_cast<float*>(P2);
-                cudaError_t e = gemm<T, Tacc, T, true, false>(m, bk, bk, Tacc(1), X + (int64_t)k0 * n + k0 + bk, n,
-                                                              RinvK, bk, Tacc(0), Pt, bk, 0, part, part_elems, s);
-                if (e != cudaSuccess) return CHOL_ERR_CUDA;
-                k_put_panel_t<<<g1, 256, 0, s>>>(X, n, k0, k0 + bk, bk, m, Pt, failed);
-                // A_>K,>K -= R_K,>K^T R_K,>K = Pt Pt^T (upper part), tensor cores
-                e = umma_gemm(m, m, bk, -1.f, mapPt, 0, 0, mapPt, 0, 0, 1.f, Ct, n, 1, nullptr, 0, split3, umma_err,
-                              s);
-                if (e != cudaSuccess) return CHOL_ERR_CUDA;
-                continue;
-            }
+        k_blk_potrf<T><<<1, kDiagThreads, potrf_smem, st>>>(X, n, n, k0, bk, RinvK, failed, info, pivot64);
+        if (m <= 0) return cudaGetLastError();
+        T* pb = pbuf[kb & 1];
+        if (use_tc) {
+            // Pt = A_K,>K^T R_KK^{-1} = (R_K,>K)^T (m x bk, K-major for the tensor cores)
+            cudaError_t e = gemm<T, Tacc, T, true, false>(m, bk, bk, Tacc(1), X + (int64_t)k0 * n + k0 + bk, n, RinvK,
+                                                          bk, Tacc(0), pb, bk, 0, pw, pw_elems, st);
+            if (e != cudaSuccess) return e;
+            if constexpr (sizeof(T) == 4) k_put_panel_t<<<g1, 256, 0, st>>>(X, n, k0, k0 + bk, bk, m, pb, failed);
+        } else {
+            // R_K,>K = R_KK^{-T} A_K,>K  (bk x m, ld m), then back into X
+            cudaError_t e = gemm<T, Tacc, T, true, false>(bk, m, bk, Tacc(1), RinvK, bk, X + (int64_t)k0 * n + k0 + bk,
+                                                          n, Tacc(0), pb, m, 0, pw, pw_elems, st);
+            if (e != cudaSuccess) return e;
+            k_put_panel<T><<<g1, 256, 0, st>>>(X, n, k0, k0 + bk, bk, m, pb, 0, failed);
         }
-        // R_K,>K = R_KK^{-T} A_K,>K  (into P), then back into X
-        cudaError_t e = gemm<T, Tacc, T, true, false>(bk, m, bk, Tacc(1), RinvK, bk, X + (int64_t)k0 * n + k0 + bk,
-                                                      n, Tacc(0), P, m, 0, part, part_elems, s);
-        if (e != cudaSuccess) return CHOL_ERR_CUDA;
-        k_put_panel<T><<<g1, 256, 0, s>>>(X, n, k0, k0 + bk, bk, m, P, 0, failed);
-        // A_>K,>K -= R_K,>K^T R_K,>K (upper part)
-        e = gemm<T, Tacc, T, true, false>(m, m, bk, Tacc(-1), P, m, P, m, Tacc(1), Ct, n, 1, part, part_elems, s);
-        if (e != cudaSuccess) return CHOL_ERR_CUDA;
+        return cudaGetLastError();
+    };
+    // A_>K,>K -= R_K,>K^T R_K,>K on rows [r0, r1) of the trailing matrix
+    // (columns >= each row: upper part)
+    auto update = [&](int kb, int r0, int r1) -> cudaError_t {
+        const int k0 = kb * b;
+        const int bk = std::min(b, n - k0);
+        const int m = n - k0 - bk;
+        if (r1 <= r0) return cudaSuccess;
+        T* Ct = X + (int64_t)(k0 + bk + r0) * n + k0 + bk + r0;
+        T* pb = pbuf[kb & 1];
+        if constexpr (sizeof(T) == 4) {
+            if (use_tc)
+                return umma_gemm(r1 - r0, m - r0, bk, -1.f, mapPt[kb & 1], 0, r0, mapPt[kb & 1], 0, r0, 1.f, Ct, n, 1,
+                                 nullptr, 0, split3, umma_err, s);
+        }
+        return gemm<T, Tacc, T, true, false>(r1 - r0, m - r0, bk, Tacc(-1), pb + r0, m, pb + r0, m, Tacc(1), Ct, n, 1,
+                                             part, part_elems, s);
+    };
+    SideStream* side = side_stream();
+    if (!side) return CHOL_ERR_CUDA;
+    std::lock_guard<std::mutex> side_lock(side->mu);
+    if (panel(0, s, part, part_elems) != cudaSuccess) return CHOL_ERR_CUDA;
+    for (int kb = 0; kb + 1 < nb; ++kb) {
+        const int k0 = kb * b;
+        const int bk = std::min(b, n - k0);
+        const int m = n - k0 - bk;
+        const int bn = std::min(b, m);  // rows of block kb+1
+        if (update(kb, 0, bn) != cudaSuccess) return CHOL_ERR_CUDA;
+        if (cudaEventRecord(side->ready, s) != cudaSuccess) return CHOL_ERR_CUDA;
+        if (cudaStreamWaitEvent(side->s, side->ready, 0) != cudaSuccess) return CHOL_ERR_CUDA;
+        if (panel(kb + 1, side->s, part2, part2_elems) != cudaSuccess) return CHOL_ERR_CUDA;
+        if (cudaEventRecord(side->done, side->s) != cudaSuccess) return CHOL_ERR_CUDA;
+        if (update(kb, bn, m) != cudaSuccess) return CHOL_ERR_CUDA;
+        if (cudaStreamWaitEvent(s, side->done, 0) != cudaSuccess) return CHOL_ERR_CUDA;
     }
     if (R) k_copy_upper<T><<<g1, 256, 0, s>>>(R, X, n, failed);
     if (!want_inv) return cudaGetLastError() == cudaSuccess ? CHOL_OK : CHOL_ERR_CUDA;
