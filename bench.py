@@ -132,7 +132,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(loaded), "power_w_max": max(r[2] for r in rows)}
 
 
+def max_over_ranks(ms, world, device):
+    """The job's step time: the slowest rank's (all-reduce MAX; a no-op on one rank)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, batch_per_rank, ms):
+    """Whole-job throughput (weak scaling): every rank inverts its own batch."""
+    return world * batch_per_rank / (ms / 1e3)
+
+
 def make_workload(rank, batch=BATCH, sizes=SIZES):
+    """Rank `rank`'s shard: its own seeded batch (no data moves between ranks)."""
     from paper_1111_4144_gb300 import workloads as wl
     return wl.mimo_covariance(batch, sizes=sizes, sigma2=SIGMA2, seed=SEED + rank, layout=wl.LAYOUT_PACKED)
 
@@ -206,6 +223,24 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t_start}
     print(json.dumps(line), flush=True)
+
+
+def measured_traffic(order, count):
+    """DRAM bytes of one launch of the order-`order` complex64 kernel, from the
+    committed ncu capture (per-matrix traffic x matrices), or None when no
+    capture matches the current kernel sources."""
+    import hashlib
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "k_group_c64_N16_traffic.json")
+    if order != 16 or not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    root = os.path.dirname(path)
+    for rel, digest in rec["source_sha256"].items():
+        with open(os.path.join(root, "..", rel), "rb") as src:
+            if hashlib.sha256(src.read()).hexdigest() != digest:
+                return None
+    return rec["dram_bytes_per_matrix"] * count
 
 
 def run_blocked(args, local_rank):
@@ -295,12 +330,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-        ms = ev0.elapsed_time(ev1) / steps
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(ev0.elapsed_time(ev1) / steps, world, dev)
 
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
@@ -317,7 +347,7 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize()
         clocks = sampler.stop() if rank == 0 else None
 
-    value = world * b.batch / (ms / 1e3)
+    value = job_value(world, b.batch, ms)
     nbytes = alg_bytes(b.n, 8)
     peaks, peak_kind = measured_peaks()
     achieved = nbytes / (ms / 1e3) / 1e9
@@ -408,7 +438,11 @@ def run_ours(args, rank, world, local_rank):
                            "l2": "inputs larger than L2 (509 MB in, 509 MB out per step)"},
                 "roofline": {"bound": "hbm", "achieved": dom_gbs, "peak": peaks.get("hbm_gbs", FALLBACK_HBM_GBS),
                              "unit": "GB/s", "frac": dom_gbs / peaks.get("hbm_gbs", FALLBACK_HBM_GBS),
-                             "traffic": None, "peak_source": peak_kind + " (hbm_gbs, copy bandwidth)",
+                             "traffic": measured_traffic(dom, int((b.n == dom).sum())),
+                             "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum per matrix from "
+                                               "profiles/k_group_c64_N16_full.md, times this launch's matrices "
+                                               "(null if the kernel sources changed since the capture)",
+                             "peak_source": peak_kind + " (hbm_gbs, copy bandwidth)",
                              "kernel": f"size-class kernel N={dom} (complex64)",
                              "kernel_ms": kern_ms[dom], "kernel_ms_last_timed_step": last[dom],
                              "algorithmic_bytes_per_launch": dom_bytes,
@@ -417,7 +451,7 @@ def run_ours(args, rank, world, local_rank):
                                             FALLBACK_HBM_GBS), "algorithmic_bytes_per_step": nbytes},
                              "per_order_kernel_ms": {str(N): kern_ms[N] for N in orders}},
                 "gflops": alg_flops(b.n) / (ms / 1e3) / 1e9,
-                "e2e": {"value": world * b.batch / (ms_e2e / 1e3), "unit": METRIC, "h2d_bytes_per_step": h2d,
+                "e2e": {"value": job_value(world, b.batch, ms_e2e), "unit": METRIC, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
                 "gpu_launches": kernels_per_step * args.steps,
                 "clocks": clocks}
