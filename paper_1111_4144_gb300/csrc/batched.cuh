@@ -106,8 +106,7 @@ CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 
             for (int k = 0; k < N; ++k)
                 if (k < i) t = fnma_abs2(col[k], t);
             if (info == 0 && !pivot_ok(t)) info = i + 1;
-            rii = sqrt(t);
-            inv = R(1) / rii;
+            pivot_root(t, rii, inv);
         }
         dinv[i] = inv;
         m.at(pidx(N, i, i)) = from_real<V>(rii);
@@ -505,8 +504,7 @@ __global__ void k_warp(BatchParams p, int N, int warps_per_cta) {
                 inv = (R)(1.0 / sqrt(td));
             } else {
                 if (info == 0 && !pivot_ok(tt)) info = i + 1;
-                rii = sqrt(tt);
-                inv = R(1) / rii;
+                pivot_root(tt, rii, inv);
             }
             if (j0 > i && j0 < N) S[i * LD + j0] = scale_v(s0, inv);
             if (j1 > i && j1 < N) S[i * LD + j1] = scale_v(s1, inv);

@@ -108,6 +108,23 @@ template <typename V> CHOL_D V nan_v() {
 
 template <typename R> CHOL_D bool pivot_ok(R t) { return (t > R(0)) && isfinite(t); }
 
+// r_ii = sqrt(t) and 1/r_ii from Eq. 3's argument t.  FP32: the hardware
+// reciprocal square root y refined by one Newton step written around its
+// residual, e = 1 - (t y) y (one fused multiply-add), y <- y + (y/2) e, which
+// keeps 1/r_ii within an ulp (a correctly rounded sqrt followed by a
+// correctly rounded divide can be 1.5 ulp off) at a fraction of their
+// instructions; then r_ii = t y.  FP64: sqrt and divide.
+CHOL_D void pivot_root(float t, float& rii, float& inv) {
+    const float y = rsqrtf(t);
+    const float e = fmaf(-(t * y), y, 1.0f);
+    inv = fmaf(0.5f * y, e, y);
+    rii = t * inv;
+}
+CHOL_D void pivot_root(double t, double& rii, double& inv) {
+    rii = sqrt(t);
+    inv = 1.0 / rii;
+}
+
 // ---------------------------------------------------------------------------
 // Index helpers.  Packed upper, row by row: row i holds columns i..n-1.
 // ---------------------------------------------------------------------------

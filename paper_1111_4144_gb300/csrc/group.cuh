@@ -36,7 +36,7 @@ struct GroupCfg {
     static constexpr int STRIDE = UNITS * 16;
     static constexpr int U = 16 / (int)sizeof(V);
     static constexpr size_t SMEM = (size_t)MPC * STRIDE + (size_t)MPC * (sizeof(int64_t) + sizeof(int)) +
-                                   2 * (size_t)TN + 16;
+                                   (size_t)MPC * N * sizeof(typename traits<V>::real) + 2 * (size_t)TN + 16;
 };
 
 // Copy the chunk's matrices into the mirrors (cp.async, not waited on).
@@ -176,8 +176,8 @@ constexpr int group_size() {
 //        mirror, each entry still receives its terms in ascending k); in the
 //        inverse every thread keeps its columns in full (the lower half
 //        mirrored in once per row), so the dot products run on registers.
-template <typename V, int N, int G, int ALG, int W = 4>
-__global__ void __launch_bounds__(GroupCfg<V, N, G, W>::THREADS)
+template <typename V, int N, int G, int ALG, int W = 4, int MINB = 1>
+__global__ void __launch_bounds__(GroupCfg<V, N, G, W>::THREADS, MINB)
 k_group(BatchParams p) {
     using C = GroupCfg<V, N, G, W>;
     using R = typename traits<V>::real;
@@ -190,7 +190,8 @@ k_group(BatchParams p) {
     unsigned char* mirs = smem_raw;                                              // [MPC][STRIDE]
     int64_t* s_off = reinterpret_cast<int64_t*>(smem_raw + (size_t)MPC * C::STRIDE);  // [MPC]
     int* s_info = reinterpret_cast<int*>(s_off + MPC);                           // [MPC]
-    uint8_t* s_i = reinterpret_cast<uint8_t*>(s_info + MPC);                     // [TN]
+    R* s_dinv = reinterpret_cast<R*>(s_info + MPC);                              // [MPC][N] (MINB > 1)
+    uint8_t* s_i = reinterpret_cast<uint8_t*>(s_dinv + MPC * N);                 // [TN]
     uint8_t* s_j = s_i + TN;
 
     const int t = threadIdx.x;
@@ -243,7 +244,21 @@ k_group(BatchParams p) {
                 }
             }
         }
-        R dinv[N];
+        // 1/r_ii of every row: in registers, or (register-capped variants) in
+        // shared memory, written by the owner of row i and read by the group
+        constexpr bool kDinvShared = MINB > 1;
+        R dinv_r[kDinvShared ? 1 : N];
+        R* dinv_s = s_dinv + (live ? q : 0) * N;
+        auto dinv_put = [&](int i, R v) {
+            if constexpr (kDinvShared) {
+                if (live && h == i % G) dinv_s[i] = v;
+            } else {
+                dinv_r[i] = v;
+            }
+        };
+        auto dinv_get = [&](int i) -> R {
+            if constexpr (kDinvShared) return dinv_s[i]; else return dinv_r[i];
+        };
         int info = 0;
         // ---------------- factor, Eqs. 3-4, row by row
 #pragma unroll
@@ -278,10 +293,9 @@ k_group(BatchParams p) {
                 inv = (R)(1.0 / sqrt(td));
             } else {
                 if (info == 0 && !pivot_ok(tt)) info = i + 1;
-                rii = sqrt(tt);
-                inv = R(1) / rii;
+                pivot_root(tt, rii, inv);
             }
-            dinv[i] = inv;
+            dinv_put(i, inv);
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 if (i <= c * G + G - 1) {
@@ -305,11 +319,9 @@ k_group(BatchParams p) {
             // ---------------- proposed inverse, Sec. IV.A, rows N..1
 #pragma unroll
             for (int i = N - 1; i >= 0; --i) {
-                V rr[N > 0 ? N : 1];  // row i of R
-#pragma unroll
-                for (int k = 0; k < N; ++k)
-                    if (k > i) rr[k] = M[row_base(N, i) + k];
-                const R inv = dinv[i];
+                V rr[N];  // row i of R (16-byte loads where a whole unit lies in the row)
+                load_row<V, N>(M, i, rr);
+                const R inv = dinv_get(i);
                 V xs[NC];
                 R sd = R(0);
 #pragma unroll
@@ -390,8 +402,8 @@ k_group(BatchParams p) {
             const int co = k / G, ho = k % G;
             const R tt = __shfl_sync(0xffffffffu, re_of(col[co][k]), gbase + ho);  // Eq. 3 argument
             if (info == 0 && !pivot_ok(tt)) info = k + 1;
-            const R rii = sqrt(tt);
-            const R inv = R(1) / rii;
+            R rii, inv;
+            pivot_root(tt, rii, inv);
             // row k of R in the owned columns (Eq. 4's division), into the mirror
 #pragma unroll
             for (int c = 0; c < NC; ++c) {

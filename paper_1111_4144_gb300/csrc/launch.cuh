@@ -65,30 +65,34 @@ static cudaError_t launch_warp(const BatchParams& p, int N, int upper_count, cud
     return cudaGetLastError();
 }
 
-template <typename V, int N, int G, int ALG>
+// W warps per CTA; MINB resident CTAs per SM requested from the register
+// allocator (MINB = 2 with W = 8 caps a thread at 128 registers).
+template <typename V, int N, int G, int ALG, int W = 4, int MINB = 1>
 static cudaError_t launch_group(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
-    using C = GroupCfg<V, N, G>;
+    using C = GroupCfg<V, N, G, W>;
+    auto kern = k_group<V, N, G, ALG, W, MINB>;
     static std::once_flag once;
     static int per_sm = 1;
     static cudaError_t setup_err = cudaSuccess;
     std::call_once(once, [&] {
-        setup_err = cudaFuncSetAttribute(k_group<V, N, G, ALG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        setup_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (setup_err == cudaSuccess)
-            setup_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group<V, N, G, ALG>, C::THREADS, C::SMEM);
+            setup_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::THREADS, C::SMEM);
         if (per_sm < 1) per_sm = 1;
     });
     if (setup_err != cudaSuccess || dry) return setup_err;
     const int chunks = (upper_count + C::MPC - 1) / C::MPC;
     if (chunks <= 0) return cudaSuccess;
     const int grid = std::min(chunks, device_info().sms * per_sm);
-    k_group<V, N, G, ALG><<<grid, C::THREADS, C::SMEM, s>>>(p);
+    kern<<<grid, C::THREADS, C::SMEM, s>>>(p);
     return cudaGetLastError();
 }
 
 // Kernel variants of one order, chosen at run time by the autotuner
 // (tune.cu) through variant_of(); variant 0 is the compiled-in default.
 //   lane orders  : 0 lane; 1 group G=2 (orders >= 8 only)
-//   group orders : 0 group G0; 1 group 2*G0 (when 2*G0 <= 32)
+//   group orders : 0 group G0; 1 group 2*G0 (when 2*G0 <= 32) in 256-thread
+//                  CTAs capped at 128 registers per thread (two CTAs per SM)
 //   warp orders  : 0 warp
 template <typename V, int N>
 constexpr int num_variants() {
@@ -108,7 +112,7 @@ static cudaError_t launch_fixed(const BatchParams& p, int variant, int upper_cou
     } else if constexpr (kind == 1) {
         constexpr int G0 = group_size<V, N>();
         if constexpr (num_variants<V, N>() > 1)
-            if (variant == 1) return launch_group<V, N, (G0 * 2 <= 32 ? G0 * 2 : G0), 1>(p, upper_count, s, dry);
+            if (variant == 1) return launch_group<V, N, (G0 * 2 <= 32 ? G0 * 2 : G0), 1, 8, 2>(p, upper_count, s, dry);
         return launch_group<V, N, G0, 1>(p, upper_count, s, dry);
     } else {
         return launch_warp<V>(p, N, upper_count, s, dry);
