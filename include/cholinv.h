@@ -123,6 +123,7 @@ typedef struct {
 #define CHOL_CALL_FACTOR 0
 #define CHOL_CALL_INV 1
 #define CHOL_CALL_BACKWARD 2
+#define CHOL_CALL_INV_HOST 3
 
 /*
  * chol_factor_batched — Cholesky factor R of each matrix (Sec. II, Eqs. 3-4).
@@ -172,6 +173,35 @@ chol_status_t chol_inv_batched(chol_dtype_t dt, int32_t batch, const int32_t* n,
 chol_status_t chol_inv_backward(chol_dtype_t dt, int32_t batch, const int32_t* n, const int64_t* off,
                                 const int64_t* xoff, int32_t max_n, const void* X, const void* G, void* dA,
                                 const chol_opts_t* opts, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * chol_inv_batched_host — chol_inv_batched for a batch that lives in HOST
+ * memory (Sec. II factor + Sec. IV.A inverse, as chol_inv_batched; the
+ * paper has no counterpart for the data movement).
+ *   A_host, X_host, n_host, off_host, info_host: host pointers.  Page-locked
+ *   (pinned) memory gives full copy speed; with pageable memory the copies
+ *   are staged by the driver and lose most of the overlap.
+ *   Batch layout: either n_host == off_host == NULL (every matrix of order
+ *   max_n, stored back to back), or both given, with the matrices stored
+ *   back to back in index order (off_host[b+1] = off_host[b] + elements of
+ *   matrix b; each chunk's span is checked, CHOL_ERR_ARG otherwise).
+ *   Orders <= 64.  In dense layout the whole n x n block of every matrix is
+ *   written back (fill_lower is implied); in packed layout the triangle.
+ *   R is not produced.  opts (precision, refinement, flags) apply as for
+ *   chol_inv_batched.
+ * The batch is cut into chunks of whole matrices (up to 16 per call, each at
+ * least 8192 matrices or the whole batch) that pass through four device
+ * slots and three internal streams (copy in, kernels, copy out), so the
+ * copies of one chunk overlap the kernels and copies of the others.  The
+ * call returns once everything is enqueued: `stream` waits for all of it,
+ * and the host buffers must stay valid and unmodified until then.
+ * ws: device workspace of chol_workspace_bytes(CHOL_CALL_INV_HOST, dt,
+ * batch, max_n, n_host != NULL, opts) bytes, 256-byte aligned (it holds the
+ * four slots).  Concurrent calls on one device serialise their enqueueing.
+ */
+chol_status_t chol_inv_batched_host(chol_dtype_t dt, int32_t batch, const int32_t* n_host, const int64_t* off_host,
+                                    int32_t max_n, const void* A_host, void* X_host, int32_t* info_host,
+                                    const chol_opts_t* opts, void* ws, size_t ws_bytes, void* stream);
 
 /*
  * chol_inv_batched_noalloc — chol_inv_batched for callers that cannot

@@ -27,7 +27,7 @@ CHOL_FLAG_PIVOT64 = 0x1
 CHOL_FLAG_GRAD_UPPER = 0x2
 CHOL_FLAG_PLAN_TIMING = 0x4
 CHOL_FLAG_TF32_SINGLE = 0x8
-CHOL_CALL_FACTOR, CHOL_CALL_INV, CHOL_CALL_BACKWARD = 0, 1, 2
+CHOL_CALL_FACTOR, CHOL_CALL_INV, CHOL_CALL_BACKWARD, CHOL_CALL_INV_HOST = 0, 1, 2, 3
 CHOL_NOALLOC_MAX_BATCH = 1048576
 
 
@@ -46,6 +46,8 @@ SIGNATURES = {
                                   ctypes.POINTER(chol_opts_t), c_vp, c_size, c_vp]),
     "chol_inv_batched_noalloc": (c_i32, [c_i32, c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp,
                                          ctypes.POINTER(chol_opts_t), c_vp]),
+    "chol_inv_batched_host": (c_i32, [c_i32, c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp,
+                                      ctypes.POINTER(chol_opts_t), c_vp, c_size, c_vp]),
     "chol_workspace_bytes": (c_size, [c_i32, c_i32, c_i32, c_i32, c_i32, ctypes.POINTER(chol_opts_t)]),
     "chol_status_string": (ctypes.c_char_p, [c_i32]),
     "chol_last_device_error": (c_i32, [c_vp]),
@@ -120,6 +122,10 @@ def chol_inv_backward(*args):
 
 def chol_inv_batched_noalloc(*args):
     return load().chol_inv_batched_noalloc(*args)
+
+
+def chol_inv_batched_host(*args):
+    return load().chol_inv_batched_host(*args)
 
 
 def chol_workspace_bytes(*args):

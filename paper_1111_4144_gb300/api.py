@@ -96,6 +96,37 @@ def inv(A, n=None, off=None, max_n=None, *, layout=LAYOUT_DENSE, prec=L.CHOL_PRE
     return (X, info, R) if want_R else (X, info)
 
 
+class HostInv:
+    """Repeated inversions of batches held in host memory (chol_inv_batched_host).
+
+    A_host (and n_host / off_host for per-matrix orders) are CPU tensors,
+    pinned for full copy speed; the device workspace for the streaming slots
+    is allocated once here.  __call__ enqueues one inversion on `stream` into
+    X_host / info_host (CPU tensors) and returns them; synchronise the stream
+    before reading them.
+    """
+
+    def __init__(self, dtype, batch, max_n, *, sizes=False, layout=LAYOUT_PACKED, prec=L.CHOL_PREC_NATIVE,
+                 refine_steps=0, flags=0, device=None):
+        self.dt = _DT[dtype]
+        self.batch, self.max_n, self.sizes = int(batch), int(max_n), bool(sizes)
+        self.o = L.opts(prec, refine_steps, 1 if layout == LAYOUT_DENSE else 0, layout, flags)
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.ws, self.nbytes = workspace(L.CHOL_CALL_INV_HOST, self.dt, self.batch, self.max_n, self.sizes, self.o,
+                                         dev)
+
+    def __call__(self, A_host, X_host, n_host=None, off_host=None, info_host=None, stream=None):
+        for t in (A_host, X_host, n_host, off_host, info_host):
+            if t is not None and (t.is_cuda or not t.is_contiguous()):
+                raise ValueError("host tensors must be contiguous CPU tensors")
+        if (n_host is not None) != self.sizes:
+            raise ValueError("n_host must be given exactly when the plan was made with sizes=True")
+        st = L.chol_inv_batched_host(self.dt, self.batch, _p(n_host), _p(off_host), self.max_n, _p(A_host),
+                                     _p(X_host), _p(info_host), self.o, _p(self.ws), self.nbytes, _s(stream))
+        L.check(st, "chol_inv_batched_host")
+        return X_host, info_host
+
+
 def factor(A, n=None, off=None, max_n=None, *, layout=LAYOUT_DENSE, flags=0, R=None, info=None, stream=None):
     """Cholesky factor R (Eqs. 3-4).  Returns (R, info)."""
     _need_cuda(A, R, info)

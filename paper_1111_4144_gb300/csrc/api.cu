@@ -126,12 +126,16 @@ cudaError_t launch_class_timed(chol_dtype_t dt, const BatchParams& p, int c, cud
 // kernel with no members exits at once).  Running the classes side by side
 // on forked streams measured no faster, and sequential kernels keep the
 // per-kernel timing of plans exact.
-cudaError_t launch_dtype(chol_dtype_t dt, const BatchParams& p, cudaStream_t s, bool dry) {
+// `present` (optional, host memory): present[c] != 0 for the orders that
+// occur in the batch, when the caller knows them; other classes are skipped.
+cudaError_t launch_dtype(chol_dtype_t dt, const BatchParams& p, cudaStream_t s, bool dry,
+                         const uint8_t* present = nullptr) {
     if (p.cls_count == nullptr) {
         if (dry) return launch_dtype_class(dt, p, p.max_n, p.batch, s, true);
         return launch_class_timed(dt, p, p.max_n, s);
     }
     for (int c = p.max_n; c >= 1; --c) {
+        if (present && !present[c]) continue;
         cudaError_t e = dry ? launch_dtype_class(dt, p, c, p.batch, s, true) : launch_class_timed(dt, p, c, s);
         if (e != cudaSuccess) return e;
     }
@@ -139,7 +143,8 @@ cudaError_t launch_dtype(chol_dtype_t dt, const BatchParams& p, cudaStream_t s, 
 }
 
 // Enqueue bucketing (if per-matrix sizes) and every class kernel.
-chol_status_t enqueue_batched(chol_dtype_t dt, BatchParams p, void* ws, cudaStream_t s, bool dry) {
+chol_status_t enqueue_batched(chol_dtype_t dt, BatchParams p, void* ws, cudaStream_t s, bool dry,
+                              const uint8_t* present = nullptr) {
     DevState* ds = nullptr;
     if (dev_state(&ds) != cudaSuccess) return CHOL_ERR_CUDA;
     p.err = ds->err;
@@ -162,7 +167,7 @@ chol_status_t enqueue_batched(chol_dtype_t dt, BatchParams p, void* ws, cudaStre
             if (cudaGetLastError() != cudaSuccess) return CHOL_ERR_CUDA;
         }
     }
-    if (launch_dtype(dt, p, s, dry) != cudaSuccess) return CHOL_ERR_CUDA;
+    if (launch_dtype(dt, p, s, dry, present) != cudaSuccess) return CHOL_ERR_CUDA;
     return CHOL_OK;
 }
 
@@ -177,8 +182,9 @@ chol_status_t inv_validate(chol_dtype_t dt, int32_t batch, const int32_t* n, int
 }
 
 // The inverse with its optional refinement pass.
-chol_status_t enqueue_inv(chol_dtype_t dt, BatchParams p, void* ws, cudaStream_t s, bool dry, const chol_opts_t& o) {
-    chol_status_t st = enqueue_batched(dt, p, ws, s, dry);
+chol_status_t enqueue_inv(chol_dtype_t dt, BatchParams p, void* ws, cudaStream_t s, bool dry, const chol_opts_t& o,
+                          const uint8_t* present = nullptr) {
+    chol_status_t st = enqueue_batched(dt, p, ws, s, dry, present);
     if (st != CHOL_OK) return st;
     if (o.prec == CHOL_PREC_FP32_REFINE && o.refine_steps != 0) {
         BatchParams q = p;
@@ -228,6 +234,72 @@ chol_status_t blocked_validate(chol_dtype_t dt, int32_t batch, const int32_t* n,
     if (batch > 0 && (ws == nullptr || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256 != 0))
         return CHOL_ERR_WORKSPACE;
     return CHOL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host-resident batches (chol_inv_batched_host): chunks of whole matrices
+// move through kHostSlots device slots, one internal stream per slot.
+// ---------------------------------------------------------------------------
+constexpr int kHostSlots = 4;
+constexpr int kHostChunks = 16;         // chunks per call (fewer for small batches)
+constexpr int kHostMinChunk = 8192;     // matrices
+
+int64_t host_chunk_matrices(int32_t batch) {
+    const int64_t c = ((int64_t)batch + kHostChunks - 1) / kHostChunks;
+    return std::max<int64_t>(std::min<int64_t>(c, batch), std::min<int64_t>(kHostMinChunk, batch));
+}
+size_t elem_size(chol_dtype_t dt) { return dt == CHOL_F32 ? 4 : dt == CHOL_C128 ? 16 : 8; }
+int64_t matrix_elems(int layout, int64_t n) { return layout ? n * (n + 1) / 2 : n * n; }
+
+struct HostSlotLayout {
+    size_t a, x, n, off, info, ws, total;  // byte offsets within one slot
+};
+HostSlotLayout host_slot_layout(chol_dtype_t dt, int32_t batch, int32_t max_n, int layout, bool has_sizes) {
+    const int64_t mc = host_chunk_matrices(batch);
+    const size_t data = align_up((size_t)mc * matrix_elems(layout, max_n) * elem_size(dt) + 16, 256);
+    HostSlotLayout l;
+    l.a = 0;
+    l.x = l.a + data;
+    l.n = l.x + data;
+    l.off = l.n + align_up((size_t)mc * sizeof(int32_t), 256);
+    l.info = l.off + align_up((size_t)mc * sizeof(int64_t), 256);
+    l.ws = l.info + align_up((size_t)mc * sizeof(int32_t), 256);
+    l.total = l.ws + ws_need_batched((int32_t)mc, has_sizes);
+    return l;
+}
+
+// Per-device streams of the host path: one per pipeline stage (copy in,
+// kernels, copy out), the events that chain a chunk through the stages and
+// free its slot again, and those that fork the stages from and join them to
+// the caller's stream.  Enqueueing holds the mutex.
+struct HostStreams {
+    cudaStream_t in = nullptr, run = nullptr, out = nullptr;
+    cudaEvent_t fork = nullptr, join[3] = {};
+    cudaEvent_t loaded[kHostChunks] = {}, computed[kHostChunks] = {}, freed[kHostSlots] = {};
+    std::mutex mu;
+};
+HostStreams* host_streams() {
+    static std::mutex init_mu;
+    static HostStreams* per_dev[kMaxDevices] = {};
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(init_mu);
+    if (!per_dev[d]) {
+        HostStreams* h = new HostStreams();
+        auto ev = [](cudaEvent_t* e) { return cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess; };
+        bool ok = cudaStreamCreateWithFlags(&h->in, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h->run, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h->out, cudaStreamNonBlocking) == cudaSuccess && ev(&h->fork);
+        for (int k = 0; k < 3 && ok; ++k) ok = ev(&h->join[k]);
+        for (int k = 0; k < kHostChunks && ok; ++k) ok = ev(&h->loaded[k]) && ev(&h->computed[k]);
+        for (int k = 0; k < kHostSlots && ok; ++k) ok = ev(&h->freed[k]);
+        if (!ok) {
+            delete h;
+            return nullptr;
+        }
+        per_dev[d] = h;
+    }
+    return per_dev[d];
 }
 
 int blocked_refine_steps(const chol_opts_t& o) {
@@ -336,12 +408,122 @@ chol_status_t chol_inv_backward(chol_dtype_t dt, int32_t batch, const int32_t* n
     return CHOL_OK;
 }
 
+chol_status_t chol_inv_batched_host(chol_dtype_t dt, int32_t batch, const int32_t* n_host, const int64_t* off_host,
+                                    int32_t max_n, const void* A_host, void* X_host, int32_t* info_host,
+                                    const chol_opts_t* opts, void* ws, size_t ws_bytes, void* stream) {
+    chol_opts_t o = opts_or_default(opts);
+    chol_status_t st = check_common(dt, batch, max_n, o);
+    if (st != CHOL_OK) return st;
+    if (max_n > kBatchedMaxN) return CHOL_ERR_UNSUPPORTED;
+    if ((n_host == nullptr) != (off_host == nullptr)) return CHOL_ERR_ARG;
+    if (batch == 0) return CHOL_OK;
+    if (A_host == nullptr || X_host == nullptr || A_host == X_host) return CHOL_ERR_ARG;
+    const bool sized = n_host != nullptr;
+    const HostSlotLayout L = host_slot_layout(dt, batch, max_n, o.layout, sized);
+    if (ws == nullptr || ws_bytes < L.total * kHostSlots || reinterpret_cast<uintptr_t>(ws) % 256 != 0)
+        return CHOL_ERR_WORKSPACE;
+    if (o.layout == 0) o.fill_lower = 1;  // every element of a dense matrix goes back to the host
+    const size_t es = elem_size(dt);
+    const int64_t mc = host_chunk_matrices(batch);
+    const int64_t nchunks = (batch + mc - 1) / mc;
+    const int64_t cap = mc * matrix_elems(o.layout, max_n);
+    // element span [e0, e1) of chunk k (matrices stored back to back in index order)
+    auto span = [&](int64_t k, int64_t* e0, int64_t* e1) {
+        const int64_t b0 = k * mc, b1 = std::min<int64_t>(b0 + mc, batch);
+        if (!sized) {
+            *e0 = b0 * matrix_elems(o.layout, max_n);
+            *e1 = b1 * matrix_elems(o.layout, max_n);
+        } else {
+            const int32_t nl = std::min(std::max(n_host[b1 - 1], 0), max_n);
+            *e0 = off_host[b0];
+            *e1 = off_host[b1 - 1] + matrix_elems(o.layout, nl);
+        }
+    };
+    for (int64_t k = 0; k < nchunks; ++k) {
+        int64_t e0, e1;
+        span(k, &e0, &e1);
+        if (e0 < 0 || e1 < e0 || e1 - e0 > cap) return CHOL_ERR_ARG;  // not stored back to back
+    }
+    HostStreams* hs = host_streams();
+    if (hs == nullptr) return CHOL_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(hs->mu);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaStream_t stage[3] = {hs->in, hs->run, hs->out};
+    if (cudaEventRecord(hs->fork, cs) != cudaSuccess) return CHOL_ERR_CUDA;
+    for (cudaStream_t st2 : stage)
+        if (cudaStreamWaitEvent(st2, hs->fork, 0) != cudaSuccess) return CHOL_ERR_CUDA;
+    const char* Ah = static_cast<const char*>(A_host);
+    char* Xh = static_cast<char*>(X_host);
+    for (int64_t k = 0; k < nchunks; ++k) {
+        const int slot = (int)(k % kHostSlots);
+        char* base = static_cast<char*>(ws) + (size_t)slot * L.total;
+        const int64_t b0 = k * mc;
+        const int32_t cnt = (int32_t)(std::min<int64_t>(b0 + mc, batch) - b0);
+        int64_t e0, e1;
+        span(k, &e0, &e1);
+        // per-matrix offsets stay absolute: the device base is shifted so that
+        // base + off[b] lands in the slot; the copy starts on a 16-byte
+        // boundary of the host array so the shifted base stays 16-byte aligned
+        const size_t pad = sized ? (size_t)(e0 * (int64_t)es) % 16 : 0;
+        const size_t bytes = (size_t)(e1 - e0) * es;
+        // copy in, once the chunk that last used this slot has been copied out
+        if (k >= kHostSlots && cudaStreamWaitEvent(hs->in, hs->freed[slot], 0) != cudaSuccess) return CHOL_ERR_CUDA;
+        if (cudaMemcpyAsync(base + L.a, Ah + e0 * (int64_t)es - pad, bytes + pad, cudaMemcpyHostToDevice, hs->in) !=
+            cudaSuccess)
+            return CHOL_ERR_CUDA;
+        if (sized) {
+            if (cudaMemcpyAsync(base + L.n, n_host + b0, (size_t)cnt * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                hs->in) != cudaSuccess ||
+                cudaMemcpyAsync(base + L.off, off_host + b0, (size_t)cnt * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                hs->in) != cudaSuccess)
+                return CHOL_ERR_CUDA;
+        }
+        if (cudaEventRecord(hs->loaded[k], hs->in) != cudaSuccess) return CHOL_ERR_CUDA;
+        // kernels
+        if (cudaStreamWaitEvent(hs->run, hs->loaded[k], 0) != cudaSuccess) return CHOL_ERR_CUDA;
+        const intptr_t shift = sized ? (intptr_t)(e0 * (int64_t)es) - (intptr_t)pad : 0;
+        const void* Ad = reinterpret_cast<const void*>(reinterpret_cast<intptr_t>(base + L.a) - shift);
+        void* Xd = reinterpret_cast<void*>(reinterpret_cast<intptr_t>(base + L.x) - shift);
+        BatchParams p = make_params(cnt, sized ? reinterpret_cast<const int32_t*>(base + L.n) : nullptr,
+                                    sized ? reinterpret_cast<const int64_t*>(base + L.off) : nullptr, max_n, Ad,
+                                    nullptr, Xd, reinterpret_cast<int32_t*>(base + L.info), o, 1);
+        // the orders are in host memory here: launch only the classes that occur
+        // (an order outside [0, max_n] is left to the device check, which flags it)
+        uint8_t present[kClasses] = {};
+        if (sized)
+            for (int32_t b = 0; b < cnt; ++b) {
+                const uint32_t nb = (uint32_t)n_host[b0 + b];
+                if (nb < (uint32_t)kClasses) present[nb] = 1;
+            }
+        st = enqueue_inv(dt, p, base + L.ws, hs->run, false, o, sized ? present : nullptr);
+        if (st != CHOL_OK) return st;
+        if (cudaEventRecord(hs->computed[k], hs->run) != cudaSuccess) return CHOL_ERR_CUDA;
+        // copy out, then free the slot
+        if (cudaStreamWaitEvent(hs->out, hs->computed[k], 0) != cudaSuccess) return CHOL_ERR_CUDA;
+        if (cudaMemcpyAsync(Xh + e0 * (int64_t)es, base + L.x + pad, bytes, cudaMemcpyDeviceToHost, hs->out) !=
+            cudaSuccess)
+            return CHOL_ERR_CUDA;
+        if (info_host && cudaMemcpyAsync(info_host + b0, base + L.info, (size_t)cnt * sizeof(int32_t),
+                                         cudaMemcpyDeviceToHost, hs->out) != cudaSuccess)
+            return CHOL_ERR_CUDA;
+        if (cudaEventRecord(hs->freed[slot], hs->out) != cudaSuccess) return CHOL_ERR_CUDA;
+    }
+    for (int k = 0; k < 3; ++k)
+        if (cudaEventRecord(hs->join[k], stage[k]) != cudaSuccess || cudaStreamWaitEvent(cs, hs->join[k], 0) != cudaSuccess)
+            return CHOL_ERR_CUDA;
+    return CHOL_OK;
+}
+
 size_t chol_workspace_bytes(int32_t call, chol_dtype_t dt, int32_t batch, int32_t max_n, int32_t has_sizes,
                             const chol_opts_t* opts) {
     const chol_opts_t o = opts_or_default(opts);
     if (max_n > kBatchedMaxN && (call == CHOL_CALL_FACTOR || call == CHOL_CALL_INV))
         return blocked_workspace_bytes(dt, max_n, call == CHOL_CALL_INV ? blocked_refine_steps(o) : 0);
     if (call == CHOL_CALL_FACTOR || call == CHOL_CALL_INV) return ws_need_batched(batch, has_sizes);
+    if (call == CHOL_CALL_INV_HOST) {
+        if (batch <= 0 || max_n < 1 || max_n > kBatchedMaxN || dt < CHOL_F32 || dt > CHOL_C128) return 0;
+        return host_slot_layout(dt, batch, max_n, o.layout, has_sizes != 0).total * kHostSlots;
+    }
     return 0;
 }
 

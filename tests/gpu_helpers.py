@@ -19,6 +19,17 @@ def tol32(kappa):
     return np.maximum(1e-7 * np.asarray(kappa), 2.4e-7)
 
 
+def check_errors(tag, b, A_wide, err, what):
+    """Assert every matrix's error is within the tolerance of its precision."""
+    if tag in ("f64", "c128"):
+        tol = np.full(b.batch, TOL64)
+    else:
+        tol = tol32(kappas(b, A_wide))
+    bad = np.nonzero(~(err <= tol))[0]
+    assert bad.size == 0, f"{what}: {bad.size} of {b.batch} matrices over tolerance; worst ratio " \
+                          f"{np.max(err / tol):.3g} at matrix {bad[0]} (N={b.n[bad[0]]})"
+
+
 def torch_dtype(tag):
     import torch
     return {"f32": torch.float32, "f64": torch.float64, "c64": torch.complex64, "c128": torch.complex128}[tag]

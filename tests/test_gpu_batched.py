@@ -11,7 +11,7 @@ import pytest
 
 from paper_1111_4144_gb300 import workloads as wl
 
-from gpu_helpers import TOL64, cast_batch, kappas, oracle_inv, run_inv, tol32, upper_errors
+from gpu_helpers import TOL64, cast_batch, check_errors, kappas, oracle_inv, run_inv, tol32, upper_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -32,16 +32,6 @@ def make_batch(tag, N, batch, layout, seed):
         return wl.mimo_covariance(batch, sizes=(N,), seed=seed, layout=layout, shuffle=False)
     return wl.qr_spectrum(batch, lambda rng, b: np.full(b, N),
                           lambda rng, m, NN: 10.0 ** rng.uniform(0.0, 3.0, size=(m, NN)), seed, layout)
-
-
-def check_errors(tag, b, A_wide, err, what):
-    if tag in ("f64", "c128"):
-        tol = np.full(b.batch, TOL64)
-    else:
-        tol = tol32(kappas(b, A_wide))
-    bad = np.nonzero(~(err <= tol))[0]
-    assert bad.size == 0, f"{what}: {bad.size} of {b.batch} matrices over tolerance; worst ratio " \
-                          f"{np.max(err / tol):.3g} at matrix {bad[0]} (N={b.n[bad[0]]})"
 
 
 @pytest.mark.parametrize("layout", [0, 1])
