@@ -110,6 +110,11 @@ typedef enum {
                                      kernel (see chol_plan_kernel_ms) */
 #define CHOL_FLAG_TF32_SINGLE 0x8 /* CHOL_PREC_TF32_REFINE: single-pass TF32 products (11 significant bits)
                                      instead of the three-product split; only for kappa * 2^-11 << 1 */
+#define CHOL_FLAG_PLAN_ORDERS 0x10 /* chol_plan_inv_create only, batches with per-matrix sizes: read n once
+                                     at creation (synchronously) and record kernels only for the orders
+                                     present then, instead of one per order 1..max_n.  At every replay a
+                                     matrix whose order was not present at creation is not inverted: its
+                                     info is -1 and the device error word becomes CHOL_ERR_ARG */
 
 typedef struct {
     int32_t prec;          /* chol_prec_t */
@@ -291,9 +296,9 @@ chol_status_t chol_plan_destroy(chol_plan_t* plan);
 /*
  * Duration in milliseconds of the kernel of matrix order `order` in the
  * plan's most recent replay (the plan must have been created with
- * CHOL_FLAG_PLAN_TIMING and the replay's stream synchronised).  For a batch
- * with per-matrix sizes the size-class kernels run on parallel streams, so
- * a duration includes any overlap with the other orders' kernels.
+ * CHOL_FLAG_PLAN_TIMING and the replay's stream synchronised).  The
+ * size-class kernels of a batch with per-matrix sizes run one after another
+ * on the replay's stream.
  * CHOL_ERR_ARG if the plan records no timing or no kernel of that order.
  */
 chol_status_t chol_plan_kernel_ms(chol_plan_t* plan, int32_t order, float* ms);

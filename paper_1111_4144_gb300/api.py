@@ -219,10 +219,15 @@ class Plan:
     """
 
     def __init__(self, A, X, n=None, off=None, max_n=None, *, R=None, info=None, layout=LAYOUT_DENSE,
-                 prec=L.CHOL_PREC_NATIVE, refine_steps=0, fill_lower=False, flags=0, timing=False):
+                 prec=L.CHOL_PREC_NATIVE, refine_steps=0, fill_lower=False, flags=0, timing=False,
+                 fixed_orders=False):
+        """timing: record per-order kernel timing (kernel_ms).  fixed_orders: record
+        kernels only for the orders n holds now (CHOL_FLAG_PLAN_ORDERS)."""
         import ctypes
         if timing:
             flags |= L.CHOL_FLAG_PLAN_TIMING
+        if fixed_orders:
+            flags |= L.CHOL_FLAG_PLAN_ORDERS
         _need_cuda(A, X, R, info)
         dt = dtype_code(A)
         batch, max_n = _geometry(A, n, off, max_n, layout)

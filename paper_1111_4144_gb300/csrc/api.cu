@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "batched.cuh"
 #include "blocked.h"
@@ -161,9 +162,11 @@ chol_status_t enqueue_batched(chol_dtype_t dt, BatchParams p, void* ws, cudaStre
             if (cudaMemsetAsync(counts, 0, kClasses * sizeof(int32_t), s) != cudaSuccess) return CHOL_ERR_CUDA;
             const int threads = 256;
             const int grid = (int)std::min<int64_t>(((int64_t)p.batch + threads - 1) / threads, (int64_t)ds->sms * 8);
-            k_bucket_hist<<<grid, threads, 0, s>>>(p.batch, p.n, p.max_n, counts, p.info, p.err);
+            k_bucket_hist<<<grid, threads, 0, s>>>(p.batch, p.n, p.max_n, p.order_mask[0], p.order_mask[1], counts,
+                                                   p.info, p.err);
             k_bucket_scan<<<1, 32, 0, s>>>(counts, starts, cursor);
-            k_bucket_scatter<<<grid, threads, 0, s>>>(p.batch, p.n, p.max_n, cursor, perm);
+            k_bucket_scatter<<<grid, threads, 0, s>>>(p.batch, p.n, p.max_n, p.order_mask[0], p.order_mask[1], cursor,
+                                                      perm);
             if (cudaGetLastError() != cudaSuccess) return CHOL_ERR_CUDA;
         }
     }
@@ -213,6 +216,7 @@ BatchParams make_params(int32_t batch, const int32_t* n, const int64_t* off, int
     p.X = X;
     p.info = info;
     p.flags = o.flags;
+    p.order_mask[0] = p.order_mask[1] = ~0ull;
     return p;
 }
 
@@ -613,12 +617,27 @@ chol_status_t chol_plan_inv_create(chol_plan_t** plan, chol_dtype_t dt, int32_t 
     *plan = nullptr;
     chol_opts_t o = opts_or_default(opts);
     const bool timed = (o.flags & CHOL_FLAG_PLAN_TIMING) != 0;
-    o.flags &= ~CHOL_FLAG_PLAN_TIMING;
+    const bool fixed_orders = (o.flags & CHOL_FLAG_PLAN_ORDERS) != 0;
+    o.flags &= ~(CHOL_FLAG_PLAN_TIMING | CHOL_FLAG_PLAN_ORDERS);
     chol_status_t st = inv_validate(dt, batch, n, max_n, A, X, o, ws, ws_bytes);
     if (st != CHOL_OK) return st;
     BatchParams p = make_params(batch, n, off, max_n, A, (R == X) ? nullptr : R, X, info, o, 1);
+    // CHOL_FLAG_PLAN_ORDERS: the orders present now (n read once, on the host)
+    uint8_t present[kClasses] = {};
+    const bool use_present = fixed_orders && n != nullptr && batch > 0 && max_n <= kBatchedMaxN;
+    if (use_present) {
+        std::vector<int32_t> nh((size_t)batch);
+        if (cudaMemcpy(nh.data(), n, (size_t)batch * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return CHOL_ERR_CUDA;
+        p.order_mask[0] = p.order_mask[1] = 0;
+        for (int32_t v : nh)
+            if (v > 0 && v <= max_n) {
+                present[v] = 1;
+                p.order_mask[v / 64] |= 1ull << (v % 64);
+            }
+    }
     // one-time kernel set-up outside the capture
-    st = enqueue_inv(dt, p, ws, nullptr, true, o);
+    st = enqueue_inv(dt, p, ws, nullptr, true, o, use_present ? present : nullptr);
     if (st != CHOL_OK) return st;
     chol_plan* pl = new chol_plan();
     if (timed) {
@@ -641,7 +660,7 @@ chol_status_t chol_plan_inv_create(chol_plan_t** plan, chol_dtype_t dt, int32_t 
     st = CHOL_OK;
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = CHOL_ERR_CUDA;
     t_timing = pl->timing;
-    if (st == CHOL_OK && batch > 0) st = enqueue_inv(dt, p, ws, cs, false, o);
+    if (st == CHOL_OK && batch > 0) st = enqueue_inv(dt, p, ws, cs, false, o, use_present ? present : nullptr);
     t_timing = nullptr;
     cudaGraph_t g = nullptr;
     if (cudaStreamEndCapture(cs, &g) != cudaSuccess && st == CHOL_OK) st = CHOL_ERR_CUDA;

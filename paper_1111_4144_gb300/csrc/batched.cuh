@@ -34,6 +34,7 @@ struct BatchParams {
     const int32_t* perm;       // matrix indices sorted by class
     int* err;                  // device error word
     int32_t flags;             // CHOL_FLAG_*
+    uint64_t order_mask[2];    // bit c: order c may occur (bucketing rejects the others)
 };
 
 // Arguments of the adjoint kernel.
@@ -577,10 +578,15 @@ __global__ void k_warp(BatchParams p, int N, int warps_per_cta) {
 // ---------------------------------------------------------------------------
 constexpr int kClasses = 72;
 
-__global__ void k_bucket_hist(int32_t batch, const int32_t* __restrict__ n, int32_t max_n, int32_t* counts,
-                              int32_t* info, int* err);
+// Orders allowed by a mask (bit c of m[c / 64]).
+CHOL_HD bool order_allowed(const uint64_t m0, const uint64_t m1, int c) {
+    return c < 64 ? ((m0 >> c) & 1u) != 0 : ((m1 >> (c - 64)) & 1u) != 0;
+}
+
+__global__ void k_bucket_hist(int32_t batch, const int32_t* __restrict__ n, int32_t max_n, uint64_t m0, uint64_t m1,
+                              int32_t* counts, int32_t* info, int* err);
 __global__ void k_bucket_scan(int32_t* counts, int32_t* starts, int32_t* cursor);
-__global__ void k_bucket_scatter(int32_t batch, const int32_t* __restrict__ n, int32_t max_n, int32_t* cursor,
-                                 int32_t* perm);
+__global__ void k_bucket_scatter(int32_t batch, const int32_t* __restrict__ n, int32_t max_n, uint64_t m0,
+                                 uint64_t m1, int32_t* cursor, int32_t* perm);
 
 }  // namespace cholinv

@@ -6,14 +6,14 @@
 
 namespace cholinv {
 
-__global__ void k_bucket_hist(int32_t batch, const int32_t* __restrict__ n, int32_t max_n, int32_t* counts,
-                              int32_t* info, int* err) {
+__global__ void k_bucket_hist(int32_t batch, const int32_t* __restrict__ n, int32_t max_n, uint64_t m0, uint64_t m1,
+                              int32_t* counts, int32_t* info, int* err) {
     __shared__ int sh[kClasses];
     for (int c = threadIdx.x; c < kClasses; c += blockDim.x) sh[c] = 0;
     __syncthreads();
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < batch; b += (int64_t)gridDim.x * blockDim.x) {
         const int nb = n[b];
-        if (nb < 0 || nb > max_n) {
+        if (nb < 0 || nb > max_n || (nb > 0 && !order_allowed(m0, m1, nb))) {
             if (info) info[b] = -1;
             report_error(err, CHOL_ERR_ARG);
         } else if (nb == 0) {
@@ -38,8 +38,8 @@ __global__ void k_bucket_scan(int32_t* counts, int32_t* starts, int32_t* cursor)
     }
 }
 
-__global__ void k_bucket_scatter(int32_t batch, const int32_t* __restrict__ n, int32_t max_n, int32_t* cursor,
-                                 int32_t* perm) {
+__global__ void k_bucket_scatter(int32_t batch, const int32_t* __restrict__ n, int32_t max_n, uint64_t m0,
+                                 uint64_t m1, int32_t* cursor, int32_t* perm) {
     __shared__ int cnt[kClasses];
     __shared__ int basec[kClasses];
     for (int64_t tile = blockIdx.x; tile * blockDim.x < batch; tile += gridDim.x) {
@@ -49,7 +49,7 @@ __global__ void k_bucket_scatter(int32_t batch, const int32_t* __restrict__ n, i
         int nb = 0, rank = 0;
         if (b < batch) {
             nb = n[b];
-            if (nb > 0 && nb <= max_n) rank = atomicAdd(&cnt[nb], 1);
+            if (nb > 0 && nb <= max_n && order_allowed(m0, m1, nb)) rank = atomicAdd(&cnt[nb], 1);
             else nb = 0;
         }
         __syncthreads();

@@ -175,6 +175,44 @@ def test_empty_batch():
     assert L.chol_inv_batched(L.CHOL_F32, 0, None, None, 4, None, None, None, None, o, None, 0, None) == L.CHOL_OK
 
 
+def test_plan_fixed_orders():
+    """CHOL_FLAG_PLAN_ORDERS: kernels only for the orders present at creation;
+    bit-identical to the eager call; a matrix whose order appears only later
+    is rejected (info -1, device error word) and the others are unaffected."""
+    import torch
+    from paper_1111_4144_gb300 import _lib as L, api
+    b = wl.mimo_covariance(6000, sizes=(4, 8, 16), seed=14, layout=1)
+    Xe, ie, _ = run_inv(b, "c64", mixed=True)
+    A = torch.from_numpy(b.A.astype(np.complex64)).cuda()
+    n = torch.from_numpy(b.n).cuda()
+    off = torch.from_numpy(b.off).cuda()
+    X = torch.zeros_like(A)
+    api.last_device_error()  # clear
+    p = api.Plan(A, X, n, off, 16, layout=1, fixed_orders=True, timing=True)
+    p.launch()
+    torch.cuda.synchronize()
+    assert np.array_equal(p.info.cpu().numpy(), ie)
+    assert np.array_equal(X.cpu().numpy().view(np.uint8), Xe.view(np.uint8))
+    with pytest.raises(L.CholError):
+        p.kernel_ms(5)  # no kernel recorded for an absent order
+    # matrix 0 (order n0) becomes an order-3 matrix in the same storage
+    k = 0
+    n0 = int(b.n[k])
+    n[k] = 3
+    X.zero_()
+    p.launch()
+    torch.cuda.synchronize()
+    info = p.info.cpu().numpy()
+    assert info[k] == -1 and np.all(info[1:] == ie[1:])
+    assert api.last_device_error() == L.CHOL_ERR_ARG
+    Xg = X.cpu().numpy()
+    for j in range(1, b.batch, 97):
+        o, T = int(b.off[j]), int(b.n[j]) * (int(b.n[j]) + 1) // 2
+        assert np.array_equal(Xg[o:o + T].view(np.uint8), Xe[o:o + T].view(np.uint8))
+    assert n0 in (4, 8, 16)
+    p.close()
+
+
 def test_plan_kernel_timing():
     import torch
     from paper_1111_4144_gb300 import api
