@@ -29,10 +29,22 @@ struct GroupCfg {
     static constexpr int WARPS = W;
     static constexpr int THREADS = 32 * WARPS;
     static constexpr int MPC = MPW * WARPS;       // matrices per CTA chunk
-    // bytes of one matrix's mirror: whole 16-byte units, an odd number of them
-    // so that the groups of a warp hit different banks
+    // bytes of one matrix's mirror, in whole 16-byte units.  A warp access is
+    // served 128 bytes at a time, and its groups touch the same offsets of
+    // consecutive mirrors (a broadcast per group) or G consecutive elements
+    // each; a mirror stride of +-G elements modulo 128 bytes lays the groups
+    // of one 128-byte phase side by side over all banks, for both patterns
+    // and for the rows of X read in the inverse.  When G elements are not a
+    // multiple of 16 bytes (or fill 128), an odd number of units.
     static constexpr int UNITS0 = (TN * (int)sizeof(V) + 15) / 16;
-    static constexpr int UNITS = UNITS0 % 2 ? UNITS0 : UNITS0 + 1;
+    static constexpr int stride_units() {
+        constexpr int gb = (G * (int)sizeof(V)) % 128;
+        int u = UNITS0;
+        if (gb == 0 || gb % 16 != 0) return u % 2 ? u : u + 1;
+        while ((u * 16) % 128 != gb && (u * 16) % 128 != 128 - gb) ++u;
+        return u;
+    }
+    static constexpr int UNITS = stride_units();
     static constexpr int STRIDE = UNITS * 16;
     static constexpr int U = 16 / (int)sizeof(V);
     static constexpr size_t SMEM = (size_t)MPC * STRIDE + (size_t)MPC * (sizeof(int64_t) + sizeof(int)) +
