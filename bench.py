@@ -256,12 +256,18 @@ def run_blocked(args, local_rank):
         from paper_1111_4144_gb300 import workloads as wl
         A = torch.from_numpy(wl.log_spaced(N, decades=4.0, seed=1004).A.reshape(1, N, N)).to(dev).to(dt)
     else:
+        # the same spectrum rotated by eight random Householder reflections
+        # H = I - 2 v v^T (applied as rank-2 updates, no factorisation needed)
         g = torch.Generator(device=dev).manual_seed(1004)
-        Q, _ = torch.linalg.qr(torch.randn(N, N, dtype=torch.float64, device=dev, generator=g))
         lam = 10.0 ** (4.0 * torch.arange(N, dtype=torch.float64, device=dev) / max(N - 1, 1))
-        A64 = (Q * lam) @ Q.T
+        A64 = torch.diag(lam)
+        for _ in range(8):
+            v = torch.randn(N, dtype=torch.float64, device=dev, generator=g)
+            v /= v.norm()
+            w = A64 @ v
+            A64 += 4.0 * (v @ w) * torch.outer(v, v) - 2.0 * (torch.outer(v, w) + torch.outer(w, v))
         A = ((A64 + A64.T) / 2).to(dt).reshape(1, N, N)
-        del Q, A64
+        del A64
     A = A.contiguous()
     kw = {}
     if args.blocked_prec == "tf32":

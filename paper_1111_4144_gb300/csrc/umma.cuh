@@ -232,11 +232,15 @@ __global__ void __launch_bounds__(THREADS) k_umma_gemm(const __grid_constant__ C
         }
     }
     __syncwarp();
-    // epilogue: warp w reads TMEM lanes 32w..32w+31 = rows m0 + 32w + lane
-    const bool ok = KT == 0 ? true : mbar_wait(done, 0, g.err);
+    // Epilogue.  Warp w reads TMEM lanes 32w..32w+31 (rows m0 + 32w + lane)
+    // into a shared-memory tile (the ring is idle once every MMA has
+    // completed); the CTA then reads and writes C along rows, coalesced.
+    const bool ok = __syncthreads_and(KT == 0 ? 1 : (int)mbar_wait(done, 0, g.err)) != 0;
     if (ok) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int row = m0 + warp * 32 + lane;
+        constexpr int LDS = BN + 1;  // row stride of the staging tile: conflict-free both ways
+        float* stage = ring;
+        const int rl = warp * 32 + lane;
         for (int c = 0; c < BN; c += 16) {
             uint32_t r[16];
             if (KT > 0) {
@@ -254,19 +258,23 @@ __global__ void __launch_bounds__(THREADS) k_umma_gemm(const __grid_constant__ C
 #pragma unroll
                 for (int i = 0; i < 16; ++i) r[i] = 0u;
             }
-            if (row < g.M) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int col = n0 + c + i;
-                    if (col >= g.N || (g.upper && row > col)) continue;
-                    const float v = __uint_as_float(r[i]);
-                    if (g.partial) {
-                        g.partial[((int64_t)blockIdx.z * g.M + row) * g.N + col] = v;
-                    } else {
-                        float o = g.alpha * v;
-                        if (g.beta != 0.f) o = fmaf(g.beta, g.C[(int64_t)row * g.ldc + col], o);
-                        g.C[(int64_t)row * g.ldc + col] = o;
-                    }
+            for (int i = 0; i < 16; ++i) stage[rl * LDS + c + i] = __uint_as_float(r[i]);
+        }
+        __syncthreads();
+        static_assert(THREADS == BN, "one thread per column of the tile");
+        const int col = n0 + (int)threadIdx.x;
+#pragma unroll 4
+        for (int rr = 0; rr < BM; ++rr) {
+            const int row = m0 + rr;
+            if (row < g.M && col < g.N && !(g.upper && row > col)) {
+                const float v = stage[rr * LDS + threadIdx.x];
+                if (g.partial) {
+                    g.partial[((int64_t)blockIdx.z * g.M + row) * g.N + col] = v;
+                } else {
+                    float o = g.alpha * v;
+                    if (g.beta != 0.f) o = fmaf(g.beta, g.C[(int64_t)row * g.ldc + col], o);
+                    g.C[(int64_t)row * g.ldc + col] = o;
                 }
             }
         }
