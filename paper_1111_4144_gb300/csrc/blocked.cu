@@ -547,13 +547,13 @@ bool make_map(CUtensorMap* m, const float* base, int64_t rows, int64_t cols, int
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int STAGES, int SPLIT3>
+template <int STAGES, int SPLIT3, int CPRE>
 cudaError_t umma_setup() {
     static std::once_flag once;
     static cudaError_t e = cudaSuccess;
     std::call_once(once, [] {
-        e = cudaFuncSetAttribute(umma::k_umma_gemm<STAGES, SPLIT3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)umma::smem_bytes<STAGES, SPLIT3>());
+        e = cudaFuncSetAttribute(umma::k_umma_gemm<STAGES, SPLIT3, CPRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)umma::smem_bytes<STAGES, SPLIT3, CPRE>());
     });
     return e;
 }
@@ -565,8 +565,6 @@ cudaError_t umma_gemm(int M, int N, int K, float alpha, const CUtensorMap& ma, i
                       int bx, int by, float beta, float* C, int64_t ldc, int upper, float* partial, size_t partial_elems,
                       int split3, int* err, cudaStream_t s) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    cudaError_t e = split3 ? umma_setup<3, 1>() : umma_setup<4, 0>();
-    if (e != cudaSuccess) return e;
     const int sms = device_info().sms;
     dim3 grid((N + umma::BN - 1) / umma::BN, (M + umma::BM - 1) / umma::BM, 1);
     int splits = 1;
@@ -585,10 +583,24 @@ cudaError_t umma_gemm(int M, int N, int K, float alpha, const CUtensorMap& ma, i
     g.split3 = split3;
     g.err = err;
     grid.z = splits;
-    if (split3)
-        umma::k_umma_gemm<3, 1><<<grid, umma::THREADS, umma::smem_bytes<3, 1>(), s>>>(ma, mb, g);
-    else
-        umma::k_umma_gemm<4, 0><<<grid, umma::THREADS, umma::smem_bytes<4, 0>(), s>>>(ma, mb, g);
+    // C prefetched by bulk copies when it is read (beta != 0, no split-K) and
+    // its rows are 16-byte aligned; two stages then leave room for the C tile
+    const bool cpre = beta != 0.f && splits == 1 && ldc % 4 == 0 && N % 4 == 0 &&
+                      reinterpret_cast<uintptr_t>(C) % 16 == 0;
+    cudaError_t e;
+    if (split3 && cpre) {
+        if ((e = umma_setup<2, 1, 1>()) != cudaSuccess) return e;
+        umma::k_umma_gemm<2, 1, 1><<<grid, umma::THREADS, umma::smem_bytes<2, 1, 1>(), s>>>(ma, mb, g);
+    } else if (split3) {
+        if ((e = umma_setup<3, 1, 0>()) != cudaSuccess) return e;
+        umma::k_umma_gemm<3, 1, 0><<<grid, umma::THREADS, umma::smem_bytes<3, 1, 0>(), s>>>(ma, mb, g);
+    } else if (cpre) {
+        if ((e = umma_setup<4, 0, 1>()) != cudaSuccess) return e;
+        umma::k_umma_gemm<4, 0, 1><<<grid, umma::THREADS, umma::smem_bytes<4, 0, 1>(), s>>>(ma, mb, g);
+    } else {
+        if ((e = umma_setup<4, 0, 0>()) != cudaSuccess) return e;
+        umma::k_umma_gemm<4, 0, 0><<<grid, umma::THREADS, umma::smem_bytes<4, 0, 0>(), s>>>(ma, mb, g);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (splits > 1) {
         const int64_t total = (int64_t)M * N;

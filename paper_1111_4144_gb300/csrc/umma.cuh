@@ -13,6 +13,10 @@
 // accurate to about FP32 (single-pass TF32 keeps only 11 significant bits).
 // Two converter warps split each tile in shared memory after it lands.
 //
+// With CPRE (beta != 0, no split-K), the producer also fetches the C tile
+// with bulk asynchronous copies (one per row) before the main loop, so that
+// the read half of the read-modify-write overlaps the products.
+//
 // Every wait on an mbarrier is bounded (about one second); on expiry the
 // kernel records an error, stops issuing work, waits (bounded) for what it
 // issued, frees its tensor memory and returns.
@@ -108,6 +112,12 @@ CHOL_D float to_tf32(float x) {
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
 }
+// One bulk asynchronous copy global -> shared (16-byte aligned, size a multiple of 16).
+CHOL_D void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sa(dst)),
+                 "l"(src), "r"(bytes), "r"(sa(bar))
+                 : "memory");
+}
 CHOL_D void commit(uint64_t* b) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(b)) : "memory");
 }
@@ -125,23 +135,26 @@ struct GemmArgs {
     int* err;
 };
 
-template <int STAGES, int SPLIT3>
+template <int STAGES, int SPLIT3, int CPRE>
 constexpr size_t smem_bytes() {
-    return (size_t)STAGES * (SPLIT3 ? 4 : 2) * TILE_FLOATS * 4 + 1024 + 512;
+    return (size_t)STAGES * (SPLIT3 ? 4 : 2) * TILE_FLOATS * 4 + (CPRE ? (size_t)BM * BN * 4 : 0) + 1024 + 512;
 }
 
-template <int STAGES, int SPLIT3>
+template <int STAGES, int SPLIT3, int CPRE>
 __global__ void __launch_bounds__(THREADS) k_umma_gemm(const __grid_constant__ CUtensorMap ta,
                                                         const __grid_constant__ CUtensorMap tb, GemmArgs g) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     constexpr int TILES = SPLIT3 ? 4 : 2;  // A, B (, A_lo, B_lo) per stage
     float* ring = reinterpret_cast<float*>(sm);
-    uint64_t* full = reinterpret_cast<uint64_t*>(ring + (size_t)STAGES * TILES * TILE_FLOATS);
+    float* cbuf = ring + (size_t)STAGES * TILES * TILE_FLOATS;  // [BM][BN] C tile (CPRE)
+    uint64_t* full = reinterpret_cast<uint64_t*>(cbuf + (CPRE ? BM * BN : 0));
     uint64_t* conv = full + STAGES;
     uint64_t* empty = conv + STAGES;
     uint64_t* done = empty + STAGES;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    uint64_t* cbar = done + 1;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(cbar + 1);
+    const bool cpre = CPRE && g.beta != 0.f && g.partial == nullptr;
     auto tile = [&](int s, int which) { return ring + ((size_t)s * TILES + which) * TILE_FLOATS; };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -158,6 +171,7 @@ __global__ void __launch_bounds__(THREADS) k_umma_gemm(const __grid_constant__ C
             mbar_init(&empty[s], 1);
         }
         mbar_init(done, 1);
+        mbar_init(cbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -171,8 +185,16 @@ __global__ void __launch_bounds__(THREADS) k_umma_gemm(const __grid_constant__ C
     const uint32_t tbase = *tslot;
     int issued = 0;  // k-tiles whose loads were issued (producer)
 
+    const int crows = min(BM, g.M - m0);
+    const uint32_t cbytes = (uint32_t)min(BN, g.N - n0) * 4u;
     if (warp == 0) {
         if (lane == 0) {
+            if (cpre) {
+                // the C tile, row by row, behind the products
+                mbar_expect_tx(cbar, (uint32_t)crows * cbytes);
+                for (int r = 0; r < crows; ++r)
+                    bulk_g2s(cbuf + r * BN, g.C + (int64_t)(m0 + r) * g.ldc + n0, cbytes, cbar);
+            }
             for (int kt = 0; kt < KT; ++kt) {
                 const int s = kt % STAGES;
                 if (kt >= STAGES && !mbar_wait(&empty[s], ((kt / STAGES) & 1) ^ 1, g.err)) break;
@@ -235,7 +257,9 @@ __global__ void __launch_bounds__(THREADS) k_umma_gemm(const __grid_constant__ C
     // Epilogue.  Warp w reads TMEM lanes 32w..32w+31 (rows m0 + 32w + lane)
     // into a shared-memory tile (the ring is idle once every MMA has
     // completed); the CTA then reads and writes C along rows, coalesced.
-    const bool ok = __syncthreads_and(KT == 0 ? 1 : (int)mbar_wait(done, 0, g.err)) != 0;
+    int mine = KT == 0 ? 1 : (int)mbar_wait(done, 0, g.err);
+    if (cpre && mine) mine = (int)mbar_wait(cbar, 0, g.err);
+    const bool ok = __syncthreads_and(mine) != 0;
     if (ok) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         constexpr int LDS = BN + 1;  // row stride of the staging tile: conflict-free both ways
@@ -273,7 +297,10 @@ __global__ void __launch_bounds__(THREADS) k_umma_gemm(const __grid_constant__ C
                     g.partial[((int64_t)blockIdx.z * g.M + row) * g.N + col] = v;
                 } else {
                     float o = g.alpha * v;
-                    if (g.beta != 0.f) o = fmaf(g.beta, g.C[(int64_t)row * g.ldc + col], o);
+                    if (g.beta != 0.f) {
+                        const float c0 = cpre ? cbuf[rr * BN + threadIdx.x] : g.C[(int64_t)row * g.ldc + col];
+                        o = fmaf(g.beta, c0, o);
+                    }
                     g.C[(int64_t)row * g.ldc + col] = o;
                 }
             }
@@ -281,6 +308,7 @@ __global__ void __launch_bounds__(THREADS) k_umma_gemm(const __grid_constant__ C
     } else if (warp == 0 && lane == 0) {
         // gave up: let the loads already issued land before the shared memory is released
         for (int kt = 0; kt < issued; ++kt) mbar_wait_quiet(&full[kt % STAGES], (kt / STAGES) & 1);
+        if (cpre) mbar_wait_quiet(cbar, 0);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
