@@ -180,10 +180,11 @@ k_blk_potrf(T* X, int64_t ldx, int n0, int k0, int b, T* Rinv, int* failed, int3
     // pivot of row `r` from its Schur value s (Eq. 3), into slot r & 1
     auto set_pivot = [&](int r, T s) {
         const bool bad = !(s > T(0)) || !isfinite(s);
-        const T rii = sqrt(s);
+        T rii, inv;
+        pivot_root(s, rii, inv);
         s_bad[r & 1] = bad;
         s_piv[r & 1][0] = rii;
-        s_piv[r & 1][1] = T(1) / rii;
+        s_piv[r & 1][1] = inv;
     };
     // FP64 form of Eq. 3 for row r: a_rr minus the exact squares of column r of R (warp 0)
     auto set_pivot64 = [&](int r) {
