@@ -312,6 +312,180 @@ k_blk_potrf(T* X, int64_t ldx, int n0, int k0, int b, T* Rinv, int* failed, int3
 }
 
 // ---------------------------------------------------------------------------
+// Diagonal block, blocked form (no FP64-pivot mode): the b x b block is split
+// into 32 x 32 sub-blocks (padded with the identity up to a multiple of 32).
+// For each sub-block row p:
+//   leaf     one warp factors the diagonal sub-block A_pp (Eqs. 3-4,
+//            right-looking, lane j holds column j in registers, rows of R
+//            passed by shuffles) and forms W_pp = R_pp^{-1} by back
+//            substitution;
+//   panel    one warp per 32 columns to the right solves R_pp^T R_pq = A_pq
+//            (Eq. 4 for the sub-block row: each entry receives its terms in
+//            ascending k, then the scaling by 1/r_ii);
+//   trailing the CTA applies A_qr -= R_pq^T R_pr (terms in ascending k);
+// then the off-diagonal blocks of W = R_KK^{-1} follow bottom-up,
+// W_pq = -W_pp sum_{p<k<=q} R_pk W_kq.  About 16 CTA barriers in all, against
+// 256 for the row-by-row kernel.
+// ---------------------------------------------------------------------------
+constexpr int kSB = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(kDiagThreads)
+k_blk_potrf_blk(T* X, int64_t ldx, int k0, int b, T* Rinv, int* failed, int32_t* info) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int NSB = (b + kSB - 1) / kSB;
+    const int B = NSB * kSB;
+    const int LD = B + 1;
+    T* S = reinterpret_cast<T*>(smem_raw);  // [B][LD] A, then R (upper)
+    T* W = S + (size_t)B * LD;              // [B][LD] R^{-1} (upper); its lower blocks hold scratch
+    T* dv = W + (size_t)B * LD;             // [B] 1 / r_ii
+    __shared__ int s_bad;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (*failed) return;
+    for (int f = t; f < B * B; f += blockDim.x) {
+        const int i = f / B, j = f % B;
+        T v;
+        if (i < b && j < b) v = (i <= j) ? X[(int64_t)(k0 + i) * ldx + k0 + j] : T(0);
+        else v = (i == j) ? T(1) : T(0);
+        S[i * LD + j] = v;
+        W[i * LD + j] = T(0);
+    }
+    if (t == 0) s_bad = 0;
+    __syncthreads();
+    for (int p = 0; p < NSB; ++p) {
+        const int o = p * kSB;
+        // ---------------- leaf (warp 0)
+        if (warp == 0) {
+            T a[kSB];
+#pragma unroll
+            for (int k = 0; k < kSB; ++k) a[k] = S[(o + k) * LD + o + lane];
+            int bad = 0;
+#pragma unroll
+            for (int i = 0; i < kSB; ++i) {
+                const T tt = __shfl_sync(0xffffffffu, a[i], i);  // Eq. 3 argument (row i, column i)
+                if (!bad && !(tt > T(0) && isfinite(tt))) bad = o + i + 1;
+                T rii, inv;
+                pivot_root(tt, rii, inv);
+                if (lane == i) a[i] = rii;
+                else if (lane > i) a[i] = a[i] * inv;  // r_ij, Eq. 4
+                if (lane == 0) dv[o + i] = inv;
+#pragma unroll
+                for (int k = 0; k < kSB; ++k) {  // fixed trip count: every index stays a constant
+                    if (k > i) {
+                        const T rik = __shfl_sync(0xffffffffu, a[i], k);
+                        if (lane >= k) a[k] = fma(-rik, a[i], a[k]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kSB; ++k)
+                if (k <= lane) S[(o + k) * LD + o + lane] = a[k];
+            __syncwarp();
+            // W_pp = R_pp^{-1}, column `lane`, rows from the last to the first
+            T w[kSB];
+#pragma unroll
+            for (int k = kSB - 1; k >= 0; --k) {
+                T acc = (k == lane) ? T(1) : T(0);
+#pragma unroll
+                for (int m = 0; m < kSB; ++m)
+                    if (m > k) acc = fma(-S[(o + k) * LD + o + m], w[m], acc);
+                w[k] = acc * dv[o + k];
+            }
+#pragma unroll
+            for (int k = 0; k < kSB; ++k) W[(o + k) * LD + o + lane] = w[k];
+            if (lane == 0 && bad) s_bad = bad;
+        }
+        __syncthreads();
+        if (s_bad) {
+            if (t == 0 && s_bad <= b && atomicCAS(failed, 0, 1) == 0 && info) *info = k0 + s_bad;
+            return;  // every thread reads the same flag
+        }
+        if (p + 1 == NSB) break;
+        // ---------------- panel: warp w takes columns o + 32 (w + 1) + lane
+        if (warp < NSB - 1 - p) {
+            const int c = o + kSB * (warp + 1) + lane;
+            T a[kSB];
+#pragma unroll
+            for (int k = 0; k < kSB; ++k) a[k] = S[(o + k) * LD + c];
+#pragma unroll
+            for (int i = 0; i < kSB; ++i) {
+                T s = a[i];
+#pragma unroll
+                for (int k = 0; k < kSB; ++k)
+                    if (k < i) s = fma(-S[(o + k) * LD + o + i], a[k], s);
+                a[i] = s * dv[o + i];
+            }
+#pragma unroll
+            for (int k = 0; k < kSB; ++k) S[(o + k) * LD + c] = a[k];
+        }
+        __syncthreads();
+        // ---------------- trailing update of rows/columns past o + 32: 4 x 4 patches
+        {
+            const int r0 = o + kSB, n = B - r0;  // trailing order (a multiple of 32)
+            const int np = n / 4;                 // patches per side
+            for (int f = t; f < np * np; f += blockDim.x) {
+                const int pr = f / np, pc = f % np;
+                if (pr > pc) continue;  // below the diagonal: not needed
+                const int rr = r0 + 4 * pr, cc = r0 + 4 * pc;
+                T acc[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = S[(rr + u) * LD + cc + v];
+#pragma unroll 4
+                for (int k = 0; k < kSB; ++k) {
+                    T x[4], y[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) x[u] = S[(o + k) * LD + rr + u];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) y[v] = S[(o + k) * LD + cc + v];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[u][v] = fma(-x[u], y[v], acc[u][v]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) S[(rr + u) * LD + cc + v] = acc[u][v];
+            }
+        }
+        __syncthreads();
+    }
+    // R_KK back to X (upper part)
+    for (int f = t; f < b * b; f += blockDim.x) {
+        const int i = f / b, j = f % b;
+        if (i <= j) X[(int64_t)(k0 + i) * ldx + k0 + j] = S[i * LD + j];
+    }
+    // ---------------- off-diagonal blocks of W, bottom-up
+    for (int p = NSB - 2; p >= 0; --p) {
+        const int o = p * kSB, r0 = o + kSB, n = B - r0;
+        // T_q = R_p,(p,q] W_(p,q],q for every column c >= r0, into W's lower block
+        // rows (its rows r0 + i, i < 32, columns o.. hold nothing else)
+        for (int f = t; f < kSB * n; f += blockDim.x) {
+            const int i = f / n, c = r0 + f % n;
+            T acc = T(0);
+            for (int m = r0; m <= c; ++m) acc = fma(S[(o + i) * LD + m], W[m * LD + c], acc);
+            W[(c) * LD + o + i] = acc;  // transposed into the strictly lower part (c > o + i)
+        }
+        __syncthreads();
+        // W_pq = -W_pp T_q
+        for (int f = t; f < kSB * n; f += blockDim.x) {
+            const int i = f / n, c = r0 + f % n;
+            T acc = T(0);
+#pragma unroll 8
+            for (int k = 0; k < kSB; ++k) acc = fma(W[(o + i) * LD + o + k], W[c * LD + o + k], acc);
+            W[(o + i) * LD + c] = -acc;
+        }
+        __syncthreads();
+    }
+    for (int f = t; f < b * b; f += blockDim.x) {
+        const int i = f / b, j = f % b;
+        Rinv[(int64_t)i * b + j] = (i <= j) ? W[i * LD + j] : T(0);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Diagonal block of X, Sec. IV.A in block form.  Row block I of R X = S
 // (S lower triangular with diagonal 1/r_ii; its diagonal block is R_II^{-T})
 // gives, with W = R_II^{-1} and Z = R_I,>I X_>I,I (= R_I,>I X_I,>I^T):
@@ -696,8 +870,13 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
     static std::once_flag once;
     static cudaError_t setup = cudaSuccess;
     const size_t potrf_smem = ((size_t)b * (b + 1) + 2 * (size_t)16 * DiagTile<T>::TC + 2 * (size_t)b) * sizeof(T);
+    const size_t potrf_blk_smem = (2 * (size_t)b * (b + 1) + (size_t)b) * sizeof(T);  // b: a multiple of 32
     std::call_once(once, [&] {
         setup = cudaFuncSetAttribute(k_blk_potrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem);
+        if constexpr (sizeof(T) == 4)
+            if (setup == cudaSuccess)
+                setup = cudaFuncSetAttribute(k_blk_potrf_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)potrf_blk_smem);
     });
     if (setup != cudaSuccess) return CHOL_ERR_CUDA;
     if (cudaMemsetAsync(failed, 0, sizeof(int), s) != cudaSuccess) return CHOL_ERR_CUDA;
@@ -716,7 +895,16 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
         const int bk = std::min(b, n - k0);
         const int m = n - k0 - bk;
         T* RinvK = Rinv + (size_t)kb * b * b;
-        k_blk_potrf<T><<<1, kDiagThreads, potrf_smem, st>>>(X, n, n, k0, bk, RinvK, failed, info, pivot64);
+        // FP32: the blocked diagonal factor; FP64 (whose 32-wide register
+        // columns do not fit) and FP64 pivots: the row-by-row one
+        bool blk = false;
+        if constexpr (sizeof(T) == 4) blk = !pivot64;
+        if (blk) {
+            if constexpr (sizeof(T) == 4)
+                k_blk_potrf_blk<T><<<1, kDiagThreads, potrf_blk_smem, st>>>(X, n, k0, bk, RinvK, failed, info);
+        } else {
+            k_blk_potrf<T><<<1, kDiagThreads, potrf_smem, st>>>(X, n, n, k0, bk, RinvK, failed, info, pivot64);
+        }
         if (m <= 0) return cudaGetLastError();
         T* pb = pbuf[kb & 1];
         if (use_tc) {
