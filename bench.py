@@ -413,6 +413,20 @@ def run_ours(args, rank, world, local_rank):
                             "speedup_fp32_over_fp64": ms64 / ms}
         plan64.close()
         del A128, X128
+        # the LDL form (Sec. IV.B) of the same library on the same FP32 matrices
+        Xl = torch.zeros_like(X)
+        planl = api.Plan(A, Xl, n, off, max(sizes), layout=api.LAYOUT_PACKED, fixed_orders=True,
+                         flags=_lib.CHOL_FLAG_LDL)
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                planl.launch(stream)
+            msl = timed(lambda: planl.launch(stream), max(3, min(args.steps, 20)), "ldl_form")
+        rl = upper_err_ratio(b, Xl.cpu().numpy(), Xo, kap, fp64=False)
+        out["ldl_form"] = {"value": b.batch / (msl / 1e3), "unit": METRIC, "ms_per_step": msl,
+                           "max_err_over_tol": rl[0], "max_rel_err": rl[1],
+                           "kernel": "one matrix per warp (the LDL form runs only there)"}
+        planl.close()
+        del Xl
 
     # ---- end to end through the public API with host buffers
     A_h = torch.from_numpy(A64).pin_memory()

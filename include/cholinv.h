@@ -110,6 +110,10 @@ typedef enum {
                                      kernel (see chol_plan_kernel_ms) */
 #define CHOL_FLAG_TF32_SINGLE 0x8 /* CHOL_PREC_TF32_REFINE: single-pass TF32 products (11 significant bits)
                                      instead of the three-product split; only for kappa * 2^-11 << 1 */
+#define CHOL_FLAG_LDL 0x20         /* the LDL form (Sec. II.A, Eqs. 9-11; Sec. IV.B, Eqs. 25-29): A = R^* D R with R
+                                     unit upper and D = diag(d_i), no square roots; X as for Cholesky.  R, when
+                                     written, holds d_i on its diagonal (the unit diagonal is implied).  Batched
+                                     path only (orders <= 64; one matrix per warp); not with CHOL_FLAG_PIVOT64 */
 #define CHOL_FLAG_PLAN_ORDERS 0x10 /* chol_plan_inv_create only, batches with per-matrix sizes: read n once
                                      at creation (synchronously) and record kernels only for the orders
                                      present then, instead of one per order 1..max_n.  At every replay a

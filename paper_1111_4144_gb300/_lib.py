@@ -28,6 +28,7 @@ CHOL_FLAG_GRAD_UPPER = 0x2
 CHOL_FLAG_PLAN_TIMING = 0x4
 CHOL_FLAG_TF32_SINGLE = 0x8
 CHOL_FLAG_PLAN_ORDERS = 0x10
+CHOL_FLAG_LDL = 0x20
 CHOL_CALL_FACTOR, CHOL_CALL_INV, CHOL_CALL_BACKWARD, CHOL_CALL_INV_HOST = 0, 1, 2, 3
 CHOL_NOALLOC_MAX_BATCH = 1048576
 

@@ -74,7 +74,8 @@ chol_status_t check_common(chol_dtype_t dt, int32_t batch, int32_t max_n, const 
     if (o.layout != 0 && o.layout != 1) return CHOL_ERR_ARG;
     if (o.prec < CHOL_PREC_NATIVE || o.prec > CHOL_PREC_BF16_REFINE) return CHOL_ERR_ARG;
     if (o.refine_steps < -1 || o.refine_steps > 2) return CHOL_ERR_ARG;
-    if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER)) return CHOL_ERR_ARG;
+    if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER | CHOL_FLAG_LDL)) return CHOL_ERR_ARG;
+    if ((o.flags & CHOL_FLAG_LDL) && (o.flags & CHOL_FLAG_PIVOT64)) return CHOL_ERR_UNSUPPORTED;
     if (max_n > kBatchedMaxN) return CHOL_ERR_UNSUPPORTED;
     if (o.prec == CHOL_PREC_TF32_REFINE || o.prec == CHOL_PREC_BF16_REFINE) return CHOL_ERR_UNSUPPORTED;
     if (o.prec == CHOL_PREC_FP32_REFINE && !is_fp32(dt)) return CHOL_ERR_UNSUPPORTED;
@@ -228,6 +229,7 @@ chol_status_t blocked_validate(chol_dtype_t dt, int32_t batch, const int32_t* n,
     if (o.layout != 0 && o.layout != 1) return CHOL_ERR_ARG;
     if (o.prec < CHOL_PREC_NATIVE || o.prec > CHOL_PREC_BF16_REFINE) return CHOL_ERR_ARG;
     if (o.refine_steps < -1 || o.refine_steps > 2) return CHOL_ERR_ARG;
+    if (o.flags & CHOL_FLAG_LDL) return CHOL_ERR_UNSUPPORTED;
     if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER | CHOL_FLAG_TF32_SINGLE)) return CHOL_ERR_ARG;
     if (n != nullptr || off != nullptr || o.layout != 0) return CHOL_ERR_UNSUPPORTED;
     if (dt != CHOL_F32 && dt != CHOL_F64) return CHOL_ERR_UNSUPPORTED;

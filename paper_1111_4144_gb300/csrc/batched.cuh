@@ -480,24 +480,38 @@ __global__ void k_warp(BatchParams p, int N, int warps_per_cta) {
                 for (int j = i + lane; j < N; j += 32) S[i * LD + j] = A[o + (int64_t)i * N + j];
         }
         __syncwarp();
-        // ---- factor, Eqs. 3-4, row by row
+        // ---- factor, Eqs. 3-4, row by row; with CHOL_FLAG_LDL the LDL form of
+        // Sec. II.A (Eqs. 9-11): d_i = a_ii - sum |r_ki|^2 d_k and
+        // r_ij = (a_ij - sum conj(r_ki) d_k r_kj) / d_i, R unit upper, d_i kept
+        // on R's diagonal
+        const bool ldl = (p.flags & CHOL_FLAG_LDL) != 0;
         int info = 0;
         for (int i = 0; i < N; ++i) {
             V s0 = zero_v<V>(), s1 = zero_v<V>();
             const int j0 = lane, j1 = lane + 32;
             if (j0 >= i && j0 < N) {
                 s0 = S[i * LD + j0];
-                for (int k = 0; k < i; ++k) s0 = fnma_conj(S[k * LD + i], S[k * LD + j0], s0);
+                for (int k = 0; k < i; ++k) {
+                    const V rki = ldl ? scale_v(S[k * LD + i], re_of(S[k * LD + k])) : S[k * LD + i];
+                    s0 = fnma_conj(rki, S[k * LD + j0], s0);
+                }
             }
             if (j1 >= i && j1 < N) {
                 s1 = S[i * LD + j1];
-                for (int k = 0; k < i; ++k) s1 = fnma_conj(S[k * LD + i], S[k * LD + j1], s1);
+                for (int k = 0; k < i; ++k) {
+                    const V rki = ldl ? scale_v(S[k * LD + i], re_of(S[k * LD + k])) : S[k * LD + i];
+                    s1 = fnma_conj(rki, S[k * LD + j1], s1);
+                }
             }
             // pivot: column i lives in lane i & 31, slot i >> 5
             R tsrc = re_of((i < 32) ? s0 : s1);
             R tt = __shfl_sync(0xffffffffu, tsrc, i & 31);
             R rii, inv;
-            if (sizeof(R) == 4 && (p.flags & CHOL_FLAG_PIVOT64)) {
+            if (ldl) {
+                if (info == 0 && !pivot_ok(tt)) info = i + 1;
+                rii = tt;  // d_i, stored on the diagonal
+                inv = R(1) / tt;
+            } else if (sizeof(R) == 4 && (p.flags & CHOL_FLAG_PIVOT64)) {
                 double td = (double)re_of(S[i * LD + i]);
                 for (int k = 0; k < i; ++k) td -= pivot64_term(S[k * LD + i]);
                 if (info == 0 && !pivot_ok(td)) info = i + 1;
@@ -544,15 +558,19 @@ __global__ void k_warp(BatchParams p, int N, int warps_per_cta) {
                         a1 = fma_v(S[i * LD + k], xt, a1);
                     }
                 }
+                // 1/r_ii, or 1/d_i in the LDL form (Sec. IV.B, Eqs. 25-29: R unit
+                // upper, s~_ii = 1/d_i, so x_ij = -sum r_ik x~_kj and
+                // x_ii = 1/d_i - sum r_ik conj(x_ik))
                 const R inv = R(1) / re_of(S[i * LD + i]);
+                const R xs = ldl ? R(-1) : -inv;
                 __syncwarp();
                 R sd = R(0);
-                if (j0 > i && j0 < N) { V x = scale_v(a0, -inv); S[i * LD + j0] = x; sd = fma_re_conjb(r0, x, sd); }
-                if (j1 > i && j1 < N) { V x = scale_v(a1, -inv); S[i * LD + j1] = x; sd = fma_re_conjb(r1, x, sd); }
+                if (j0 > i && j0 < N) { V x = scale_v(a0, xs); S[i * LD + j0] = x; sd = fma_re_conjb(r0, x, sd); }
+                if (j1 > i && j1 < N) { V x = scale_v(a1, xs); S[i * LD + j1] = x; sd = fma_re_conjb(r1, x, sd); }
 #pragma unroll
                 for (int d = 16; d > 0; d >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, d);
                 __syncwarp();
-                if (lane == 0) S[i * LD + i] = from_real<V>((inv - sd) * inv);
+                if (lane == 0) S[i * LD + i] = from_real<V>(ldl ? inv - sd : (inv - sd) * inv);
                 __syncwarp();
             }
             // store X

@@ -156,6 +156,7 @@ constexpr int kSplitN = 14;
 // which half of the orders this translation unit instantiates.
 template <typename V, bool LOW>
 cudaError_t launch_class_half(const BatchParams& p, int cls, int upper_count, cudaStream_t s, bool dry) {
+    if (p.flags & CHOL_FLAG_LDL) return launch_warp<V>(p, cls, upper_count, s, dry);  // LDL form: warp kernel
     const int v = variant_of(dtype_code<V>(), cls);
     if constexpr (LOW) {
         return launch_fixed_range<V, 1, kSplitN>(p, cls, v, upper_count, s, dry);
