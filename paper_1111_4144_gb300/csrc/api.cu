@@ -160,12 +160,14 @@ chol_status_t enqueue_batched(chol_dtype_t dt, BatchParams p, void* ws, cudaStre
         p.cls_start = starts;
         p.perm = perm;
         if (!dry) {
-            if (cudaMemsetAsync(counts, 0, kClasses * sizeof(int32_t), s) != cudaSuccess) return CHOL_ERR_CUDA;
+            // counts and the done counter (right after cursor) cleared together
+            unsigned* done = reinterpret_cast<unsigned*>(cursor + kClasses);
+            if (cudaMemsetAsync(counts, 0, (3 * kClasses + 1) * sizeof(int32_t), s) != cudaSuccess)
+                return CHOL_ERR_CUDA;
             const int threads = 256;
             const int grid = (int)std::min<int64_t>(((int64_t)p.batch + threads - 1) / threads, (int64_t)ds->sms * 8);
             k_bucket_hist<<<grid, threads, 0, s>>>(p.batch, p.n, p.max_n, p.order_mask[0], p.order_mask[1], counts,
-                                                   p.info, p.err);
-            k_bucket_scan<<<1, 32, 0, s>>>(counts, starts, cursor);
+                                                   starts, cursor, done, p.info, p.err);
             k_bucket_scatter<<<grid, threads, 0, s>>>(p.batch, p.n, p.max_n, p.order_mask[0], p.order_mask[1], cursor,
                                                       perm);
             if (cudaGetLastError() != cudaSuccess) return CHOL_ERR_CUDA;

@@ -592,7 +592,7 @@ __global__ void k_warp(BatchParams p, int N, int warps_per_cta) {
 
 // ---------------------------------------------------------------------------
 // Size-class bucketing for batches with per-matrix orders.
-// ws layout: counts[72] | starts[72] | cursor[72] | pad to 1024 B | perm[batch]
+// ws layout: counts[72] | starts[72] | cursor[72] | done | pad to 1024 B | perm[batch]
 // ---------------------------------------------------------------------------
 constexpr int kClasses = 72;
 
@@ -602,8 +602,8 @@ CHOL_HD bool order_allowed(const uint64_t m0, const uint64_t m1, int c) {
 }
 
 __global__ void k_bucket_hist(int32_t batch, const int32_t* __restrict__ n, int32_t max_n, uint64_t m0, uint64_t m1,
-                              int32_t* counts, int32_t* info, int* err);
-__global__ void k_bucket_scan(int32_t* counts, int32_t* starts, int32_t* cursor);
+                              int32_t* counts, int32_t* starts, int32_t* cursor, unsigned* done, int32_t* info,
+                              int* err);
 __global__ void k_bucket_scatter(int32_t batch, const int32_t* __restrict__ n, int32_t max_n, uint64_t m0,
                                  uint64_t m1, int32_t* cursor, int32_t* perm);
 

@@ -1,13 +1,14 @@
 // Size-class bucketing of a batch with per-matrix orders: a histogram of
-// n[b], an exclusive scan over the classes and a scatter of the matrix
-// indices into class order.  Every kernel is a plain grid-stride loop; no
-// CTA waits on another, so nothing here can stall.
+// n[b] whose last CTA takes the exclusive scan over the classes, then a
+// scatter of the matrix indices into class order.  Every kernel is a plain
+// grid-stride loop; no CTA waits on another, so nothing here can stall.
 #include "batched.cuh"
 
 namespace cholinv {
 
 __global__ void k_bucket_hist(int32_t batch, const int32_t* __restrict__ n, int32_t max_n, uint64_t m0, uint64_t m1,
-                              int32_t* counts, int32_t* info, int* err) {
+                              int32_t* counts, int32_t* starts, int32_t* cursor, unsigned* done, int32_t* info,
+                              int* err) {
     __shared__ int sh[kClasses];
     for (int c = threadIdx.x; c < kClasses; c += blockDim.x) sh[c] = 0;
     __syncthreads();
@@ -25,16 +26,23 @@ __global__ void k_bucket_hist(int32_t batch, const int32_t* __restrict__ n, int3
     __syncthreads();
     for (int c = threadIdx.x; c < kClasses; c += blockDim.x)
         if (sh[c]) atomicAdd(&counts[c], sh[c]);
-}
-
-__global__ void k_bucket_scan(int32_t* counts, int32_t* starts, int32_t* cursor) {
-    if (threadIdx.x == 0) {
+    // the last CTA to finish turns the counts into class starts (no CTA waits:
+    // each one only adds to a counter after its own counts are visible)
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
         int s = 0;
         for (int c = 0; c < kClasses; ++c) {
+            const int v = *reinterpret_cast<volatile int32_t*>(&counts[c]);
             starts[c] = s;
             cursor[c] = s;
-            s += counts[c];
+            s += v;
         }
+        *done = 0u;  // ready for the next call (the counters are cleared before each call too)
     }
 }
 
