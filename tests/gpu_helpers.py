@@ -101,3 +101,28 @@ def oracle_inv(orc, b: wl.Batch, tag, fill_lower=False):
     R, X, info = orc.inv_batch(A_wide, b.n, b.off, b.layout, np.iscomplexobj(A_wide), want_R=True,
                                fill_lower=fill_lower)
     return R, X, info, A_wide
+
+
+def sub_batch(b: wl.Batch, idx, flat=None):
+    """Matrices idx of batch b (elements taken from `flat`, default b.A),
+    laid out back to back in b's layout, as a new Batch."""
+    flat = b.A if flat is None else np.asarray(flat)
+    idx = np.asarray(idx, dtype=np.int64)
+    n = b.n[idx].astype(np.int32)
+    off, total = wl.layout_offsets(n, b.layout)
+    per = wl.tri(n.astype(np.int64)) if b.layout == wl.LAYOUT_PACKED else n.astype(np.int64) ** 2
+    out = np.zeros(total, dtype=flat.dtype)
+    for k, src in enumerate(b.off[idx]):
+        out[off[k]:off[k] + per[k]] = flat[src:src + per[k]]
+    return wl.Batch(out, n, off, b.layout)
+
+
+def diagonal_positions(b: wl.Batch):
+    """Flat element positions of every diagonal entry of every matrix of b."""
+    n = b.n.astype(np.int64)
+    owner = np.repeat(np.arange(b.batch), n)
+    i = np.arange(int(n.sum()), dtype=np.int64) - np.repeat(np.cumsum(n) - n, n)
+    N = n[owner]
+    if b.layout == wl.LAYOUT_PACKED:
+        return b.off[owner] + i * N - i * (i - 1) // 2
+    return b.off[owner] + i * (N + 1)
