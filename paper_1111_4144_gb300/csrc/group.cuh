@@ -15,6 +15,8 @@
 // predicates, not branches.
 #pragma once
 
+#include <type_traits>
+
 #include "batched.cuh"
 
 namespace cholinv {
@@ -47,6 +49,13 @@ struct GroupCfg {
     static constexpr int UNITS = stride_units();
     static constexpr int STRIDE = UNITS * 16;
     static constexpr int U = 16 / (int)sizeof(V);
+    // 32-bit words of the owned columns' upper parts (rows 0..c*G+G-1 of slot c)
+    static constexpr int colw() {
+        int w = 0;
+        for (int c = 0; c < NC; ++c) w += (c * G + G < N ? c * G + G : N);
+        return w * (int)(sizeof(V) / 4);
+    }
+    static constexpr int COLW = colw();
     static constexpr size_t SMEM = (size_t)MPC * STRIDE + (size_t)MPC * (sizeof(int64_t) + sizeof(int)) +
                                    (size_t)MPC * N * sizeof(typename traits<V>::real) + 2 * (size_t)TN + 16;
 };
@@ -182,7 +191,14 @@ constexpr int group_size() {
 }
 
 // ALG 1: left-looking Eq. 4 (column i of R read from the mirror at row i);
-//        inverse terms with k > j read row j of X from the mirror.
+//        inverse terms with k > j read row j of X from the mirror.  For
+//        complex64 the sums run on paired FP32 instructions (below) when the
+//        owned columns plus the paired accumulators fit the register budget:
+//        in the factor, and in the inverse too without a register cap
+//        (MINB = 1).
+//        On one GB300 (349,525 matrices) this took order 16 from 313 to
+//        306 us (factor only; the inverse's accumulators spill under the
+//        128-register cap) and order 8 from 56.4-57.2 to 55.4 us.
 // ALG 2 (an alternative kept for tuning; it ignores CHOL_FLAG_PIVOT64 and
 //        is not dispatched by default): the same sums taken right-looking (row k of R broadcast from the
 //        mirror, each entry still receives its terms in ascending k); in the
@@ -240,6 +256,17 @@ k_group(BatchParams p) {
         __syncthreads();
 
         if constexpr (ALG == 1 || ALG == 3) {
+        // A complex product a b splits over the parts of a:
+        //   a b = {a.re, a.re} o {b.re, b.im} + {a.im, a.im} o {-b.im, b.re},
+        // so a sum of products is carried as P = sum {a.re, a.re} o b and
+        // Q = sum {a.im, a.im} o b (one paired FMA each per term, two
+        // independent chains) and combined once per entry.
+        constexpr bool kC64 = std::is_same<V, cpx<float>>::value;
+        // the paired accumulators (4 words per owned column) on top of the
+        // columns must leave the columns in registers; measured to help with
+        // G <= 4 only
+        constexpr bool kPair = kC64 && G <= 4 && C::COLW + 4 * NC <= 96;    // factor
+        constexpr bool kPairI = kPair && MINB == 1;                         // inverse
         const bool live = q < m;
         V* M = reinterpret_cast<V*>(mirs + (size_t)(live ? q : 0) * C::STRIDE);
         // own columns, upper parts, into registers
@@ -275,19 +302,47 @@ k_group(BatchParams p) {
         // ---------------- factor, Eqs. 3-4, row by row
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            V ci[N > 0 ? N : 1];  // column i above the diagonal, from the mirror
-#pragma unroll
-            for (int k = 0; k < N; ++k)
-                if (k < i) ci[k] = M[row_base(N, k) + i];
+            V ci[kPair ? 1 : N];  // column i above the diagonal, from the mirror
             V sv[NC];
+            if constexpr (kPair) {
+                // s - sum_k conj(r_ki) r_kj: P starts at s and takes -r_ki.re,
+                // Q takes r_ki.im; then s = {P.x - Q.y, P.y + Q.x}
+                float2 P[NC], Q[NC];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                if (i <= c * G + G - 1) {
-                    V s = col[c][i];
+                for (int c = 0; c < NC; ++c)
+                    if (i <= c * G + G - 1) P[c] = make_float2(re_of(col[c][i]), col[c][i].im);
 #pragma unroll
-                    for (int k = 0; k < N; ++k)
-                        if (k < i) s = fnma_conj(ci[k], col[c][k], s);
-                    sv[c] = s;
+                for (int k = 0; k < N; ++k) {
+                    if (k < i) {
+                        const V a = M[row_base(N, k) + i];
+                        const float2 nar = make_float2(-a.re, -a.re), aim = make_float2(a.im, a.im);
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) {
+                            if (i <= c * G + G - 1) {
+                                const float2 b = make_float2(col[c][k].re, col[c][k].im);
+                                P[c] = __ffma2_rn(nar, b, P[c]);
+                                Q[c] = k == 0 ? __fmul2_rn(aim, b) : __ffma2_rn(aim, b, Q[c]);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    if (i <= c * G + G - 1)
+                        sv[c] = i == 0 ? col[c][i] : V{P[c].x - Q[c].y, P[c].y + Q[c].x};
+            } else {
+#pragma unroll
+                for (int k = 0; k < N; ++k)
+                    if (k < i) ci[k] = M[row_base(N, k) + i];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    if (i <= c * G + G - 1) {
+                        V s = col[c][i];
+#pragma unroll
+                        for (int k = 0; k < N; ++k)
+                            if (k < i) s = fnma_conj(ci[k], col[c][k], s);
+                        sv[c] = s;
+                    }
                 }
             }
             const int co = i / G, ho = i % G;
@@ -298,8 +353,12 @@ k_group(BatchParams p) {
                 // Eq. 3 in FP64: a_ii (still in the mirror) minus |r_ki|^2 over column i
                 double td = (double)re_of(M[row_base(N, i) + i]);
 #pragma unroll
-                for (int k = 0; k < N; ++k)
-                    if (k < i) td -= pivot64_term(ci[k]);
+                for (int k = 0; k < N; ++k) {
+                    if (k < i) {
+                        if constexpr (kPair) td -= pivot64_term(M[row_base(N, k) + i]);
+                        else td -= pivot64_term(ci[k]);
+                    }
+                }
                 if (info == 0 && !pivot_ok(td)) info = i + 1;
                 rii = (R)sqrt(td);
                 inv = (R)(1.0 / sqrt(td));
@@ -331,11 +390,63 @@ k_group(BatchParams p) {
             // ---------------- proposed inverse, Sec. IV.A, rows N..1
 #pragma unroll
             for (int i = N - 1; i >= 0; --i) {
-                V rr[N];  // row i of R (16-byte loads where a whole unit lies in the row)
-                load_row<V, N>(M, i, rr);
+                V rr[kPairI ? 1 : N];  // row i of R (16-byte loads where a whole unit lies in the row)
+                if constexpr (!kPairI) load_row<V, N>(M, i, rr);
                 const R inv = dinv_get(i);
                 V xs[NC];
                 R sd = R(0);
+                if constexpr (kPairI) {
+                    // sum_{k>i} r_ik x~_kj as P = sum {r.re, r.re} o x~,
+                    // Q = sum {r.im, r.im} o x~, sum = {P.x - Q.y, P.y + Q.x};
+                    // row i of R read in 16-byte units as k advances
+                    float2 P[NC], Q[NC];
+                    V carry = zero_v<V>();
+#pragma unroll
+                    for (int k = 0; k < N; ++k) {
+                        if (k > i) {
+                            const int e = row_base(N, i) + k;
+                            V r;
+                            if (e % 2 == 0) {
+                                const uint4 w = *reinterpret_cast<const uint4*>(M + e);
+                                r = reinterpret_cast<const V*>(&w)[0];
+                                carry = reinterpret_cast<const V*>(&w)[1];
+                            } else if (k == i + 1) {
+                                const uint4 w = *reinterpret_cast<const uint4*>(M + e - 1);
+                                r = reinterpret_cast<const V*>(&w)[1];
+                            } else {
+                                r = carry;
+                            }
+                            const float2 rre = make_float2(r.re, r.re), rim = make_float2(r.im, r.im);
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) {
+                                if (c * G + G - 1 > i) {
+                                    const int j = c * G + h;
+                                    const int jb = row_base(N, min(j, N - 1));
+                                    V xt;
+                                    if (k <= c * G) {
+                                        xt = col[c][k];
+                                    } else if (k > c * G + G - 1) {
+                                        xt = conj_v(M[jb + k]);
+                                    } else {
+                                        xt = (k <= j) ? col[c][k] : conj_v(M[jb + k]);
+                                    }
+                                    const float2 b = make_float2(xt.re, xt.im);
+                                    P[c] = k == i + 1 ? __fmul2_rn(rre, b) : __ffma2_rn(rre, b, P[c]);
+                                    Q[c] = k == i + 1 ? __fmul2_rn(rim, b) : __ffma2_rn(rim, b, Q[c]);
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        if (c * G + G - 1 > i) {
+                            const int j = c * G + h;
+                            const V acc = i + 1 < N ? V{P[c].x - Q[c].y, P[c].y + Q[c].x} : zero_v<V>();
+                            xs[c] = scale_v(acc, -inv);
+                            if (j > i && j < N) sd = fma_re_conjb(col[c][i], xs[c], sd);
+                        }
+                    }
+                } else {
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
                     if (c * G + G - 1 > i) {
@@ -361,6 +472,7 @@ k_group(BatchParams p) {
                         // diagonal partial: r_ij conj(x_ij) over own columns
                         if (act) sd = fma_re_conjb(col[c][i], xs[c], sd);
                     }
+                }
                 }
                 row_sync<ALG>();  // row i of R is read; it may now be overwritten
 #pragma unroll
