@@ -52,6 +52,8 @@ def parse():
                     help="time the blocked path instead: one FP32 matrix of this order, lambda log-spaced over "
                          "[1, 1e4], tensor-core products (prints one JSON line)")
     ap.add_argument("--blocked-prec", default="tf32", choices=["tf32", "fp32", "fp64"])
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other batched workloads (FP64 order 8, uneven FP32, forward + adjoint)")
     return ap.parse_args()
 
 
@@ -241,6 +243,189 @@ def measured_traffic(order, count):
             if hashlib.sha256(src.read()).hexdigest() != digest:
                 return None
     return rec["dram_bytes_per_matrix"] * count
+
+
+def _event_ms(stream, fn, reps, flush=None):
+    """Mean device time of fn() over reps launches on `stream` (CUDA events
+    around each launch; with `flush`, L2 is overwritten before each one)."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    torch.cuda.synchronize()
+    for e0, e1 in evs:
+        if flush is not None:
+            flush.add_(1)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return sum(e0.elapsed_time(e1) for e0, e1 in evs) / reps
+
+
+def _oracle_sample(b, idx, tag):
+    """The oracle on matrices idx of batch b (inputs rounded to the working
+    precision): (sub-batch, oracle X, inverses/s, threads, seconds)."""
+    import oracle
+    from paper_1111_4144_gb300 import workloads as wl
+    n = b.n[idx].astype(np.int32)
+    off, total = wl.layout_offsets(n, b.layout)
+    per = n.astype(np.int64) ** 2 if b.layout == wl.LAYOUT_DENSE else wl.tri(n.astype(np.int64))
+    A = np.zeros(total, dtype=np.float64)
+    for k, src in enumerate(b.off[idx]):
+        A[off[k]:off[k] + per[k]] = b.A[src:src + per[k]]
+    if tag == "f32":
+        A = A.astype(np.float32).astype(np.float64)
+    sb = wl.Batch(A, n, off, b.layout)
+    threads = os.cpu_count() or 1
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        _, Xo, _ = oracle.inv_batch(A, n, off, b.layout, False, fill_lower=True, nthreads=threads)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= 0.5:
+            break
+    return sb, Xo, reps * len(idx) / el, threads, el
+
+
+def _dense_err_ratio(sb, Xg_sub, Xo, fp64):
+    """max over matrices of the relative Frobenius error of the upper triangle
+    over its tolerance (FP64 1e-11; FP32 max(1e-7 kappa, 2.4e-7))."""
+    worst, worst_rel = 0.0, 0.0
+    for k in range(sb.batch):
+        N = int(sb.n[k]); o = int(sb.off[k])
+        G = np.triu(Xg_sub[o:o + N * N].reshape(N, N).astype(np.float64))
+        R = np.triu(Xo[o:o + N * N].reshape(N, N))
+        rel = np.linalg.norm(G - R) / np.linalg.norm(R)
+        if fp64:
+            tol = 1e-11
+        else:
+            M = sb.A[o:o + N * N].reshape(N, N)
+            M = np.triu(M) + np.triu(M, 1).T
+            ev = np.linalg.eigvalsh(M)
+            tol = max(1e-7 * ev[-1] / ev[0], 2.4e-7)
+        worst, worst_rel = max(worst, rel / tol), max(worst_rel, rel)
+    return worst, worst_rel
+
+
+def extra_workloads(dev, stream, steps):
+    """The method's other batched workloads, each timed on its own after
+    warm-up (CUDA events on `stream`; inputs larger than L2, or L2 overwritten
+    before each launch), each with a bounded oracle sample as its CPU baseline
+    and accuracy check.  Rank 0 only; no collective."""
+    import torch
+    from paper_1111_4144_gb300 import _lib as L, api, workloads as wl
+    peaks, peak_kind = measured_peaks()
+    hbm = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
+    reps = max(5, min(steps, 20))
+    out = {}
+    flush = torch.zeros(64 << 20, dtype=torch.int32, device=dev)  # 256 MB, twice the L2
+    with torch.cuda.stream(stream):
+        # ---- 4,096 real FP64 matrices of order 8, A = B B^T + 8 I; R and X written
+        b = wl.spd_gram_shift(4096, 8, 8.0, seed=1000, layout=wl.LAYOUT_DENSE)
+        A = torch.from_numpy(b.A).to(dev).view(4096, 8, 8)
+        X = torch.zeros_like(A)
+        R = torch.zeros_like(A)
+        plan = api.Plan(A, X, R=R)
+        for _ in range(3):
+            plan.launch(stream)
+        ms = _event_ms(stream, lambda: plan.launch(stream), reps, flush)
+        torch.cuda.synchronize()
+        sb, Xo, cpu_v, thr, _ = _oracle_sample(b, np.arange(4096), "f64")
+        r = _dense_err_ratio(sb, X.cpu().numpy().reshape(-1), Xo, fp64=True)
+        plan.close()
+        out["gram_shift_f64_N8_x4096"] = {
+            "value": 4096 / (ms / 1e3), "unit": METRIC, "us_per_batch": ms * 1e3,
+            "launch": "cuda_graph (uniform order, one kernel)", "l2": "overwritten before each replay",
+            "bytes_per_batch": 4096 * 3 * 36 * 8, "note": "3.5 MB per batch: latency-bound, not a roofline case",
+            "max_err_over_tol": r[0], "max_rel_err": r[1], "tolerance": "1e-11",
+            "cpu_baseline": {"value": cpu_v, "unit": METRIC, "cores": thr, "kind": "oracle",
+                             "sample": "the whole 4,096-matrix batch"}}
+        del A, X, R
+
+        # ---- 262,144 real FP32 matrices, orders uniform on 2..64, dense
+        b = wl.uneven_loguniform(1 << 18, nmin=2, nmax=64, seed=1002, layout=wl.LAYOUT_DENSE)
+        A = torch.from_numpy(b.A.astype(np.float32)).to(dev)
+        X = torch.zeros_like(A)
+        n = torch.from_numpy(b.n).to(dev)
+        off = torch.from_numpy(b.off).to(dev)
+        tuned = api.autotune(torch.float32, 64, layout=api.LAYOUT_DENSE, batch=16384, stream=stream)
+        plan = api.Plan(A, X, n, off, 64, fixed_orders=True)
+        plan_t = api.Plan(A, X, n, off, 64, fixed_orders=True, timing=True)
+        for _ in range(3):
+            plan.launch(stream)
+        ms = _event_ms(stream, lambda: plan.launch(stream), reps)
+        kms = {N: 0.0 for N in range(2, 65)}
+        for _ in range(3):
+            plan_t.launch(stream)
+        for _ in range(reps):
+            plan_t.launch(stream)
+            stream.synchronize()
+            for N in kms:
+                kms[N] += plan_t.kernel_ms(N) / reps
+        torch.cuda.synchronize()
+        buckets = {}
+        for N in range(2, 65):
+            cnt = int((b.n == N).sum())
+            nb = cnt * 2 * (N * (N + 1) // 2) * 4
+            buckets[str(N)] = {"matrices": cnt, "kernel_ms": kms[N], "gbs": nb / (kms[N] / 1e3) / 1e9,
+                               "frac": nb / (kms[N] / 1e3) / 1e9 / hbm}
+        idx = np.unique(np.random.default_rng(12).choice(b.batch, 1024, replace=False))
+        sb, Xo, cpu_v, thr, _ = _oracle_sample(b, idx, "f32")
+        Xg = X.cpu().numpy()
+        Xs = np.concatenate([Xg[b.off[k]:b.off[k] + int(b.n[k]) ** 2] for k in idx])
+        r = _dense_err_ratio(sb, Xs, Xo, fp64=False)
+        nbytes = alg_bytes(b.n, 4)
+        small = [buckets[str(N)]["frac"] for N in range(2, 33)]
+        out["uneven_f32_N2-64_x262144"] = {
+            "value": b.batch / (ms / 1e3), "unit": METRIC, "ms_per_step": ms, "layout": "dense row-major",
+            "launch": "cuda_graph: bucketing + one kernel per order present", "l2": "inputs larger than L2 (1.49 GB)",
+            "autotuned_variants": {str(k): v for k, v in tuned.items()},
+            "whole_step": {"achieved_gbs": nbytes / (ms / 1e3) / 1e9, "frac": nbytes / (ms / 1e3) / 1e9 / hbm,
+                           "algorithmic_bytes": nbytes},
+            "orders_2_32_frac": {"min": min(small), "median": float(np.median(small)), "max": max(small)},
+            "per_order": buckets,
+            "bytes_rule": "2 * N(N+1)/2 * 4 B per matrix (A upper read, X upper written)",
+            "peak": hbm, "peak_source": peak_kind + " (hbm_gbs)",
+            "max_err_over_tol": r[0], "max_rel_err": r[1],
+            "cpu_baseline": {"value": cpu_v, "unit": METRIC, "cores": thr, "kind": "oracle",
+                             "sample": f"{len(idx)} seeded matrices of the batch"}}
+        plan.close()
+        plan_t.close()
+        del A, X, n, off
+
+        # ---- 65,536 real FP32 matrices of order 32, kappa = 1e2: forward and adjoint
+        batch, N = 1 << 16, 32
+        b = wl.fixed_kappa(batch, N, 1e2, seed=1003, layout=wl.LAYOUT_DENSE)
+        A = torch.from_numpy(b.A.astype(np.float32)).to(dev).view(batch, N, N)
+        W = torch.from_numpy(wl.gaussian((batch, N, N), 1003).astype(np.float32)).to(dev)
+        X = torch.zeros_like(A)
+        dA = torch.empty_like(A)
+        fwd = lambda: api.inv(A, fill_lower=True, X=X, stream=stream)
+        bwd = lambda: api.backward(X, W, upper_param=True, dA=dA, stream=stream)
+        for _ in range(3):
+            fwd()
+            bwd()
+        ms_f = _event_ms(stream, fwd, reps)
+        ms_b = _event_ms(stream, bwd, reps)
+        torch.cuda.synchronize()
+        idx = np.arange(0, batch, batch // 64)
+        sb, Xo, cpu_v, thr, _ = _oracle_sample(b, idx, "f32")
+        Xs = X.cpu().numpy()[idx].reshape(-1)
+        r = _dense_err_ratio(sb, Xs, Xo, fp64=False)
+        fb, bb = batch * 2 * 528 * 4, batch * (528 + 2 * 1024) * 4
+        out["autograd_f32_N32_x65536"] = {
+            "value": batch / ((ms_f + ms_b) / 1e3), "unit": "matrices/s (forward + adjoint)",
+            "forward_ms": ms_f, "adjoint_ms": ms_b,
+            "forward": {"achieved_gbs": fb / (ms_f / 1e3) / 1e9, "frac": fb / (ms_f / 1e3) / 1e9 / hbm,
+                        "bytes_rule": "A upper read + X upper written, 2 * 528 * 4 B per matrix "
+                                      "(the full X is written: fill_lower)"},
+            "adjoint": {"achieved_gbs": bb / (ms_b / 1e3) / 1e9, "frac": bb / (ms_b / 1e3) / 1e9 / hbm,
+                        "bytes_rule": "X upper + G + dA dense, (528 + 2 * 1024) * 4 B per matrix"},
+            "l2": "inputs larger than L2 (268 MB per operand)",
+            "max_err_over_tol": r[0], "max_rel_err": r[1],
+            "cpu_baseline": {"value": cpu_v, "unit": "inverses/s (forward)", "cores": thr, "kind": "oracle",
+                             "sample": f"{len(idx)} evenly spaced matrices of the batch"}}
+        del A, W, X, dA, flush
+    return out
 
 
 def run_blocked(args, local_rank):
@@ -459,6 +644,9 @@ def run_ours(args, rank, world, local_rank):
         ms_e2e = timed(e2e_step, max(3, min(args.steps, 20)), "e2e")
     h2d = A_h.numel() * 8 + n_h.numel() * 4 + off_h.numel() * 8
     d2h = X_h.numel() * 8 + info_h.numel() * 4
+    # the other workloads last, so that nothing they leave allocated affects the legs above
+    if rank == 0 and not args.no_extra:
+        out["configs"] = extra_workloads(dev, stream, args.steps)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,

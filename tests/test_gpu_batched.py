@@ -213,6 +213,39 @@ def test_plan_fixed_orders():
     p.close()
 
 
+def test_forked_classes_match_sequential(orc):
+    """Many orders (2..64): the class kernels run side by side on forked
+    streams (eager call, and parallel branches of a plan); a timing plan runs
+    them one after another.  All three give bit-identical X and info, and X
+    matches the oracle."""
+    import torch
+    from paper_1111_4144_gb300 import api
+    b = wl.uneven_loguniform(3000, nmin=2, nmax=64, seed=21, layout=0)
+    A_np, _ = cast_batch(b, "f32")
+    A = torch.from_numpy(A_np).cuda()
+    n = torch.from_numpy(b.n).cuda()
+    off = torch.from_numpy(b.off).cuda()
+    outs = []
+    for timing in (False, True):
+        X = torch.full_like(A, float("nan"))
+        p = api.Plan(A, X, n, off, 64, fixed_orders=True, timing=timing)
+        p.launch()
+        p.launch()
+        torch.cuda.synchronize()
+        outs.append((X.cpu().numpy(), p.info.cpu().numpy()))
+        p.close()
+    Xe, ie, _ = run_inv(b, "f32", mixed=True)
+    for Xg, ig in outs:
+        assert np.array_equal(ig, ie)
+        for k in range(b.batch):
+            o, N = int(b.off[k]), int(b.n[k])
+            got = np.triu(Xg[o:o + N * N].reshape(N, N))
+            want = np.triu(Xe[o:o + N * N].reshape(N, N))
+            assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), k
+    Ro, Xo, info_o, A_wide = oracle_inv(orc, b, "f32")
+    check_errors("f32", b, A_wide, upper_errors(b, Xe, Xo), "X")
+
+
 def test_plan_kernel_timing():
     import torch
     from paper_1111_4144_gb300 import api
