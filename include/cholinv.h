@@ -23,7 +23,14 @@
  *   Stream.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
  *     default stream).  Calls only enqueue work and never synchronise, so
  *     they may be captured into a CUDA graph; errors found on the device are
- *     reported through `info` and chol_last_device_error().
+ *     reported through `info` and chol_last_device_error().  A batched call
+ *     that launches kernels for 8 or more orders forks them onto side streams
+ *     and joins them back into `stream` before it returns (within a capture:
+ *     parallel branches of the graph).  The side streams (8 non-blocking
+ *     streams and 9 events per host thread and device) are created by the
+ *     first such call made outside a capture and kept until the process
+ *     ends; a call inside a capture before they exist runs its orders in
+ *     sequence on `stream`.
  *   Element types.  CHOL_F32 float, CHOL_F64 double, CHOL_C64 complex float
  *     (interleaved re, im floats), CHOL_C128 complex double.
  *   Sizes and offsets.  Matrix b has order n[b] and starts at element off[b]
