@@ -15,6 +15,9 @@ Function map (paper passages are cited in ``oracle.c``):
   gj(A)                 long-double Gauss-Jordan -> full inverse (independent)
   grad(X, G)            dA = -X (G+G^H)/2 X
   inv_batch(...)        batched driver over per-matrix sizes and offsets
+  nonhermitian_inverse  Sec. III.C: D^{-1} = D^* (D D^*)^{-1}
+  mmse_filter(H, s2)    (H^* H + s2 I)^{-1} H^*, the consumer of the MIMO matrices
+The fixed-point emulation of the methods (Sec. IV.C) is ``fixedpoint.py``.
 """
 from __future__ import annotations
 
@@ -211,6 +214,37 @@ def full_hermitian(Xu):
     U = np.triu(Xu)
     L = np.conj(np.triu(Xu, 1)).T
     return U + L
+
+
+def nonhermitian_inverse(D):
+    """Sec. III.C: the inverse of an arbitrary square D through the Hermitian
+    A = D D^* (product by numpy), A^{-1} by the proposed method (Cholesky,
+    Eqs. 3-4, then Sec. IV.A), and D^{-1} = D^* A^{-1}.  Returns (D^{-1}, info);
+    info != 0 (D singular to working precision) gives None."""
+    D = np.asarray(D)
+    cplx = np.iscomplexobj(D)
+    D = D.astype(np.complex128 if cplx else np.float64)
+    A = D @ np.conj(D).T
+    _, Xu, info = inverse(A)
+    if info:
+        return None, info
+    return np.conj(D).T @ full_hermitian(Xu), 0
+
+
+def mmse_filter(H, sigma2):
+    """W = (H^* H + sigma2 I)^{-1} H^* for an M x N channel H (M >= N): the
+    Hermitian inverse by the proposed method, then one product (numpy).  The
+    matrices of the MIMO workload are these A = H^* H + sigma2 I; W is their
+    usual consumer (not a formula of the paper).  Returns (W, info)."""
+    H = np.asarray(H)
+    cplx = np.iscomplexobj(H)
+    H = H.astype(np.complex128 if cplx else np.float64)
+    N = H.shape[1]
+    A = np.conj(H).T @ H + sigma2 * np.eye(N)
+    _, Xu, info = inverse(A)
+    if info:
+        return None, info
+    return full_hermitian(Xu) @ np.conj(H).T, 0
 
 
 def inv_batch(A_flat, n, off, layout, cplx, want_R=False, fill_lower=False, nthreads=None):
