@@ -10,6 +10,11 @@ step.  Prints one JSON line.
 --impl reference times the CPU FP64 oracle (the plain C implementation the
 tests check against) on this machine's host cores.  Under torchrun each rank
 inverts its own batch (weak scaling; no data-path collective).
+
+After the timed legs, rank 0 adds a `configs` object that times the other
+batched workloads (4,096 FP64 order-8 matrices; 262,144 FP32 matrices of
+orders 2..64; forward + adjoint of 65,536 FP32 order-32 matrices), each with
+an oracle sample as its CPU baseline and accuracy check; --no-extra skips it.
 """
 from __future__ import annotations
 
