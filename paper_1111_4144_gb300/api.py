@@ -34,6 +34,25 @@ def _need_cuda(*ts):
             raise ValueError("tensors must be contiguous")
 
 
+def _like(name, t, ref):
+    """An output buffer supplied by the caller must match its input in dtype
+    and element count (the kernels write as many elements as they read)."""
+    if t is None:
+        return
+    if t.dtype != ref.dtype:
+        raise ValueError(f"{name} must have dtype {ref.dtype}, not {t.dtype}")
+    if t.numel() != ref.numel():
+        raise ValueError(f"{name} must have {ref.numel()} elements, not {t.numel()}")
+
+
+def _per_matrix(info, off, batch):
+    """info (int32) and off (int64) need an entry for every matrix."""
+    if info is not None and (info.dtype != torch.int32 or info.numel() < batch):
+        raise ValueError(f"info must be int32 with at least {batch} entries")
+    if off is not None and off.numel() < batch:
+        raise ValueError(f"off must have at least {batch} entries")
+
+
 def _p(t):
     return None if t is None else t.data_ptr()
 
@@ -82,6 +101,9 @@ def inv(A, n=None, off=None, max_n=None, *, layout=LAYOUT_DENSE, prec=L.CHOL_PRE
     _need_cuda(A, X, R, info)
     dt = dtype_code(A)
     batch, max_n = _geometry(A, n, off, max_n, layout)
+    _like("X", X, A)
+    _like("R", R, A)
+    _per_matrix(info, off, batch)
     o = L.opts(prec, refine_steps, int(fill_lower), layout, flags)
     if X is None:
         X = torch.zeros_like(A)
@@ -132,6 +154,8 @@ def factor(A, n=None, off=None, max_n=None, *, layout=LAYOUT_DENSE, flags=0, R=N
     _need_cuda(A, R, info)
     dt = dtype_code(A)
     batch, max_n = _geometry(A, n, off, max_n, layout)
+    _like("R", R, A)
+    _per_matrix(info, off, batch)
     o = L.opts(L.CHOL_PREC_NATIVE, 0, 0, layout, flags)
     if R is None:
         R = torch.zeros_like(A)
@@ -158,6 +182,11 @@ def backward(X, G, n=None, off=None, xoff=None, max_n=None, *, layout=LAYOUT_DEN
     if G.dtype != X.dtype:
         raise ValueError("X and G must have the same dtype")
     batch, max_n = _geometry(G, n, off, max_n, LAYOUT_DENSE)
+    _like("dA", dA, G)
+    if n is None and off is None and xoff is None and layout == LAYOUT_DENSE:
+        _like("X", X, G)
+    _per_matrix(None, off, batch)
+    _per_matrix(None, xoff, batch)
     if dA is None:
         dA = torch.empty_like(G)
     flags = L.CHOL_FLAG_GRAD_UPPER if upper_param else 0
@@ -231,6 +260,9 @@ class Plan:
         _need_cuda(A, X, R, info)
         dt = dtype_code(A)
         batch, max_n = _geometry(A, n, off, max_n, layout)
+        _like("X", X, A)
+        _like("R", R, A)
+        _per_matrix(info, off, batch)
         o = L.opts(prec, refine_steps, int(fill_lower), layout, flags)
         self.info = info if info is not None else torch.empty(batch, dtype=torch.int32, device=A.device)
         self.ws, nbytes = workspace(L.CHOL_CALL_INV, dt, batch, max_n, n is not None, o, A.device)

@@ -1,0 +1,76 @@
+"""The PyTorch binding rejects mismatched output buffers and short per-matrix
+arrays before it calls the library (these checks run on the host; the C call
+is replaced by a stub that records that it was reached, and CPU tensors stand
+in for device ones)."""
+import types
+
+import pytest
+import torch
+
+from paper_1111_4144_gb300 import _lib, api
+
+
+@pytest.fixture()
+def stubbed(monkeypatch):
+    _lib.load(build_if_missing=True)
+    calls = []
+
+    def stub(name):
+        def f(*args):
+            calls.append(name)
+            return 0
+        return f
+
+    for name in ("chol_inv_batched", "chol_factor_batched", "chol_inv_backward"):
+        monkeypatch.setattr(_lib, name, stub(name))
+    monkeypatch.setattr(api, "_need_cuda", lambda *ts: None)
+    return calls
+
+
+STREAM = types.SimpleNamespace(cuda_stream=0)
+
+
+def test_inv_accepts_matching_buffers(stubbed):
+    A = torch.zeros(5, 4, 4)
+    api.inv(A, X=torch.zeros_like(A), R=torch.zeros_like(A), want_R=True,
+            info=torch.zeros(5, dtype=torch.int32), stream=STREAM)
+    assert stubbed == ["chol_inv_batched"]
+
+
+@pytest.mark.parametrize("bad", ["X_short", "X_dtype", "R_short", "info_short", "info_dtype", "off_short"])
+def test_inv_rejects_mismatched_buffers(stubbed, bad):
+    A = torch.zeros(5, 4, 4)
+    kw = {"stream": STREAM}
+    n = off = None
+    if bad == "X_short":
+        kw["X"] = torch.zeros(4, 4, 4)
+    elif bad == "X_dtype":
+        kw["X"] = torch.zeros(5, 4, 4, dtype=torch.float64)
+    elif bad == "R_short":
+        kw["R"] = torch.zeros(5 * 16 - 1)
+        kw["want_R"] = True
+    elif bad == "info_short":
+        kw["info"] = torch.zeros(4, dtype=torch.int32)
+    elif bad == "info_dtype":
+        kw["info"] = torch.zeros(5, dtype=torch.int64)
+    else:
+        A = torch.zeros(80)
+        n = torch.full((5,), 4, dtype=torch.int32)
+        off = torch.arange(4, dtype=torch.int64) * 16
+    with pytest.raises(ValueError):
+        api.inv(A, n, off, 4, **kw)
+    assert stubbed == []
+
+
+def test_factor_and_backward_checks(stubbed):
+    A = torch.zeros(3, 5, 5)
+    with pytest.raises(ValueError):
+        api.factor(A, R=torch.zeros(3, 5, 4), stream=STREAM)
+    with pytest.raises(ValueError):
+        api.backward(A, torch.zeros_like(A), dA=torch.zeros(3, 5, 5, dtype=torch.float64), stream=STREAM)
+    with pytest.raises(ValueError):
+        api.backward(torch.zeros(2, 5, 5), torch.zeros_like(A), stream=STREAM)
+    assert stubbed == []
+    api.factor(A, R=torch.zeros_like(A), stream=STREAM)
+    api.backward(A, torch.zeros_like(A), dA=torch.zeros_like(A), stream=STREAM)
+    assert stubbed == ["chol_factor_batched", "chol_inv_backward"]
