@@ -143,6 +143,13 @@ class HostInv:
                 raise ValueError("host tensors must be contiguous CPU tensors")
         if (n_host is not None) != self.sizes:
             raise ValueError("n_host must be given exactly when the plan was made with sizes=True")
+        if _DT.get(A_host.dtype) != self.dt:
+            raise ValueError(f"A_host has dtype {A_host.dtype}; this HostInv was made for another")
+        _like("X_host", X_host, A_host)
+        for name, t, dt in (("info_host", info_host, torch.int32), ("n_host", n_host, torch.int32),
+                            ("off_host", off_host, torch.int64)):
+            if t is not None and (t.dtype != dt or t.numel() < self.batch):
+                raise ValueError(f"{name} must be {dt} with at least {self.batch} entries")
         st = L.chol_inv_batched_host(self.dt, self.batch, _p(n_host), _p(off_host), self.max_n, _p(A_host),
                                      _p(X_host), _p(info_host), self.o, _p(self.ws), self.nbytes, _s(stream))
         L.check(st, "chol_inv_batched_host")

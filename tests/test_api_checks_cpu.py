@@ -74,3 +74,33 @@ def test_factor_and_backward_checks(stubbed):
     api.factor(A, R=torch.zeros_like(A), stream=STREAM)
     api.backward(A, torch.zeros_like(A), dA=torch.zeros_like(A), stream=STREAM)
     assert stubbed == ["chol_factor_batched", "chol_inv_backward"]
+
+
+@pytest.mark.parametrize("bad", [None, "A_dtype", "X_short", "info_short", "n_dtype", "off_short"])
+def test_host_inv_checks(monkeypatch, bad):
+    _lib.load(build_if_missing=True)
+    calls = []
+    monkeypatch.setattr(_lib, "chol_inv_batched_host", lambda *a: calls.append(1) or 0)
+    h = api.HostInv(torch.complex64, 10, 4, sizes=True, layout=api.LAYOUT_PACKED, device=torch.device("cpu"))
+    A = torch.zeros(100, dtype=torch.complex64)
+    X = torch.zeros_like(A)
+    n = torch.full((10,), 4, dtype=torch.int32)
+    off = torch.arange(10, dtype=torch.int64) * 10
+    info = torch.zeros(10, dtype=torch.int32)
+    if bad == "A_dtype":
+        A, X = A.to(torch.complex128), X.to(torch.complex128)
+    elif bad == "X_short":
+        X = torch.zeros(99, dtype=torch.complex64)
+    elif bad == "info_short":
+        info = torch.zeros(9, dtype=torch.int32)
+    elif bad == "n_dtype":
+        n = n.to(torch.int64)
+    elif bad == "off_short":
+        off = off[:9]
+    if bad is None:
+        h(A, X, n, off, info, stream=STREAM)
+        assert calls == [1]
+    else:
+        with pytest.raises(ValueError):
+            h(A, X, n, off, info, stream=STREAM)
+        assert calls == []
