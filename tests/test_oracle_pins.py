@@ -321,3 +321,36 @@ def test_batch_driver_matches_single(orc, layout, cplx):
         R, _ = orc.chol(M)
         assert np.array_equal(b.matrix(k), orc.inv_rows(R))
         assert np.array_equal(br.matrix(k), R)
+
+
+# --------------------------------------------------------------------------
+# the block form of Sec. IV.A used by the large-order path (a reading)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("n,b", [(37, 8), (64, 16), (50, 50), (9, 4)])
+def test_block_form_reading(orc, n, b, cplx):
+    """Row block I of R X = S (S's diagonal block is R_II^{-*}, the blocks
+    right of it zero) gives, for block rows I = last..first,
+        X_I,>I = -R_II^{-1} R_I,>I X_>I,>I
+        X_II   =  R_II^{-1} (R_II^{-*} - R_I,>I X_>I,I),  X_>I,I = X_I,>I^*.
+    Carried out with numpy's triangular inverses on the oracle's R, it gives
+    the oracle's element recurrence to rounding, ragged last block included."""
+    rng = np.random.default_rng(900 + n + b + cplx)
+    A = rand_hpd(rng, n, cplx)
+    R, info = orc.chol(A)
+    assert info == 0
+    X = np.zeros_like(R)
+    starts = list(range(0, n, b))
+    for s in reversed(starts):
+        e = min(s + b, n)
+        Rii_inv = np.linalg.inv(R[s:e, s:e])
+        if e < n:
+            X[s:e, e:] = -Rii_inv @ (R[s:e, e:] @ X[e:, e:])
+            X[e:, s:e] = np.conj(X[s:e, e:]).T
+            Z = R[s:e, e:] @ X[e:, s:e]
+        else:
+            Z = np.zeros((e - s, e - s), dtype=R.dtype)
+        X[s:e, s:e] = Rii_inv @ (np.conj(Rii_inv).T - Z)
+    ref = full(orc.inv_rows(R))
+    kap = np.linalg.cond(A)
+    assert np.linalg.norm(X - ref) / np.linalg.norm(ref) <= 50 * n * kap * 2.0 ** -53
