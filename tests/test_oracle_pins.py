@@ -354,3 +354,31 @@ def test_block_form_reading(orc, n, b, cplx):
     ref = full(orc.inv_rows(R))
     kap = np.linalg.cond(A)
     assert np.linalg.norm(X - ref) / np.linalg.norm(ref) <= 50 * n * kap * 2.0 ** -53
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_refinement_indicator_bounds(orc, cplx):
+    """The automatic-refinement indicator gamma = max_i a_ii x_ii lies in
+    [1, (1 + kappa)^2 / (4 kappa)] with kappa = kappa_2(A): a_ii x_ii =
+    (e_i^* A e_i)(e_i^* A^{-1} e_i) is >= 1 by Cauchy-Schwarz and <= the
+    Kantorovich bound.  Both ends are reached: gamma = 1 for a diagonal A,
+    the upper bound for A = Q diag(1, kappa) Q^T with Q a 45-degree
+    rotation."""
+    rng = np.random.default_rng(31 + cplx)
+    for n in (2, 5, 12, 30):
+        for shift in (n, 1e-2, 1e-5):
+            A = rand_hpd(rng, n, cplx, shift=shift)
+            _, Xu, info = orc.inverse(A)
+            assert info == 0
+            g = float(np.max(np.real(np.diag(A)) * np.real(np.diag(Xu))))
+            kap = np.linalg.cond(A)
+            assert 1.0 - 1e-12 <= g <= (1 + kap) ** 2 / (4 * kap) * (1.0 + 1e-9), (g, kap)
+    _, Xu, _ = orc.inverse(np.diag([3.0, 7.0, 0.5]))
+    assert np.max(np.diag(np.diag([3.0, 7.0, 0.5])) * np.diag(Xu)) == 1.0
+    c = np.sqrt(0.5)
+    Q = np.array([[c, -c], [c, c]])
+    kappa = 1e4
+    A = Q @ np.diag([1.0, kappa]) @ Q.T
+    _, Xu, _ = orc.inverse(A)
+    g = float(np.max(np.diag(A) * np.diag(Xu)))
+    assert g == pytest.approx((1 + kappa) ** 2 / (4 * kappa), rel=1e-12)
