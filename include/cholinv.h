@@ -160,7 +160,8 @@ chol_status_t chol_factor_batched(chol_dtype_t dt, int32_t batch, const int32_t*
  *   X <- X + X (I - A X), the residual accumulated in FP64 from exact
  *   products of the FP32 operands.  refine_steps = -1 (automatic) refines a
  *   matrix once when gamma = max_i a_ii x_ii > 4096; gamma lies in
- *   [1, kappa_2(A)], so well-conditioned matrices are left as they are.
+ *   [1, (1 + kappa)^2 / (4 kappa)] with kappa = kappa_2(A), so only
+ *   matrices with kappa above about 16,382 can be refined.
  *   Refinement reads A again after X is formed, so X == A is rejected
  *   (CHOL_ERR_ARG) when refine_steps != 0.  CHOL_FLAG_PIVOT64 accumulates
  *   the sum of Eq. 3 in FP64 for F32 / C64 (pivots lost to cancellation).

@@ -29,9 +29,11 @@ CHOL_D cpx<double> widen(cpx<float> v) { return {(double)v.re, (double)v.im}; }
 CHOL_D float narrow(double v) { return (float)v; }
 CHOL_D cpx<float> narrow(cpx<double> v) { return {(float)v.re, (float)v.im}; }
 
-// gamma = max_i a_ii x_ii lies in [1, kappa_2(A)] for a Hermitian positive
-// definite A (a_ii <= lambda_max and x_ii <= 1/lambda_min).  The automatic
-// mode refines a matrix once when gamma exceeds this bound.
+// gamma = max_i a_ii x_ii lies in [1, (1 + kappa)^2 / (4 kappa)], kappa =
+// kappa_2(A), for a Hermitian positive definite A: a_ii x_ii is
+// (e_i^* A e_i)(e_i^* A^{-1} e_i), at least 1 by Cauchy-Schwarz and at most
+// the Kantorovich bound.  The automatic mode refines a matrix once when gamma
+// exceeds this threshold (reachable for kappa above about 16,382).
 constexpr double kAutoRefineGamma = 4096.0;
 
 template <typename V>
