@@ -224,9 +224,11 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "batch": BATCH, "sizes": list(SIZES), "layout": "packed_upper"},
+            "config": {"workload": WORKLOAD if b.batch == BATCH and sizes == SIZES else
+                       f"mimo_covariance_c64_N{'-'.join(map(str, sizes))}_x{b.batch}_packed",
+                       "batch": b.batch, "sizes": list(sizes), "layout": "packed_upper"},
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle",
-                             "sample": f"full {BATCH}-matrix batch per step, FP64 oracle, {threads} threads"},
+                             "sample": f"full {b.batch}-matrix batch per step, FP64 oracle, {threads} threads"},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t_start}
     print(json.dumps(line), flush=True)
