@@ -15,6 +15,8 @@ Function map (paper passages are cited in ``oracle.c``):
   gj(A)                 long-double Gauss-Jordan -> full inverse (independent)
   grad(X, G)            dA = -X (G+G^H)/2 X
   inv_batch(...)        batched driver over per-matrix sizes and offsets
+  chol_mt, inv_rows_mt  chol / inv_rows for one large real matrix on several threads (same bits)
+  solve_cols(R, cols)   chosen columns of A^{-1} by Eq. 15's two triangular solves (every row)
   nonhermitian_inverse  Sec. III.C: D^{-1} = D^* (D D^*)^{-1}
   mmse_filter(H, s2)    (H^* H + s2 I)^{-1} H^*, the consumer of the MIMO matrices
 The fixed-point emulation of the methods (Sec. IV.C) is ``fixedpoint.py``.
@@ -75,6 +77,12 @@ def _load():
                 f = getattr(lib, name); f.restype = ctypes.c_int; f.argtypes = [ctypes.c_int, _d, _d]
             for name in ("orc_grad_d", "orc_grad_z"):
                 f = getattr(lib, name); f.restype = None; f.argtypes = [ctypes.c_int, _d, _d, _d]
+            lib.orc_chol_mt_d.restype = ctypes.c_int
+            lib.orc_chol_mt_d.argtypes = [ctypes.c_int, _d, _d, ctypes.c_int]
+            lib.orc_inv_rows_mt_d.restype = None
+            lib.orc_inv_rows_mt_d.argtypes = [ctypes.c_int, _d, _d, ctypes.c_int]
+            lib.orc_solve_cols_d.restype = None
+            lib.orc_solve_cols_d.argtypes = [ctypes.c_int, _d, ctypes.c_int, _i32, _d, ctypes.c_int]
             lib.orc_inv_batch.restype = ctypes.c_int
             lib.orc_inv_batch.argtypes = [ctypes.c_int, ctypes.c_longlong, _i32, _ll, ctypes.c_int, ctypes.c_int,
                                           _d, _d, _d, _i32, ctypes.c_int]
@@ -198,6 +206,42 @@ def grad(X, G):
     dA = np.zeros_like(X)
     (lib.orc_grad_z if cplx else lib.orc_grad_d)(n, _ptr(X), _ptr(G), _ptr(dA))
     return dA
+
+
+def chol_mt(A, nthreads=None):
+    """chol(A) for one real matrix with the entries of each row split over
+    threads; the same operations in the same order, so the same bits."""
+    lib = _load()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    R = np.zeros_like(A)
+    info = lib.orc_chol_mt_d(n, _ptr(A), _ptr(R), int(nthreads or os.cpu_count() or 1))
+    return R, info
+
+
+def inv_rows_mt(R, nthreads=None):
+    """inv_rows(R) for one real matrix, threaded like chol_mt (the same bits)."""
+    lib = _load()
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    n = R.shape[0]
+    X = np.zeros_like(R)
+    lib.orc_inv_rows_mt_d(n, _ptr(R), _ptr(X), int(nthreads or os.cpu_count() or 1))
+    return X
+
+
+def solve_cols(R, cols, nthreads=None):
+    """Columns `cols` of A^{-1} (A = R^T R, real) by the two triangular solves
+    of Eq. 15, R^T y = e_j then R x = y, each column on its own (every row,
+    no values taken from other columns).  Returns an array [len(cols), n]
+    whose row c is column cols[c] of A^{-1}."""
+    lib = _load()
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    n = R.shape[0]
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    Xc = np.zeros((len(cols), n), dtype=np.float64)
+    lib.orc_solve_cols_d(n, _ptr(R), len(cols), cols.ctypes.data_as(_i32), _ptr(Xc),
+                         int(nthreads or os.cpu_count() or 1))
+    return Xc
 
 
 def inverse(A):

@@ -26,6 +26,10 @@
  *   orc_gj_{ld,lz}      Gauss-Jordan in long double (an independent method, not in the paper)
  *   orc_grad_{d,z}      dA = -X sym(G) X (adjoint of the inverse; not in the paper)
  *   orc_inv_batch       batched driver over per-matrix sizes/offsets (threads over matrices)
+ *   orc_chol_mt_d       orc_chol_d for one large matrix, the entries of each row split over threads
+ *   orc_inv_rows_mt_d   orc_inv_rows_d for one large matrix, the same way
+ *   orc_solve_cols_d    chosen columns of A^{-1} by the two triangular solves of Eq. 15
+ *                       (R^* y = e_j, then R x = y), every row of each column, threads over columns
  *
  * Multiply counting (Table 1): every function that takes a `long long* mults`
  * adds one for each multiply inside an inner sum (a complex multiply counts as
@@ -608,4 +612,167 @@ int orc_inv_batch(int cplx, long long batch, const int* n, const long long* off,
     for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
     free(jobs); free(th);
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Large single matrices (threads).  orc_chol_mt_d and orc_inv_rows_mt_d     */
+/* perform exactly the operations of orc_chol_d and orc_inv_rows_d, with the */
+/* same operands in the same order for every entry (so the results are the  */
+/* same bits); only the entries of one row are shared out over threads, and */
+/* a transposed copy keeps each inner sum on contiguous memory.              */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int n, t, nt;
+    const double* A; double* R; double* L;   /* L[j*n+k] = r_kj (k <= j) */
+    double* X; double* F;                    /* F: full symmetric X (F[j*n+k] = x~_kj) */
+    double* piv; int* info;
+    pthread_barrier_t* bar;
+} orc_mt;
+
+static void* orc_chol_mt_worker(void* p)
+{
+    orc_mt* w = (orc_mt*)p;
+    const int n = w->n;
+    double* L = w->L;
+    for (int i = 0; i < n; ++i) {
+        if (w->t == 0) {
+            /* Eq. 3 */
+            double t = w->A[(size_t)i * n + i];
+            for (int k = 0; k < i; ++k) t -= L[(size_t)i * n + k] * L[(size_t)i * n + k];
+            if (!(t > 0.0) || !isfinite(t)) { if (*w->info == 0) *w->info = i + 1; }
+            *w->piv = sqrt(t);
+            L[(size_t)i * n + i] = *w->piv;
+        }
+        pthread_barrier_wait(w->bar);
+        if (*w->info) return NULL;
+        const double rii = *w->piv;
+        /* Eq. 4 for j = i+1..n-1, this thread's share */
+        for (int j = i + 1 + w->t; j < n; j += w->nt) {
+            double s = w->A[(size_t)i * n + j];
+            for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+            L[(size_t)j * n + i] = s / rii;
+        }
+        pthread_barrier_wait(w->bar);
+    }
+    return NULL;
+}
+
+static void orc_run_mt(orc_mt* base, int nthreads, void* (*fn)(void*))
+{
+    pthread_barrier_t bar;
+    pthread_barrier_init(&bar, NULL, (unsigned)nthreads);
+    orc_mt* jobs = (orc_mt*)calloc((size_t)nthreads, sizeof(orc_mt));
+    pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+    for (int t = 0; t < nthreads; ++t) { jobs[t] = *base; jobs[t].t = t; jobs[t].nt = nthreads; jobs[t].bar = &bar; }
+    for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, fn, &jobs[t]);
+    fn(&jobs[0]);
+    for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+    pthread_barrier_destroy(&bar);
+    free(jobs); free(th);
+}
+
+/* Cholesky (Eqs. 3-4) as orc_chol_d; returns 0 or the failing 1-based row. */
+int orc_chol_mt_d(int n, const double* A, double* R, int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    double* L = (double*)calloc((size_t)n * n, sizeof(double));
+    double piv = 0.0;
+    int info = 0;
+    orc_mt base = { n, 0, 1, A, R, L, NULL, NULL, &piv, &info, NULL };
+    orc_run_mt(&base, nthreads, orc_chol_mt_worker);
+    memset(R, 0, sizeof(double) * (size_t)n * n);
+    if (info == 0)
+        for (int j = 0; j < n; ++j)
+            for (int k = 0; k <= j; ++k) R[(size_t)k * n + j] = L[(size_t)j * n + k];
+    free(L);
+    return info;
+}
+
+static void* orc_inv_mt_worker(void* p)
+{
+    orc_mt* w = (orc_mt*)p;
+    const int n = w->n;
+    const double* R = w->R;
+    double* F = w->F;
+    for (int i = n - 1; i >= 0; --i) {
+        const double rii = R[(size_t)i * n + i];
+        /* x_ij, j = i+1..n-1 (Sec. IV.A); F's row j holds x~_kj for every k > i */
+        for (int j = i + 1 + w->t; j < n; j += w->nt) {
+            double s = 0.0;
+            for (int k = i + 1; k < n; ++k) s += R[(size_t)i * n + k] * F[(size_t)j * n + k];
+            const double x = (0.0 - s) / rii;
+            F[(size_t)i * n + j] = x;
+            F[(size_t)j * n + i] = x;
+        }
+        pthread_barrier_wait(w->bar);
+        if (w->t == 0) {
+            double s = 0.0;
+            for (int k = i + 1; k < n; ++k) s += R[(size_t)i * n + k] * F[(size_t)i * n + k];
+            F[(size_t)i * n + i] = (1.0 / rii - s) / rii;
+        }
+        pthread_barrier_wait(w->bar);
+    }
+    return NULL;
+}
+
+/* Proposed inverse (Sec. IV.A) as orc_inv_rows_d: upper half of X, lower zero. */
+void orc_inv_rows_mt_d(int n, const double* R, double* X, int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    double* F = (double*)calloc((size_t)n * n, sizeof(double));
+    orc_mt base = { n, 0, 1, NULL, (double*)R, NULL, NULL, F, NULL, NULL, NULL };
+    orc_run_mt(&base, nthreads, orc_inv_mt_worker);
+    memset(X, 0, sizeof(double) * (size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j) X[(size_t)i * n + j] = F[(size_t)i * n + j];
+    free(F);
+}
+
+/* Columns cols[0..ncols-1] of A^{-1} = R^{-1} R^{-*}, each from the two      */
+/* triangular solves of Eq. 15 for the right-hand side e_j: the forward     */
+/* solve R^* y = e_j (y_k = 0 for k < j; each y_k's terms in ascending l,    */
+/* taken column by column over R's rows), then the back solve R x = y over  */
+/* every row.  Xc[c*n + i] = (A^{-1})_{i, cols[c]}.  Threads over columns.   */
+typedef struct { int n, ncols, t, nt; const double* R; const int* cols; double* Xc; } orc_cols_job;
+
+static void* orc_cols_worker(void* p)
+{
+    orc_cols_job* w = (orc_cols_job*)p;
+    const int n = w->n;
+    const double* R = w->R;
+    double* y = (double*)calloc((size_t)n, sizeof(double));
+    for (int c = w->t; c < w->ncols; c += w->nt) {
+        const int j = w->cols[c];
+        double* x = w->Xc + (size_t)c * n;
+        /* forward: y_k = (delta_kj - sum_{l<k} r_lk y_l) / r_kk */
+        for (int k = 0; k < n; ++k) y[k] = (k == j) ? 1.0 : 0.0;
+        for (int l = j; l < n; ++l) {
+            y[l] = y[l] / R[(size_t)l * n + l];
+            for (int k = l + 1; k < n; ++k) y[k] -= R[(size_t)l * n + k] * y[l];
+        }
+        /* back: x_i = (y_i - sum_{l>i} r_il x_l) / r_ii, i = n-1..0 */
+        for (int i = n - 1; i >= 0; --i) {
+            double s = 0.0;
+            for (int l = i + 1; l < n; ++l) s += R[(size_t)i * n + l] * x[l];
+            x[i] = (y[i] - s) / R[(size_t)i * n + i];
+        }
+    }
+    free(y);
+    return NULL;
+}
+
+void orc_solve_cols_d(int n, const double* R, int ncols, const int* cols, double* Xc, int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > ncols) nthreads = ncols > 0 ? ncols : 1;
+    orc_cols_job* jobs = (orc_cols_job*)calloc((size_t)nthreads, sizeof(orc_cols_job));
+    pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+    for (int t = 0; t < nthreads; ++t) {
+        orc_cols_job j = { n, ncols, t, nthreads, R, cols, Xc };
+        jobs[t] = j;
+    }
+    for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, orc_cols_worker, &jobs[t]);
+    orc_cols_worker(&jobs[0]);
+    for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+    free(jobs); free(th);
 }

@@ -382,3 +382,58 @@ def test_refinement_indicator_bounds(orc, cplx):
     _, Xu, _ = orc.inverse(A)
     g = float(np.max(np.diag(A) * np.diag(Xu)))
     assert g == pytest.approx((1 + kappa) ** 2 / (4 * kappa), rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# the large-matrix forms: threaded Cholesky and inverse, column solves
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 7, 33, 130])
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_threaded_forms_are_the_serial_ones(orc, n, threads):
+    """chol_mt / inv_rows_mt split each row's entries over threads: the same
+    operations as the pinned serial chol / inv_rows, so the same bits."""
+    rng = np.random.default_rng(900 + n)
+    A = rand_hpd(rng, n, False)
+    R, info = orc.chol(A)
+    R2, info2 = orc.chol_mt(A, threads)
+    assert info == info2 == 0 and np.array_equal(R, R2)
+    assert np.array_equal(orc.inv_rows(R), orc.inv_rows_mt(R, threads))
+    # a failing pivot is reported at the same row
+    A[n // 2, n // 2] = -1.0
+    assert orc.chol_mt(A, threads)[1] == orc.chol(A)[1] == n // 2 + 1
+
+
+@pytest.mark.parametrize("n", [1, 3, 8, 16, 33])
+def test_solve_cols_min_matrix_exact(orc, n):
+    """min(i, j) has R = all-ones upper and inverse tridiag(-1, 2, -1) with
+    x_nn = 1: every column from the two triangular solves is exact."""
+    i = np.arange(1, n + 1)
+    A = np.minimum.outer(i, i).astype(np.float64)
+    R, info = orc.chol(A)
+    T = 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    T[-1, -1] = 1.0
+    cols = np.arange(n)
+    assert np.array_equal(orc.solve_cols(R, cols, 3), T[:, cols].T)
+
+
+@pytest.mark.parametrize("n", [2, 6, 13, 40])
+def test_solve_cols_tridiagonal_closed_form(orc, n):
+    """tridiag(-1, 2, -1): (T^-1)_ij = min(i, j)(n + 1 - max(i, j))/(n + 1), 1-based."""
+    T = 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    R, _ = orc.chol(T)
+    i = np.arange(1, n + 1)
+    ref = np.minimum.outer(i, i) * (n + 1 - np.maximum.outer(i, i)) / (n + 1)
+    cols = np.array([0, n // 2, n - 1])
+    got = orc.solve_cols(R, cols)
+    assert np.allclose(got, ref[:, cols].T, rtol=0, atol=64 * n * 2.0 ** -52 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("n", [2, 4, 6])
+def test_solve_cols_gauss_jordan_long_double(orc, n):
+    rng = np.random.default_rng(950 + n)
+    A = rand_hpd(rng, n, False, shift=0.5)
+    R, _ = orc.chol(A)
+    ref = orc.gj(A)
+    kap = np.linalg.cond(A)
+    got = orc.solve_cols(R, np.arange(n), 2)
+    assert np.abs(got - ref.T).max() <= 1e-13 * kap * np.abs(ref).max()
