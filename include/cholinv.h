@@ -121,6 +121,18 @@ typedef enum {
                                      unit upper and D = diag(d_i), no square roots; X as for Cholesky.  R, when
                                      written, holds d_i on its diagonal (the unit diagonal is implied).  Batched
                                      path only (orders <= 64; one matrix per warp); not with CHOL_FLAG_PIVOT64 */
+#define CHOL_FLAG_PIVOT64_AUTO 0x40 /* F32/C64 batched calls: FP64 pivots only for the matrices that need them.
+                                     The FP32 pass watches Eq. 3 at every row i; a matrix whose argument
+                                     t_i falls below 2^-10 a_ii (cancellation: about 10 of FP32's 24 bits
+                                     lost), or is <= 0 or not finite, is not stored by that pass and is
+                                     factored and inverted again with the sum of Eq. 3 accumulated in FP64
+                                     (as CHOL_FLAG_PIVOT64), in a second kernel over the batch.  Since
+                                     t_i >= lambda_min and a_ii <= lambda_max, a matrix with kappa_2 < 2^10
+                                     is never redone.  info must not be NULL (CHOL_ERR_ARG): it carries the
+                                     list of matrices to redo between the two kernels.  The number redone
+                                     is counted on the device (chol_pivot64_redo_count).  FP64 value types
+                                     ignore the flag; the blocked path (max_n > 64) takes it as
+                                     CHOL_FLAG_PIVOT64.  Not with CHOL_FLAG_LDL */
 #define CHOL_FLAG_PLAN_ORDERS 0x10 /* chol_plan_inv_create only, batches with per-matrix sizes: read n once
                                      at creation (synchronously) and record kernels only for the orders
                                      present then, instead of one per order 1..max_n.  At every replay a
@@ -246,9 +258,10 @@ chol_status_t chol_inv_batched_host(chol_dtype_t dt, int32_t batch, const int32_
  *     call's contents (each call clears the counters it needs before use).
  *     Calls whose executions overlap on the GPU (different streams, or
  *     concurrent graph replays) race on it: serialise them.
- *   - Inputs, outputs, info and the stream are the caller's, as for
- *     chol_inv_batched; no cudaMalloc, cudaFree or allocating library
- *     routine is called.
+ *   - Inputs, outputs, info, opts and the stream are the caller's, as for
+ *     chol_inv_batched (refinement included: X == A is then rejected with
+ *     CHOL_ERR_ARG); no cudaMalloc, cudaFree or allocating library routine
+ *     is called.
  */
 #define CHOL_NOALLOC_MAX_BATCH 1048576
 chol_status_t chol_inv_batched_noalloc(chol_dtype_t dt, int32_t batch, const int32_t* n, const int64_t* off,
@@ -265,6 +278,11 @@ const char* chol_status_string(chol_status_t status);
 /* Synchronises `stream`, then reads and clears the device error word of the
  * current device (CHOL_OK if no kernel reported an error). */
 chol_status_t chol_last_device_error(void* stream);
+
+/* Synchronises `stream`, then reads and clears the number of matrices that
+ * CHOL_FLAG_PIVOT64_AUTO calls on the current device have redone with FP64
+ * pivots (Eq. 3) since the last read.  CHOL_ERR_ARG if count is NULL. */
+chol_status_t chol_pivot64_redo_count(void* stream, int64_t* count);
 
 /*
  * Autotuning (not in the paper).  Orders up to 32 have more than one
@@ -286,6 +304,33 @@ chol_status_t chol_tune_load(const char* cache_path);
 int32_t chol_tune_variants(chol_dtype_t dt, int32_t order);
 int32_t chol_tune_get(chol_dtype_t dt, int32_t order);
 chol_status_t chol_tune_set(chol_dtype_t dt, int32_t order, int32_t variant);
+
+/*
+ * Kernel timing of the blocked path (orders > 64; not in the paper).
+ * chol_blocked_timing(1) starts recording on the calling host thread (and
+ * clears what was recorded); from then on every blocked call that thread
+ * makes records a CUDA event pair, on the call's stream, around each product
+ * of these kinds, with the product's algorithmic flops (2 M N K, or the
+ * upper part only where only it is formed):
+ *   CHOL_BLK_TRAILING_UPDATE  A_>K,>K -= R_K,>K^* R_K,>K  (Eqs. 3-4 in block form)
+ *   CHOL_BLK_INVERSE_PRODUCT  R_I,>I X_>I,>I              (Sec. IV.A in block form)
+ *   CHOL_BLK_RESIDUAL         E = I - A X                 (refinement)
+ *   CHOL_BLK_CORRECTION       X E                         (refinement)
+ *   CHOL_BLK_WHOLE_CALL       each matrix's whole call, flops counted as n^3
+ * chol_blocked_timing(0) stops and frees the events.  The events cost
+ * launch time, so time a call without them for its throughput.
+ * chol_blocked_timing_read waits for the recorded events and returns the
+ * summed milliseconds, flops and number of products of one kind since
+ * recording started; CHOL_ERR_ARG for an unknown kind, NULL outputs or no
+ * recording on this thread.
+ */
+#define CHOL_BLK_TRAILING_UPDATE 0
+#define CHOL_BLK_INVERSE_PRODUCT 1
+#define CHOL_BLK_RESIDUAL 2
+#define CHOL_BLK_CORRECTION 3
+#define CHOL_BLK_WHOLE_CALL 4
+chol_status_t chol_blocked_timing(int32_t enable);
+chol_status_t chol_blocked_timing_read(int32_t kind, float* ms, double* flops, int32_t* launches);
 
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int32_t chol_version(void);

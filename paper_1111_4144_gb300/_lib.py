@@ -29,7 +29,10 @@ CHOL_FLAG_PLAN_TIMING = 0x4
 CHOL_FLAG_TF32_SINGLE = 0x8
 CHOL_FLAG_PLAN_ORDERS = 0x10
 CHOL_FLAG_LDL = 0x20
+CHOL_FLAG_PIVOT64_AUTO = 0x40
 CHOL_CALL_FACTOR, CHOL_CALL_INV, CHOL_CALL_BACKWARD, CHOL_CALL_INV_HOST = 0, 1, 2, 3
+CHOL_BLK_TRAILING_UPDATE, CHOL_BLK_INVERSE_PRODUCT, CHOL_BLK_RESIDUAL, CHOL_BLK_CORRECTION, CHOL_BLK_WHOLE_CALL = \
+    0, 1, 2, 3, 4
 CHOL_NOALLOC_MAX_BATCH = 1048576
 
 
@@ -53,6 +56,10 @@ SIGNATURES = {
     "chol_workspace_bytes": (c_size, [c_i32, c_i32, c_i32, c_i32, c_i32, ctypes.POINTER(chol_opts_t)]),
     "chol_status_string": (ctypes.c_char_p, [c_i32]),
     "chol_last_device_error": (c_i32, [c_vp]),
+    "chol_pivot64_redo_count": (c_i32, [c_vp, ctypes.POINTER(c_i64)]),
+    "chol_blocked_timing": (c_i32, [c_i32]),
+    "chol_blocked_timing_read": (c_i32, [c_i32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(c_i32)]),
     "chol_version": (c_i32, []),
     "chol_plan_inv_create": (c_i32, [ctypes.POINTER(c_vp), c_i32, c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp,
                                      c_vp, ctypes.POINTER(chol_opts_t), c_vp, c_size]),
@@ -140,6 +147,18 @@ def chol_status_string(*args):
 
 def chol_last_device_error(*args):
     return load().chol_last_device_error(*args)
+
+
+def chol_pivot64_redo_count(*args):
+    return load().chol_pivot64_redo_count(*args)
+
+
+def chol_blocked_timing(*args):
+    return load().chol_blocked_timing(*args)
+
+
+def chol_blocked_timing_read(*args):
+    return load().chol_blocked_timing_read(*args)
 
 
 def chol_version():

@@ -12,6 +12,8 @@
 
 // The per-device error word; kernels receive its address as an argument.
 __device__ int g_chol_error_word;
+// Matrices redone with FP64 pivots under CHOL_FLAG_PIVOT64_AUTO (per device).
+__device__ unsigned long long g_chol_redo_count;
 
 namespace cholinv {
 
@@ -24,6 +26,7 @@ struct DevState {
     bool init = false;
     int sms = 0;
     int* err = nullptr;
+    unsigned long long* redo = nullptr;
 };
 DevState g_dev[kMaxDevices];
 std::mutex g_dev_mu;
@@ -40,13 +43,16 @@ cudaError_t dev_state(DevState** out) {
         if (e != cudaSuccess) return e;
         e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.err), g_chol_error_word);
         if (e != cudaSuccess) return e;
+        e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.redo), g_chol_redo_count);
+        if (e != cudaSuccess) return e;
         s.init = true;
     }
     *out = &s;
     return cudaSuccess;
 }
 
-constexpr size_t kWsHeader = 1024;  // counts | starts | cursor (kClasses int32 each), padded
+constexpr size_t kWsHeader = 1024;  // counts | starts | cursor (kClasses int32 each) | done, padded
+static_assert((3 * kClasses + 1) * sizeof(int32_t) <= kWsHeader, "bucketing header overlaps the permutation");
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -74,8 +80,10 @@ chol_status_t check_common(chol_dtype_t dt, int32_t batch, int32_t max_n, const 
     if (o.layout != 0 && o.layout != 1) return CHOL_ERR_ARG;
     if (o.prec < CHOL_PREC_NATIVE || o.prec > CHOL_PREC_BF16_REFINE) return CHOL_ERR_ARG;
     if (o.refine_steps < -1 || o.refine_steps > 2) return CHOL_ERR_ARG;
-    if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER | CHOL_FLAG_LDL)) return CHOL_ERR_ARG;
-    if ((o.flags & CHOL_FLAG_LDL) && (o.flags & CHOL_FLAG_PIVOT64)) return CHOL_ERR_UNSUPPORTED;
+    if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER | CHOL_FLAG_LDL | CHOL_FLAG_PIVOT64_AUTO))
+        return CHOL_ERR_ARG;
+    if ((o.flags & CHOL_FLAG_LDL) && (o.flags & (CHOL_FLAG_PIVOT64 | CHOL_FLAG_PIVOT64_AUTO)))
+        return CHOL_ERR_UNSUPPORTED;
     if (max_n > kBatchedMaxN) return CHOL_ERR_UNSUPPORTED;
     if (o.prec == CHOL_PREC_TF32_REFINE || o.prec == CHOL_PREC_BF16_REFINE) return CHOL_ERR_UNSUPPORTED;
     if (o.prec == CHOL_PREC_FP32_REFINE && !is_fp32(dt)) return CHOL_ERR_UNSUPPORTED;
@@ -224,6 +232,7 @@ chol_status_t enqueue_batched(chol_dtype_t dt, BatchParams p, void* ws, cudaStre
     DevState* ds = nullptr;
     if (dev_state(&ds) != cudaSuccess) return CHOL_ERR_CUDA;
     p.err = ds->err;
+    p.redo_count = ds->redo;
     if (p.n != nullptr) {
         char* w = static_cast<char*>(ws);
         int32_t* counts = reinterpret_cast<int32_t*>(w);
@@ -248,15 +257,20 @@ chol_status_t enqueue_batched(chol_dtype_t dt, BatchParams p, void* ws, cudaStre
         }
     }
     if (launch_dtype(dt, p, s, dry, present) != cudaSuccess) return CHOL_ERR_CUDA;
+    // matrices whose FP32 pivots cancelled, again with FP64 pivots
+    if ((p.flags & CHOL_FLAG_PIVOT64_AUTO) && !(p.flags & CHOL_FLAG_PIVOT64) && is_fp32(dt) &&
+        launch_redo(dt, p, s, dry) != cudaSuccess)
+        return CHOL_ERR_CUDA;
     return CHOL_OK;
 }
 
 chol_status_t inv_validate(chol_dtype_t dt, int32_t batch, const int32_t* n, int32_t max_n, const void* A,
-                           void* X, const chol_opts_t& o, void* ws, size_t ws_bytes) {
+                           void* X, const int32_t* info, const chol_opts_t& o, void* ws, size_t ws_bytes) {
     chol_status_t st = check_common(dt, batch, max_n, o);
     if (st != CHOL_OK) return st;
     if (batch == 0) return CHOL_OK;
     if (A == nullptr || X == nullptr) return CHOL_ERR_ARG;
+    if ((o.flags & CHOL_FLAG_PIVOT64_AUTO) && info == nullptr) return CHOL_ERR_ARG;  // the redo list lives in info
     if (o.prec == CHOL_PREC_FP32_REFINE && o.refine_steps != 0 && X == A) return CHOL_ERR_ARG;
     return check_ws(batch, n, ws, ws_bytes);
 }
@@ -294,6 +308,8 @@ BatchParams make_params(int32_t batch, const int32_t* n, const int64_t* off, int
     p.info = info;
     p.flags = o.flags;
     p.order_mask[0] = p.order_mask[1] = ~0ull;
+    p.aligned16 = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(R) | reinterpret_cast<uintptr_t>(X)) %
+                   16) == 0;
     return p;
 }
 
@@ -306,7 +322,8 @@ chol_status_t blocked_validate(chol_dtype_t dt, int32_t batch, const int32_t* n,
     if (o.prec < CHOL_PREC_NATIVE || o.prec > CHOL_PREC_BF16_REFINE) return CHOL_ERR_ARG;
     if (o.refine_steps < -1 || o.refine_steps > 2) return CHOL_ERR_ARG;
     if (o.flags & CHOL_FLAG_LDL) return CHOL_ERR_UNSUPPORTED;
-    if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER | CHOL_FLAG_TF32_SINGLE)) return CHOL_ERR_ARG;
+    if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER | CHOL_FLAG_TF32_SINGLE | CHOL_FLAG_PIVOT64_AUTO))
+        return CHOL_ERR_ARG;
     if (n != nullptr || off != nullptr || o.layout != 0) return CHOL_ERR_UNSUPPORTED;
     if (dt != CHOL_F32 && dt != CHOL_F64) return CHOL_ERR_UNSUPPORTED;
     if (o.prec == CHOL_PREC_BF16_REFINE) return CHOL_ERR_UNSUPPORTED;
@@ -389,6 +406,10 @@ int blocked_refine_steps(const chol_opts_t& o) {
     return o.refine_steps < 0 ? 1 : o.refine_steps;
 }
 
+// The blocked path has one matrix per call: CHOL_FLAG_PIVOT64_AUTO there
+// means FP64 pivots for its diagonal blocks.
+int blocked_pivot64(const chol_opts_t& o) { return (o.flags & (CHOL_FLAG_PIVOT64 | CHOL_FLAG_PIVOT64_AUTO)) ? 1 : 0; }
+
 // Tensor-core mode of the blocked products (see blocked_run).
 int blocked_tc(const chol_opts_t& o) {
     if (o.prec != CHOL_PREC_TF32_REFINE) return 0;
@@ -432,13 +453,14 @@ chol_status_t chol_factor_batched(chol_dtype_t dt, int32_t batch, const int32_t*
         if (sb != CHOL_OK || batch == 0) return sb;
         if (A == nullptr || R == nullptr) return CHOL_ERR_ARG;
         // the factor is formed in R itself (R is the working storage)
-        return blocked_run(dt, batch, max_n, A, nullptr, R, info, o.flags & CHOL_FLAG_PIVOT64, 0, 0, blocked_tc(o),
+        return blocked_run(dt, batch, max_n, A, nullptr, R, info, blocked_pivot64(o), 0, 0, blocked_tc(o),
                            device_error_word(), ws, static_cast<cudaStream_t>(stream));
     }
     chol_status_t st = check_common(dt, batch, max_n, o);
     if (st != CHOL_OK) return st;
     if (batch == 0) return CHOL_OK;
     if (A == nullptr || R == nullptr) return CHOL_ERR_ARG;
+    if ((o.flags & CHOL_FLAG_PIVOT64_AUTO) && info == nullptr) return CHOL_ERR_ARG;
     st = check_ws(batch, n, ws, ws_bytes);
     if (st != CHOL_OK) return st;
     BatchParams p = make_params(batch, n, off, max_n, A, R, nullptr, info, o, 0);
@@ -456,10 +478,10 @@ chol_status_t chol_inv_batched(chol_dtype_t dt, int32_t batch, const int32_t* n,
         if (sb != CHOL_OK || batch == 0) return sb;
         if (A == nullptr || X == nullptr) return CHOL_ERR_ARG;
         if (X == A || (R != nullptr && (R == A || R == X))) return CHOL_ERR_ARG;
-        return blocked_run(dt, batch, max_n, A, R, X, info, o.flags & CHOL_FLAG_PIVOT64, rs, 1, blocked_tc(o),
+        return blocked_run(dt, batch, max_n, A, R, X, info, blocked_pivot64(o), rs, 1, blocked_tc(o),
                            device_error_word(), ws, static_cast<cudaStream_t>(stream));
     }
-    chol_status_t st = inv_validate(dt, batch, n, max_n, A, X, o, ws, ws_bytes);
+    chol_status_t st = inv_validate(dt, batch, n, max_n, A, X, info, o, ws, ws_bytes);
     if (st != CHOL_OK || batch == 0) return st;
     BatchParams p = make_params(batch, n, off, max_n, A, (R == X) ? nullptr : R, X, info, o, 1);
     return enqueue_inv(dt, p, ws, static_cast<cudaStream_t>(stream), false, o);
@@ -634,6 +656,36 @@ chol_status_t chol_last_device_error(void* stream) {
     return static_cast<chol_status_t>(v);
 }
 
+chol_status_t chol_blocked_timing(int32_t enable) {
+    if (enable != 0 && enable != 1) return CHOL_ERR_ARG;
+    blocked_timing_enable(enable);
+    return CHOL_OK;
+}
+
+chol_status_t chol_blocked_timing_read(int32_t kind, float* ms, double* flops, int32_t* launches) {
+    if (ms == nullptr || flops == nullptr || launches == nullptr) return CHOL_ERR_ARG;
+    int l = 0;
+    const cudaError_t e = blocked_timing_read(kind, ms, flops, &l);
+    *launches = l;
+    if (e == cudaErrorInvalidValue) return CHOL_ERR_ARG;
+    return e == cudaSuccess ? CHOL_OK : CHOL_ERR_CUDA;
+}
+
+chol_status_t chol_pivot64_redo_count(void* stream, int64_t* count) {
+    if (count == nullptr) return CHOL_ERR_ARG;
+    DevState* ds = nullptr;
+    if (dev_state(&ds) != cudaSuccess) return CHOL_ERR_CUDA;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return CHOL_ERR_CUDA;
+    unsigned long long v = 0;
+    if (cudaMemcpy(&v, ds->redo, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return CHOL_ERR_CUDA;
+    if (v != 0) {
+        const unsigned long long z = 0;
+        if (cudaMemcpy(ds->redo, &z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) return CHOL_ERR_CUDA;
+    }
+    *count = (int64_t)v;
+    return CHOL_OK;
+}
+
 // ---------------------------------------------------------------------------
 // chol_inv_batched_noalloc: the bucketing scratch of a batch with per-matrix
 // sizes lives in this fixed device array instead of a caller workspace.
@@ -675,7 +727,8 @@ chol_status_t chol_inv_batched_noalloc(chol_dtype_t dt, int32_t batch, const int
     chol_status_t st = check_common(dt, batch, max_n, o);
     if (st != CHOL_OK || batch == 0) return st;
     if (A == nullptr || X == nullptr) return CHOL_ERR_ARG;
-    if (o.prec == CHOL_PREC_FP32_REFINE && o.refine_steps != 0) return CHOL_ERR_UNSUPPORTED;
+    if (o.prec == CHOL_PREC_FP32_REFINE && o.refine_steps != 0 && X == A) return CHOL_ERR_ARG;
+    if ((o.flags & CHOL_FLAG_PIVOT64_AUTO) && info == nullptr) return CHOL_ERR_ARG;
     if (n != nullptr && batch > CHOL_NOALLOC_MAX_BATCH) return CHOL_ERR_WORKSPACE;
     void* scratch = nullptr;
     if (n != nullptr) {
@@ -683,7 +736,7 @@ chol_status_t chol_inv_batched_noalloc(chol_dtype_t dt, int32_t batch, const int
         if (st != CHOL_OK) return st;
     }
     BatchParams p = make_params(batch, n, off, max_n, A, (R == X) ? nullptr : R, X, info, o, 1);
-    return enqueue_batched(dt, p, scratch, static_cast<cudaStream_t>(stream), false);
+    return enqueue_inv(dt, p, scratch, static_cast<cudaStream_t>(stream), false, o);
 }
 
 int32_t chol_version(void) { return 100; }
@@ -697,7 +750,7 @@ chol_status_t chol_plan_inv_create(chol_plan_t** plan, chol_dtype_t dt, int32_t 
     const bool timed = (o.flags & CHOL_FLAG_PLAN_TIMING) != 0;
     const bool fixed_orders = (o.flags & CHOL_FLAG_PLAN_ORDERS) != 0;
     o.flags &= ~(CHOL_FLAG_PLAN_TIMING | CHOL_FLAG_PLAN_ORDERS);
-    chol_status_t st = inv_validate(dt, batch, n, max_n, A, X, o, ws, ws_bytes);
+    chol_status_t st = inv_validate(dt, batch, n, max_n, A, X, info, o, ws, ws_bytes);
     if (st != CHOL_OK) return st;
     BatchParams p = make_params(batch, n, off, max_n, A, (R == X) ? nullptr : R, X, info, o, 1);
     // CHOL_FLAG_PLAN_ORDERS: the orders present now (n read once, on the host)

@@ -35,7 +35,18 @@ struct BatchParams {
     int* err;                  // device error word
     int32_t flags;             // CHOL_FLAG_*
     uint64_t order_mask[2];    // bit c: order c may occur (bucketing rejects the others)
+    unsigned long long* redo_count;  // matrices redone with FP64 pivots (CHOL_FLAG_PIVOT64_AUTO)
+    int32_t aligned16;         // A, R and X all start on 16-byte boundaries (16-byte copies allowed)
 };
+
+// CHOL_FLAG_PIVOT64_AUTO: a matrix whose FP32 pass saw cancellation in Eq. 3
+// (t_i < 2^-10 a_ii at some row, or a non-positive or non-finite t_i) is
+// marked with this info value, nothing of it is stored, and a second pass
+// (k_redo) factors and inverts it again with the sum of Eq. 3 accumulated in
+// FP64.  t_i >= lambda_min(A) and a_ii <= lambda_max(A), so a matrix with
+// kappa_2(A) < 2^10 is never marked.
+constexpr int kInfoRedo = -2;
+template <typename R> CHOL_D bool pivot_cancels(R t, R aii) { return !(t >= aii * R(0.0009765625)); }
 
 // Arguments of the adjoint kernel.
 struct BwdParams {
@@ -81,9 +92,11 @@ CHOL_D int class_count(const BatchParams& p, int N) {
 // bounds that depend on an outer index the front end leaves a register array
 // in local memory.)
 template <typename V, int N, class Acc>
-CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 1], bool pivot64 = false) {
+CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 1], bool pivot64 = false,
+                           bool gate = false) {
     using R = typename traits<V>::real;
     int info = 0;
+    bool redo = false;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         V col[N > 0 ? N : 1];  // column i of R above the diagonal: r_ki, k < i
@@ -103,9 +116,11 @@ CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 
             inv = (R)(1.0 / sqrt(td));
             if (info == 0 && !pivot_ok(td)) info = i + 1;
         } else {
+            const R aii = t;
 #pragma unroll
             for (int k = 0; k < N; ++k)
                 if (k < i) t = fnma_abs2(col[k], t);
+            if (gate && pivot_cancels(t, aii)) redo = true;
             if (info == 0 && !pivot_ok(t)) info = i + 1;
             pivot_root(t, rii, inv);
         }
@@ -123,7 +138,7 @@ CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 
             }
         }
     }
-    return info;
+    return redo ? kInfoRedo : info;
 }
 
 // Proposed inverse (Eqs. 20-24) in place over R: row i of R is read into
@@ -268,7 +283,8 @@ CHOL_D void lane_stage(const BatchParams& p, const V* A, uint4* buf, const int64
 }
 
 // Write the chunk's results (X, or R when factoring) from a unit buffer.
-template <typename V, int N>
+// GATE: matrices marked kInfoRedo are skipped (CHOL_FLAG_PIVOT64_AUTO).
+template <typename V, int N, bool GATE = false>
 CHOL_D void lane_store(const BatchParams& p, V* out, uint4* buf, const int64_t* s_off, const int* s_info,
                        const uint8_t* s_i, const uint8_t* s_j, int m, bool vec, bool is_factor, bool fill_lower) {
     using C = LaneCfg<V, N>;
@@ -276,6 +292,8 @@ CHOL_D void lane_store(const BatchParams& p, V* out, uint4* buf, const int64_t* 
     if (vec) {
         for (int f = t; f < m * C::NU; f += C::THREADS) {
             const int q = f / C::NU, u = f - q * C::NU;
+            if constexpr (GATE)
+                if (s_info[q] == kInfoRedo) continue;  // left to the FP64-pivot pass
             V* dst = out + s_off[q] + u * C::U;
             uint4 v = buf[u * C::LD + q];
             if (s_info[q] != 0) {
@@ -294,6 +312,8 @@ CHOL_D void lane_store(const BatchParams& p, V* out, uint4* buf, const int64_t* 
     } else {
         for (int f = t; f < m * C::TN; f += C::THREADS) {
             const int q = f / C::TN, e = f - q * C::TN;
+            if constexpr (GATE)
+                if (s_info[q] == kInfoRedo) continue;
             const int64_t o = s_off[q];
             const int i = s_i[e], j = s_j[e];
             const bool bad = s_info[q] != 0;
@@ -314,7 +334,8 @@ CHOL_D void lane_store(const BatchParams& p, V* out, uint4* buf, const int64_t* 
 // ---------------------------------------------------------------------------
 // Lane kernel: one matrix per thread.
 // ---------------------------------------------------------------------------
-template <typename V, int N>
+// GATE: CHOL_FLAG_PIVOT64_AUTO's cancellation test (FP32 value types only).
+template <typename V, int N, bool GATE = false>
 __global__ void __launch_bounds__(LaneCfg<V, N>::THREADS)
 k_lane(BatchParams p) {
     using C = LaneCfg<V, N>;
@@ -342,6 +363,7 @@ k_lane(BatchParams p) {
     V* Xo = static_cast<V*>(p.X);
     V* Ro = static_cast<V*>(p.R);
     const bool store_R = p.R != nullptr && p.want_inv;
+    constexpr bool gate = GATE;
 
     // Offsets of a chunk's matrices into s_off; returns (CTA-uniformly)
     // whether whole 16-byte units can be copied.
@@ -353,7 +375,7 @@ k_lane(BatchParams p) {
             s_off[t] = o;
             ok = (o % C::U) == 0;
         }
-        return __syncthreads_and(ok) != 0 && p.layout == 1;
+        return __syncthreads_and(ok) != 0 && p.layout == 1 && p.aligned16;
     };
 
     if constexpr (C::REGS) {
@@ -386,8 +408,8 @@ k_lane(BatchParams p) {
             int info = 0;
             R dinv[N];
             if (t < m) {
-                info = factor_unrolled<V, N>(r, dinv, p.flags & CHOL_FLAG_PIVOT64);
-                if (store_R) {
+                info = factor_unrolled<V, N>(r, dinv, p.flags & CHOL_FLAG_PIVOT64, gate);
+                if (store_R && (!GATE || info != kInfoRedo)) {
 #pragma unroll
                     for (int e = 0; e < TN; ++e) {
                         const int64_t g = p.layout ? (int64_t)e : (int64_t)s_i[e] * N + s_j[e];
@@ -406,7 +428,7 @@ k_lane(BatchParams p) {
                 s_info[t] = info;
             }
             __syncthreads();
-            lane_store<V, N>(p, p.want_inv ? Xo : Ro, buf, s_off, s_info, s_i, s_j, m, vec, !p.want_inv,
+            lane_store<V, N, GATE>(p, p.want_inv ? Xo : Ro, buf, s_off, s_info, s_i, s_j, m, vec, !p.want_inv,
                              p.fill_lower != 0);
             if (p.info)
                 for (int q = t; q < m; q += THREADS) p.info[member_index(p, N, chunk * THREADS + q)] = s_info[q];
@@ -428,16 +450,16 @@ k_lane(BatchParams p) {
             int info = 0;
             R dinv[N];
             SmemMat<V, N> sm{buf, t};
-            if (t < m) info = factor_unrolled<V, N>(sm, dinv, p.flags & CHOL_FLAG_PIVOT64);
+            if (t < m) info = factor_unrolled<V, N>(sm, dinv, p.flags & CHOL_FLAG_PIVOT64, gate);
             if (t < m) s_info[t] = info;
             if (store_R) {
                 __syncthreads();
-                lane_store<V, N>(p, Ro, buf, s_off, s_info, s_i, s_j, m, vec, true, false);
+                lane_store<V, N, GATE>(p, Ro, buf, s_off, s_info, s_i, s_j, m, vec, true, false);
                 __syncthreads();
             }
             if (p.want_inv && t < m) inverse_unrolled<V, N>(sm, dinv);
             __syncthreads();
-            lane_store<V, N>(p, p.want_inv ? Xo : Ro, buf, s_off, s_info, s_i, s_j, m, vec, !p.want_inv,
+            lane_store<V, N, GATE>(p, p.want_inv ? Xo : Ro, buf, s_off, s_info, s_i, s_j, m, vec, !p.want_inv,
                              p.fill_lower != 0);
             if (p.info)
                 for (int q = t; q < m; q += THREADS) p.info[member_index(p, N, chunk * THREADS + q)] = s_info[q];
@@ -451,142 +473,173 @@ k_lane(BatchParams p) {
 // columns j = lane and j = lane + 32.  The matrix is a padded dense square
 // in shared memory (row stride N+1).
 // ---------------------------------------------------------------------------
+// One matrix (index b, element offset o, order N) on one warp; S holds
+// N x (N+1) elements.  pivot64: Eq. 3 accumulated in FP64 (FP32 value
+// types); gate: mark the matrix for the FP64-pivot pass on cancellation.
+template <typename V>
+CHOL_D void warp_one(const BatchParams& p, int N, int64_t b, int64_t o, V* S, int lane, bool pivot64, bool gate) {
+    using R = typename traits<V>::real;
+    const int LD = N + 1;
+    const V* A = static_cast<const V*>(p.A);
+    V* Xo = static_cast<V*>(p.X);
+    V* Ro = static_cast<V*>(p.R);
+    const int TN = tri(N);
+    // load the upper triangle
+    if (p.layout) {
+        for (int e = lane; e < TN; e += 32) {
+            int i = 0;
+            while (pidx(N, i + 1, i + 1) <= e && i + 1 < N) ++i;
+            const int j = e - pidx(N, i, i) + i;
+            S[i * LD + j] = A[o + e];
+        }
+    } else {
+        for (int i = 0; i < N; ++i)
+            for (int j = i + lane; j < N; j += 32) S[i * LD + j] = A[o + (int64_t)i * N + j];
+    }
+    __syncwarp();
+    // ---- factor, Eqs. 3-4, row by row; with CHOL_FLAG_LDL the LDL form of
+    // Sec. II.A (Eqs. 9-11): d_i = a_ii - sum |r_ki|^2 d_k and
+    // r_ij = (a_ij - sum conj(r_ki) d_k r_kj) / d_i, R unit upper, d_i kept
+    // on R's diagonal
+    const bool ldl = (p.flags & CHOL_FLAG_LDL) != 0;
+    int info = 0;
+    bool redo = false;
+    for (int i = 0; i < N; ++i) {
+        const R aii = re_of(S[i * LD + i]);  // read before this row is written
+        V s0 = zero_v<V>(), s1 = zero_v<V>();
+        const int j0 = lane, j1 = lane + 32;
+        if (j0 >= i && j0 < N) {
+            s0 = S[i * LD + j0];
+            for (int k = 0; k < i; ++k) {
+                const V rki = ldl ? scale_v(S[k * LD + i], re_of(S[k * LD + k])) : S[k * LD + i];
+                s0 = fnma_conj(rki, S[k * LD + j0], s0);
+            }
+        }
+        if (j1 >= i && j1 < N) {
+            s1 = S[i * LD + j1];
+            for (int k = 0; k < i; ++k) {
+                const V rki = ldl ? scale_v(S[k * LD + i], re_of(S[k * LD + k])) : S[k * LD + i];
+                s1 = fnma_conj(rki, S[k * LD + j1], s1);
+            }
+        }
+        // pivot: column i lives in lane i & 31, slot i >> 5
+        R tsrc = re_of((i < 32) ? s0 : s1);
+        R tt = __shfl_sync(0xffffffffu, tsrc, i & 31);
+        R rii, inv;
+        if (ldl) {
+            if (info == 0 && !pivot_ok(tt)) info = i + 1;
+            rii = tt;  // d_i, stored on the diagonal
+            inv = R(1) / tt;
+        } else if (sizeof(R) == 4 && pivot64) {
+            double td = (double)aii;
+            for (int k = 0; k < i; ++k) td -= pivot64_term(S[k * LD + i]);
+            if (info == 0 && !pivot_ok(td)) info = i + 1;
+            rii = (R)sqrt(td);
+            inv = (R)(1.0 / sqrt(td));
+        } else {
+            if (gate && pivot_cancels(tt, aii)) redo = true;
+            if (info == 0 && !pivot_ok(tt)) info = i + 1;
+            pivot_root(tt, rii, inv);
+        }
+        if (j0 > i && j0 < N) S[i * LD + j0] = scale_v(s0, inv);
+        if (j1 > i && j1 < N) S[i * LD + j1] = scale_v(s1, inv);
+        if (lane == (i & 31)) S[i * LD + i] = from_real<V>(rii);
+        __syncwarp();
+    }
+    if (redo) info = kInfoRedo;  // nothing stored: the FP64-pivot pass redoes this matrix
+    if (p.R && !redo) {
+        // store R (dense: zero strictly lower part)
+        for (int i = 0; i < N; ++i)
+            for (int j = lane; j < N; j += 32) {
+                if (j >= i) {
+                    const int64_t g = p.layout ? (int64_t)pidx(N, i, j) : (int64_t)i * N + j;
+                    Ro[o + g] = info ? nan_v<V>() : S[i * LD + j];
+                } else if (!p.layout) {
+                    Ro[o + (int64_t)i * N + j] = info ? nan_v<V>() : zero_v<V>();
+                }
+            }
+    }
+    if (p.want_inv && !redo) {
+        // ---- proposed inverse, rows N..1
+        for (int i = N - 1; i >= 0; --i) {
+            const int j0 = lane, j1 = lane + 32;
+            V a0 = zero_v<V>(), a1 = zero_v<V>();
+            V r0 = zero_v<V>(), r1 = zero_v<V>();
+            if (j0 > i && j0 < N) {
+                r0 = S[i * LD + j0];
+                for (int k = i + 1; k < N; ++k) {
+                    V xt = (k <= j0) ? S[k * LD + j0] : conj_v(S[j0 * LD + k]);
+                    a0 = fma_v(S[i * LD + k], xt, a0);
+                }
+            }
+            if (j1 > i && j1 < N) {
+                r1 = S[i * LD + j1];
+                for (int k = i + 1; k < N; ++k) {
+                    V xt = (k <= j1) ? S[k * LD + j1] : conj_v(S[j1 * LD + k]);
+                    a1 = fma_v(S[i * LD + k], xt, a1);
+                }
+            }
+            // 1/r_ii, or 1/d_i in the LDL form (Sec. IV.B, Eqs. 25-29: R unit
+            // upper, s~_ii = 1/d_i, so x_ij = -sum r_ik x~_kj and
+            // x_ii = 1/d_i - sum r_ik conj(x_ik))
+            const R inv = R(1) / re_of(S[i * LD + i]);
+            const R xs = ldl ? R(-1) : -inv;
+            __syncwarp();
+            R sd = R(0);
+            if (j0 > i && j0 < N) { V x = scale_v(a0, xs); S[i * LD + j0] = x; sd = fma_re_conjb(r0, x, sd); }
+            if (j1 > i && j1 < N) { V x = scale_v(a1, xs); S[i * LD + j1] = x; sd = fma_re_conjb(r1, x, sd); }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, d);
+            __syncwarp();
+            if (lane == 0) S[i * LD + i] = from_real<V>(ldl ? inv - sd : (inv - sd) * inv);
+            __syncwarp();
+        }
+        // store X
+        for (int i = 0; i < N; ++i)
+            for (int j = i + lane; j < N; j += 32) {
+                V v = info ? nan_v<V>() : S[i * LD + j];
+                if (p.layout) {
+                    Xo[o + pidx(N, i, j)] = v;
+                } else {
+                    Xo[o + (int64_t)i * N + j] = v;
+                    if (p.fill_lower && j > i) Xo[o + (int64_t)j * N + i] = conj_v(v);
+                }
+            }
+    }
+    if (p.info && lane == 0) p.info[b] = info;
+    __syncwarp();
+}
+
 template <typename V>
 __global__ void k_warp(BatchParams p, int N, int warps_per_cta) {
     using R = typename traits<V>::real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int LD = N + 1;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    V* S = reinterpret_cast<V*>(smem_raw) + (size_t)w * N * LD;
-    const V* A = static_cast<const V*>(p.A);
-    V* Xo = static_cast<V*>(p.X);
-    V* Ro = static_cast<V*>(p.R);
+    V* S = reinterpret_cast<V*>(smem_raw) + (size_t)w * N * (N + 1);
     const int count = class_count(p, N);
-    const int TN = tri(N);
-
+    const bool pivot64 = (p.flags & CHOL_FLAG_PIVOT64) != 0;
+    const bool gate = sizeof(R) == 4 && (p.flags & CHOL_FLAG_PIVOT64_AUTO) && !pivot64;
     for (int k0 = blockIdx.x * warps_per_cta + w; k0 < count; k0 += gridDim.x * warps_per_cta) {
         const int64_t b = member_index(p, N, k0);
-        const int64_t o = matrix_offset(p, N, b);
-        // load the upper triangle
-        if (p.layout) {
-            for (int e = lane; e < TN; e += 32) {
-                int i = 0;
-                while (pidx(N, i + 1, i + 1) <= e && i + 1 < N) ++i;
-                const int j = e - pidx(N, i, i) + i;
-                S[i * LD + j] = A[o + e];
-            }
-        } else {
-            for (int i = 0; i < N; ++i)
-                for (int j = i + lane; j < N; j += 32) S[i * LD + j] = A[o + (int64_t)i * N + j];
-        }
-        __syncwarp();
-        // ---- factor, Eqs. 3-4, row by row; with CHOL_FLAG_LDL the LDL form of
-        // Sec. II.A (Eqs. 9-11): d_i = a_ii - sum |r_ki|^2 d_k and
-        // r_ij = (a_ij - sum conj(r_ki) d_k r_kj) / d_i, R unit upper, d_i kept
-        // on R's diagonal
-        const bool ldl = (p.flags & CHOL_FLAG_LDL) != 0;
-        int info = 0;
-        for (int i = 0; i < N; ++i) {
-            V s0 = zero_v<V>(), s1 = zero_v<V>();
-            const int j0 = lane, j1 = lane + 32;
-            if (j0 >= i && j0 < N) {
-                s0 = S[i * LD + j0];
-                for (int k = 0; k < i; ++k) {
-                    const V rki = ldl ? scale_v(S[k * LD + i], re_of(S[k * LD + k])) : S[k * LD + i];
-                    s0 = fnma_conj(rki, S[k * LD + j0], s0);
-                }
-            }
-            if (j1 >= i && j1 < N) {
-                s1 = S[i * LD + j1];
-                for (int k = 0; k < i; ++k) {
-                    const V rki = ldl ? scale_v(S[k * LD + i], re_of(S[k * LD + k])) : S[k * LD + i];
-                    s1 = fnma_conj(rki, S[k * LD + j1], s1);
-                }
-            }
-            // pivot: column i lives in lane i & 31, slot i >> 5
-            R tsrc = re_of((i < 32) ? s0 : s1);
-            R tt = __shfl_sync(0xffffffffu, tsrc, i & 31);
-            R rii, inv;
-            if (ldl) {
-                if (info == 0 && !pivot_ok(tt)) info = i + 1;
-                rii = tt;  // d_i, stored on the diagonal
-                inv = R(1) / tt;
-            } else if (sizeof(R) == 4 && (p.flags & CHOL_FLAG_PIVOT64)) {
-                double td = (double)re_of(S[i * LD + i]);
-                for (int k = 0; k < i; ++k) td -= pivot64_term(S[k * LD + i]);
-                if (info == 0 && !pivot_ok(td)) info = i + 1;
-                rii = (R)sqrt(td);
-                inv = (R)(1.0 / sqrt(td));
-            } else {
-                if (info == 0 && !pivot_ok(tt)) info = i + 1;
-                pivot_root(tt, rii, inv);
-            }
-            if (j0 > i && j0 < N) S[i * LD + j0] = scale_v(s0, inv);
-            if (j1 > i && j1 < N) S[i * LD + j1] = scale_v(s1, inv);
-            if (lane == (i & 31)) S[i * LD + i] = from_real<V>(rii);
-            __syncwarp();
-        }
-        if (p.R) {
-            // store R (dense: zero strictly lower part)
-            for (int i = 0; i < N; ++i)
-                for (int j = lane; j < N; j += 32) {
-                    if (j >= i) {
-                        const int64_t g = p.layout ? (int64_t)pidx(N, i, j) : (int64_t)i * N + j;
-                        Ro[o + g] = info ? nan_v<V>() : S[i * LD + j];
-                    } else if (!p.layout) {
-                        Ro[o + (int64_t)i * N + j] = info ? nan_v<V>() : zero_v<V>();
-                    }
-                }
-        }
-        if (p.want_inv) {
-            // ---- proposed inverse, rows N..1
-            for (int i = N - 1; i >= 0; --i) {
-                const int j0 = lane, j1 = lane + 32;
-                V a0 = zero_v<V>(), a1 = zero_v<V>();
-                V r0 = zero_v<V>(), r1 = zero_v<V>();
-                if (j0 > i && j0 < N) {
-                    r0 = S[i * LD + j0];
-                    for (int k = i + 1; k < N; ++k) {
-                        V xt = (k <= j0) ? S[k * LD + j0] : conj_v(S[j0 * LD + k]);
-                        a0 = fma_v(S[i * LD + k], xt, a0);
-                    }
-                }
-                if (j1 > i && j1 < N) {
-                    r1 = S[i * LD + j1];
-                    for (int k = i + 1; k < N; ++k) {
-                        V xt = (k <= j1) ? S[k * LD + j1] : conj_v(S[j1 * LD + k]);
-                        a1 = fma_v(S[i * LD + k], xt, a1);
-                    }
-                }
-                // 1/r_ii, or 1/d_i in the LDL form (Sec. IV.B, Eqs. 25-29: R unit
-                // upper, s~_ii = 1/d_i, so x_ij = -sum r_ik x~_kj and
-                // x_ii = 1/d_i - sum r_ik conj(x_ik))
-                const R inv = R(1) / re_of(S[i * LD + i]);
-                const R xs = ldl ? R(-1) : -inv;
-                __syncwarp();
-                R sd = R(0);
-                if (j0 > i && j0 < N) { V x = scale_v(a0, xs); S[i * LD + j0] = x; sd = fma_re_conjb(r0, x, sd); }
-                if (j1 > i && j1 < N) { V x = scale_v(a1, xs); S[i * LD + j1] = x; sd = fma_re_conjb(r1, x, sd); }
-#pragma unroll
-                for (int d = 16; d > 0; d >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, d);
-                __syncwarp();
-                if (lane == 0) S[i * LD + i] = from_real<V>(ldl ? inv - sd : (inv - sd) * inv);
-                __syncwarp();
-            }
-            // store X
-            for (int i = 0; i < N; ++i)
-                for (int j = i + lane; j < N; j += 32) {
-                    V v = info ? nan_v<V>() : S[i * LD + j];
-                    if (p.layout) {
-                        Xo[o + pidx(N, i, j)] = v;
-                    } else {
-                        Xo[o + (int64_t)i * N + j] = v;
-                        if (p.fill_lower && j > i) Xo[o + (int64_t)j * N + i] = conj_v(v);
-                    }
-                }
-        }
-        if (p.info && lane == 0) p.info[b] = info;
-        __syncwarp();
+        warp_one<V>(p, N, b, matrix_offset(p, N, b), S, lane, pivot64, gate);
+    }
+}
+
+// The FP64-pivot pass of CHOL_FLAG_PIVOT64_AUTO: every matrix of the batch
+// whose info holds kInfoRedo is factored and inverted again, one per warp,
+// with Eq. 3 accumulated in FP64; its outputs and info are written then.
+// `smax` is the largest order of the call (shared memory per warp).
+template <typename V>
+__global__ void k_redo(BatchParams p, int smax, int warps_per_cta) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    V* S = reinterpret_cast<V*>(smem_raw) + (size_t)w * smax * (smax + 1);
+    for (int64_t b = (int64_t)blockIdx.x * warps_per_cta + w; b < p.batch; b += (int64_t)gridDim.x * warps_per_cta) {
+        if (p.info[b] != kInfoRedo) continue;  // warp-uniform
+        const int N = p.n ? p.n[b] : p.max_n;
+        if (N < 1 || N > smax) continue;       // orders outside [1, max_n] were rejected by the bucketing
+        warp_one<V>(p, N, b, matrix_offset(p, N, b), S, lane, true, false);
+        if (lane == 0 && p.redo_count) atomicAdd(p.redo_count, 1ull);
     }
 }
 

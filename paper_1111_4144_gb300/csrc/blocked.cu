@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "batched.cuh"
 #include "blocked.h"
@@ -817,6 +818,84 @@ SideStream* side_stream() {
 }
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Kernel timing of the blocked path (chol_blocked_timing*): while enabled on
+// a host thread, the calls it makes record an event pair around each product
+// of the kinds below on the stream that runs it, with the product's
+// algorithmic flops (2 M N K; the upper half only where only it is formed).
+// ---------------------------------------------------------------------------
+struct BlkTiming {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[kBlkTimingKinds];
+    double flops[kBlkTimingKinds] = {};
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    cudaEvent_t take() {
+        if (used == pool.size()) {
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+};
+thread_local BlkTiming* t_blk = nullptr;
+
+// f() bracketed by an event pair of `kind` when timing is on.
+template <class F>
+cudaError_t timed(int kind, double flops, cudaStream_t s, F&& f) {
+    BlkTiming* t = t_blk;
+    cudaEvent_t e0 = t ? t->take() : nullptr, e1 = t ? t->take() : nullptr;
+    if (t && e0 && e1 && cudaEventRecord(e0, s) != cudaSuccess) return cudaGetLastError();
+    cudaError_t e = f();
+    if (e != cudaSuccess) return e;
+    if (t && e0 && e1) {
+        if ((e = cudaEventRecord(e1, s)) != cudaSuccess) return e;
+        t->ev[kind].push_back({e0, e1});
+        t->flops[kind] += flops;
+    }
+    return cudaSuccess;
+}
+
+// Algorithmic flops of an M x N product with inner dimension K whose region
+// starts on the diagonal and keeps only its upper part (upper != 0).
+double gemm_flops(int M, int N, int K, int upper) {
+    if (!upper) return 2.0 * M * N * K;
+    const double rows = std::min(M, N);
+    return 2.0 * K * (rows * N - rows * (rows - 1) / 2);
+}
+
+void blocked_timing_enable(int on) {
+    if (on) {
+        if (!t_blk) t_blk = new BlkTiming();
+        for (int k = 0; k < kBlkTimingKinds; ++k) {
+            t_blk->ev[k].clear();
+            t_blk->flops[k] = 0;
+        }
+        t_blk->used = 0;
+    } else if (t_blk) {
+        for (cudaEvent_t e : t_blk->pool) cudaEventDestroy(e);
+        delete t_blk;
+        t_blk = nullptr;
+    }
+}
+
+cudaError_t blocked_timing_read(int kind, float* ms, double* flops, int* launches) {
+    *ms = 0.f;
+    *flops = 0.0;
+    *launches = 0;
+    if (!t_blk || kind < 0 || kind >= kBlkTimingKinds) return cudaErrorInvalidValue;
+    for (auto& pr : t_blk->ev[kind]) {
+        cudaError_t e = cudaEventSynchronize(pr.second);
+        if (e != cudaSuccess) return e;
+        float m = 0.f;
+        if ((e = cudaEventElapsedTime(&m, pr.first, pr.second)) != cudaSuccess) return e;
+        *ms += m;
+    }
+    *flops = t_blk->flops[kind];
+    *launches = (int)t_blk->ev[kind].size();
+    return cudaSuccess;
+}
+
 size_t blocked_workspace_bytes(int dtype, int n, int refine) {
     if (n <= 0) return 0;
     const size_t es = (dtype == CHOL_F64) ? 8 : 4;
@@ -933,11 +1012,15 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
         T* pb = pbuf[kb & 1];
         if constexpr (sizeof(T) == 4) {
             if (use_tc)
-                return umma_gemm(r1 - r0, m - r0, bk, -1.f, mapPt[kb & 1], 0, r0, mapPt[kb & 1], 0, r0, 1.f, Ct, n, 1,
-                                 nullptr, 0, split3, umma_err, s);
+                return timed(kBlkTrailingUpdate, gemm_flops(r1 - r0, m - r0, bk, 1), s, [&] {
+                    return umma_gemm(r1 - r0, m - r0, bk, -1.f, mapPt[kb & 1], 0, r0, mapPt[kb & 1], 0, r0, 1.f, Ct,
+                                     n, 1, nullptr, 0, split3, umma_err, s);
+                });
         }
-        return gemm<T, Tacc, T, true, false>(r1 - r0, m - r0, bk, Tacc(-1), pb + r0, m, pb + r0, m, Tacc(1), Ct, n, 1,
-                                             part, part_elems, s);
+        return timed(kBlkTrailingUpdate, gemm_flops(r1 - r0, m - r0, bk, 1), s, [&] {
+            return gemm<T, Tacc, T, true, false>(r1 - r0, m - r0, bk, Tacc(-1), pb + r0, m, pb + r0, m, Tacc(1), Ct, n,
+                                                 1, part, part_elems, s);
+        });
     };
     SideStream* side = side_stream();
     if (!side) return CHOL_ERR_CUDA;
@@ -970,12 +1053,16 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
             // P = R_I,>I X_>I,>I  (X is symmetric, so X_>I,>I read by rows is K-major)
             cudaError_t e;
             if (use_tc && bi == b) {
-                e = umma_gemm(bi, m, m, 1.f, mapX, i0 + bi, i0, mapX, i0 + bi, i0 + bi, 0.f,
-                              reinterpret_cast<float*>(P), m, 0, reinterpret_cast<float*>(part), part_elems, split3,
-                              umma_err, s);
+                e = timed(kBlkInverseProduct, gemm_flops(bi, m, m, 0), s, [&] {
+                    return umma_gemm(bi, m, m, 1.f, mapX, i0 + bi, i0, mapX, i0 + bi, i0 + bi, 0.f,
+                                     reinterpret_cast<float*>(P), m, 0, reinterpret_cast<float*>(part), part_elems,
+                                     split3, umma_err, s);
+                });
             } else {
-                e = gemm<T, Tacc, T, false, false>(bi, m, m, Tacc(1), RIr, n, Xrr, n, Tacc(0), P, m, 0, part,
-                                                   part_elems, s);
+                e = timed(kBlkInverseProduct, gemm_flops(bi, m, m, 0), s, [&] {
+                    return gemm<T, Tacc, T, false, false>(bi, m, m, Tacc(1), RIr, n, Xrr, n, Tacc(0), P, m, 0, part,
+                                                          part_elems, s);
+                });
             }
             if (e != cudaSuccess) return CHOL_ERR_CUDA;
             // P2 = -R_II^{-1} P   (X_I,>I)
@@ -1005,14 +1092,19 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
         k_sym_full<float><<<g1, 256, 0, s>>>(Af, A32, n);
         for (int st = 0; st < refine_steps; ++st) {
             k_identity<double><<<g1, 256, 0, s>>>(E, n);
-            cudaError_t e = gemm<float, double, double, false, false>(n, n, n, -1.0, Af, n, X32, n, 1.0, E, n, 0,
-                                                                     nullptr, 0, s);
+            cudaError_t e = timed(kBlkResidual, gemm_flops(n, n, n, 0), s, [&] {
+                return gemm<float, double, double, false, false>(n, n, n, -1.0, Af, n, X32, n, 1.0, E, n, 0, nullptr,
+                                                                 0, s);
+            });
             if (e != cudaSuccess) return CHOL_ERR_CUDA;
             k_narrow<<<g1, 256, 0, s>>>(E32, E, (int64_t)n * n);
             // the correction X E goes to a separate buffer (the FP64 one, now free): the
             // product reads X while it runs
             float* Cx = reinterpret_cast<float*>(E);
-            e = gemm<float, float, float, false, false>(n, n, n, 1.0f, X32, n, E32, n, 0.0f, Cx, n, 0, nullptr, 0, s);
+            e = timed(kBlkCorrection, gemm_flops(n, n, n, 0), s, [&] {
+                return gemm<float, float, float, false, false>(n, n, n, 1.0f, X32, n, E32, n, 0.0f, Cx, n, 0, nullptr,
+                                                               0, s);
+            });
             if (e != cudaSuccess) return CHOL_ERR_CUDA;
             k_axpy<<<g1, 256, 0, s>>>(X32, Cx, (int64_t)n * n);
         }
@@ -1026,7 +1118,10 @@ chol_status_t blocked_run(int dtype, int32_t batch, int32_t n, const void* A, vo
                           cudaStream_t s) {
     for (int32_t bi = 0; bi < batch; ++bi) {
         const int64_t o = (int64_t)bi * n * n;
-        chol_status_t st;
+        chol_status_t st = CHOL_OK;
+        BlkTiming* tm = t_blk;
+        cudaEvent_t w0 = tm ? tm->take() : nullptr, w1 = tm ? tm->take() : nullptr;
+        if (w0 && w1 && cudaEventRecord(w0, s) != cudaSuccess) return CHOL_ERR_CUDA;
         if (dtype == CHOL_F32)
             st = blocked_one<float>(static_cast<const float*>(A) + o, R ? static_cast<float*>(R) + o : nullptr,
                                     static_cast<float*>(X) + o, n, info ? info + bi : nullptr, pivot64,
@@ -1038,6 +1133,11 @@ chol_status_t blocked_run(int dtype, int32_t batch, int32_t n, const void* A, vo
         else
             return CHOL_ERR_UNSUPPORTED;
         if (st != CHOL_OK) return st;
+        if (w0 && w1) {
+            if (cudaEventRecord(w1, s) != cudaSuccess) return CHOL_ERR_CUDA;
+            tm->ev[kBlkWholeCall].push_back({w0, w1});
+            tm->flops[kBlkWholeCall] += (double)n * n * n;  // the factor's n^3/3 and the inverse's 2 n^3/3
+        }
     }
     return CHOL_OK;
 }

@@ -22,4 +22,14 @@ chol_status_t blocked_run(int dtype, int32_t batch, int32_t n, const void* A, vo
                           int pivot64, int refine_steps, int want_inv, int tc, int* err_word, void* ws,
                           cudaStream_t s);
 
+// Kernel timing (chol_blocked_timing): kinds of recorded products.
+constexpr int kBlkTrailingUpdate = 0;  // A_>K,>K -= R_K,>K^T R_K,>K (tensor cores)
+constexpr int kBlkInverseProduct = 1;  // P = R_I,>I X_>I,>I (tensor cores)
+constexpr int kBlkResidual = 2;        // refinement: E = I - A X (FP64 accumulation)
+constexpr int kBlkCorrection = 3;      // refinement: X E
+constexpr int kBlkWholeCall = 4;       // one matrix's whole factor + inverse (+ refinement)
+constexpr int kBlkTimingKinds = 5;
+void blocked_timing_enable(int on);
+cudaError_t blocked_timing_read(int kind, float* ms, double* flops, int* launches);
+
 }  // namespace cholinv

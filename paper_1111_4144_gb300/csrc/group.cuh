@@ -42,9 +42,9 @@ struct GroupCfg {
     static constexpr int stride_units() {
         constexpr int gb = (G * (int)sizeof(V)) % 128;
         int u = UNITS0;
-        if (gb == 0 || gb % 16 != 0) return u % 2 ? u : u + 1;
-        while ((u * 16) % 128 != gb && (u * 16) % 128 != 128 - gb) ++u;
-        return u;
+        const bool odd = gb == 0 || gb % 16 != 0;
+        while (!odd && (u * 16) % 128 != gb && (u * 16) % 128 != 128 - gb) ++u;
+        return odd ? (u % 2 ? u : u + 1) : u;
     }
     static constexpr int UNITS = stride_units();
     static constexpr int STRIDE = UNITS * 16;
@@ -90,8 +90,9 @@ CHOL_D void group_stage(const BatchParams& p, const V* A, unsigned char* mir, co
     cp_async_commit();
 }
 
-// Store the mirrors (X, or R when factoring) to global memory.
-template <typename V, int N, class C>
+// Store the mirrors (X, or R when factoring) to global memory.  GATE:
+// matrices marked kInfoRedo are skipped (CHOL_FLAG_PIVOT64_AUTO).
+template <typename V, int N, class C, bool GATE = false>
 CHOL_D void group_store(const BatchParams& p, V* out, const unsigned char* mir, const int64_t* s_off,
                         const int* s_info, const uint8_t* s_i, const uint8_t* s_j, int m, bool vec, bool is_factor,
                         bool fill_lower) {
@@ -101,6 +102,8 @@ CHOL_D void group_store(const BatchParams& p, V* out, const unsigned char* mir, 
         constexpr int TAIL = C::TN - FULL * C::U;
         for (int f = t; f < m * FULL; f += C::THREADS) {
             const int q = f / FULL, u = f - q * FULL;
+            if constexpr (GATE)
+                if (s_info[q] == kInfoRedo) continue;  // left to the FP64-pivot pass
             uint4 v = *reinterpret_cast<const uint4*>(mir + (size_t)q * C::STRIDE + u * 16);
             if (s_info[q] != 0) {
                 const V qn = nan_v<V>();
@@ -112,6 +115,8 @@ CHOL_D void group_store(const BatchParams& p, V* out, const unsigned char* mir, 
         if constexpr (TAIL > 0) {
             for (int f = t; f < m * TAIL; f += C::THREADS) {
                 const int q = f / TAIL, r = f - q * TAIL;
+                if constexpr (GATE)
+                    if (s_info[q] == kInfoRedo) continue;
                 const int e = FULL * C::U + r;
                 const V v = *reinterpret_cast<const V*>(mir + (size_t)q * C::STRIDE + e * sizeof(V));
                 out[s_off[q] + e] = s_info[q] ? nan_v<V>() : v;
@@ -120,6 +125,8 @@ CHOL_D void group_store(const BatchParams& p, V* out, const unsigned char* mir, 
     } else {
         for (int f = t; f < m * C::TN; f += C::THREADS) {
             const int q = f / C::TN, e = f - q * C::TN;
+            if constexpr (GATE)
+                if (s_info[q] == kInfoRedo) continue;
             const int64_t o = s_off[q];
             const int i = s_i[e], j = s_j[e];
             const bool bad = s_info[q] != 0;
@@ -204,7 +211,8 @@ constexpr int group_size() {
 //        mirror, each entry still receives its terms in ascending k); in the
 //        inverse every thread keeps its columns in full (the lower half
 //        mirrored in once per row), so the dot products run on registers.
-template <typename V, int N, int G, int ALG, int W = 4, int MINB = 1>
+// GATE: CHOL_FLAG_PIVOT64_AUTO's cancellation test (FP32 value types only).
+template <typename V, int N, int G, int ALG, int W = 4, int MINB = 1, bool GATE = false>
 __global__ void __launch_bounds__(GroupCfg<V, N, G, W>::THREADS, MINB)
 k_group(BatchParams p) {
     using C = GroupCfg<V, N, G, W>;
@@ -250,7 +258,7 @@ k_group(BatchParams p) {
             s_off[t] = o;
             ok = (o % C::U) == 0;
         }
-        const bool vec = (__syncthreads_and(ok) != 0) && p.layout == 1;
+        const bool vec = (__syncthreads_and(ok) != 0) && p.layout == 1 && p.aligned16;
         group_stage<V, N, C>(p, A, mirs, s_off, s_i, s_j, m, vec);
         cp_async_wait<0>();
         __syncthreads();
@@ -299,9 +307,14 @@ k_group(BatchParams p) {
             if constexpr (kDinvShared) return dinv_s[i]; else return dinv_r[i];
         };
         int info = 0;
+        bool redo = false;
+        constexpr bool gate = GATE;
         // ---------------- factor, Eqs. 3-4, row by row
 #pragma unroll
         for (int i = 0; i < N; ++i) {
+            // a_ii, for the cancellation test (row i of the mirror is written at the end of this step)
+            R aii = R(1);
+            if constexpr (gate) aii = re_of(M[row_base(N, i) + i]);
             V ci[kPair ? 1 : N];  // column i above the diagonal, from the mirror
             V sv[NC];
             if constexpr (kPair) {
@@ -363,6 +376,7 @@ k_group(BatchParams p) {
                 rii = (R)sqrt(td);
                 inv = (R)(1.0 / sqrt(td));
             } else {
+                if (gate && pivot_cancels(tt, aii)) redo = true;
                 if (info == 0 && !pivot_ok(tt)) info = i + 1;
                 pivot_root(tt, rii, inv);
             }
@@ -380,10 +394,10 @@ k_group(BatchParams p) {
             }
             row_sync<ALG>();
         }
-        if (live && h == 0) s_info[q] = info;
+        if (live && h == 0) s_info[q] = redo ? kInfoRedo : info;
         if (store_R || !p.want_inv) {
             __syncthreads();
-            group_store<V, N, C>(p, Ro, mirs, s_off, s_info, s_i, s_j, m, vec, true, false);
+            group_store<V, N, C, GATE>(p, Ro, mirs, s_off, s_info, s_i, s_j, m, vec, true, false);
             __syncthreads();
         }
         if (p.want_inv) {
@@ -496,7 +510,7 @@ k_group(BatchParams p) {
                 row_sync<ALG>();
             }
             __syncthreads();
-            group_store<V, N, C>(p, Xo, mirs, s_off, s_info, s_i, s_j, m, vec, false, p.fill_lower != 0);
+            group_store<V, N, C, GATE>(p, Xo, mirs, s_off, s_info, s_i, s_j, m, vec, false, p.fill_lower != 0);
         }
         } else {
         const bool live = q < m;

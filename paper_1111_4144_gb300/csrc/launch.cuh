@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "batched.cuh"
 #include "dispatch.h"
@@ -22,25 +23,43 @@ constexpr int kernel_kind() {  // 0 lane, 1 group, 2 warp
     return LaneCfg<V, N>::REGS ? 0 : (N <= kGroupMaxN && group_size<V, N>() > 0) ? 1 : 2;
 }
 
-template <typename V, int N>
-static cudaError_t launch_lane(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
+// CHOL_FLAG_PIVOT64_AUTO's FP32 pass: the kernels compiled with the
+// cancellation test (GATE = true; FP32 value types), default variants only.
+template <typename V>
+CHOL_HD bool gate_on(const BatchParams& p) {
+    return sizeof(typename traits<V>::real) == 4 && (p.flags & CHOL_FLAG_PIVOT64_AUTO) &&
+           !(p.flags & CHOL_FLAG_PIVOT64);
+}
+template <typename V>
+constexpr bool gate_built() { return sizeof(typename traits<V>::real) == 4; }
+
+template <typename V, int N, bool GATE>
+static cudaError_t launch_lane_t(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
     constexpr int THREADS = LaneCfg<V, N>::THREADS;
     constexpr size_t SMEM = LaneCfg<V, N>::SMEM;
+    auto kern = k_lane<V, N, GATE>;
     static std::once_flag once;
     static int per_sm = 1;
     static cudaError_t setup_err = cudaSuccess;
     std::call_once(once, [&] {
-        setup_err = cudaFuncSetAttribute(k_lane<V, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+        setup_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
         if (setup_err == cudaSuccess)
-            setup_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lane<V, N>, THREADS, SMEM);
+            setup_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, SMEM);
         if (per_sm < 1) per_sm = 1;
     });
     if (setup_err != cudaSuccess || dry) return setup_err;
     const int chunks = (upper_count + THREADS - 1) / THREADS;
     if (chunks <= 0) return cudaSuccess;
     const int grid = std::min(chunks, device_info().sms * per_sm);
-    k_lane<V, N><<<grid, THREADS, SMEM, s>>>(p);
+    kern<<<grid, THREADS, SMEM, s>>>(p);
     return cudaGetLastError();
+}
+
+template <typename V, int N>
+static cudaError_t launch_lane(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
+    if constexpr (gate_built<V>())
+        if (gate_on<V>(p)) return launch_lane_t<V, N, true>(p, upper_count, s, dry);
+    return launch_lane_t<V, N, false>(p, upper_count, s, dry);
 }
 
 template <typename V>
@@ -67,10 +86,10 @@ static cudaError_t launch_warp(const BatchParams& p, int N, int upper_count, cud
 
 // W warps per CTA; MINB resident CTAs per SM requested from the register
 // allocator (MINB = 2 with W = 8 caps a thread at 128 registers).
-template <typename V, int N, int G, int ALG, int W = 4, int MINB = 1>
+template <typename V, int N, int G, int ALG, int W = 4, int MINB = 1, bool GATE = false>
 static cudaError_t launch_group(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
     using C = GroupCfg<V, N, G, W>;
-    auto kern = k_group<V, N, G, ALG, W, MINB>;
+    auto kern = k_group<V, N, G, ALG, W, MINB, GATE>;
     static std::once_flag once;
     static int per_sm = 1;
     static cudaError_t setup_err = cudaSuccess;
@@ -105,12 +124,15 @@ constexpr int num_variants() {
 template <typename V, int N>
 static cudaError_t launch_fixed(const BatchParams& p, int variant, int upper_count, cudaStream_t s, bool dry) {
     constexpr int kind = kernel_kind<V, N>();
+    // with the cancellation test (CHOL_FLAG_PIVOT64_AUTO) the default variant runs
     if constexpr (kind == 0) {
         if constexpr (num_variants<V, N>() > 1)
-            if (variant == 1) return launch_group<V, N, 2, 1>(p, upper_count, s, dry);
+            if (variant == 1 && !gate_on<V>(p)) return launch_group<V, N, 2, 1>(p, upper_count, s, dry);
         return launch_lane<V, N>(p, upper_count, s, dry);
     } else if constexpr (kind == 1) {
         constexpr int G0 = group_size<V, N>();
+        if constexpr (gate_built<V>())
+            if (gate_on<V>(p)) return launch_group<V, N, G0, 1, 4, 1, true>(p, upper_count, s, dry);
         if constexpr (num_variants<V, N>() > 1)
             if (variant == 1) return launch_group<V, N, (G0 * 2 <= 32 ? G0 * 2 : G0), 1, 8, 2>(p, upper_count, s, dry);
         return launch_group<V, N, G0, 1>(p, upper_count, s, dry);
@@ -154,6 +176,12 @@ constexpr int kSplitN = 14;
 // Launch the kernel of one size class (cls) whose member count is at most
 // upper_count, in the variant the tuning table holds for it; LOW selects
 // which half of the orders this translation unit instantiates.
+// FP32 orders 33..64 (kWideLo..kWideHi in wide.cuh): variant 0 is the
+// register-resident one-warp-per-matrix kernel (k_wide, in its own
+// translation units), variant 1 the shared-memory warp kernel.  FP64 pivots
+// on request (CHOL_FLAG_PIVOT64) run on the warp kernel.
+constexpr int kWideMinN = 33;
+
 template <typename V, bool LOW>
 cudaError_t launch_class_half(const BatchParams& p, int cls, int upper_count, cudaStream_t s, bool dry) {
     if (p.flags & CHOL_FLAG_LDL) return launch_warp<V>(p, cls, upper_count, s, dry);  // LDL form: warp kernel
@@ -162,6 +190,9 @@ cudaError_t launch_class_half(const BatchParams& p, int cls, int upper_count, cu
         return launch_fixed_range<V, 1, kSplitN>(p, cls, v, upper_count, s, dry);
     } else {
         if (cls <= kGroupMaxN) return launch_fixed_range<V, kSplitN + 1, kGroupMaxN>(p, cls, v, upper_count, s, dry);
+        if constexpr (std::is_same<V, float>::value)
+            if (cls >= kWideMinN && (v == 0 || gate_on<V>(p)) && !(p.flags & CHOL_FLAG_PIVOT64))
+                return launch_wide_f32(p, cls, upper_count, s, dry);
         return launch_warp<V>(p, cls, upper_count, s, dry);
     }
 }
@@ -169,7 +200,8 @@ cudaError_t launch_class_half(const BatchParams& p, int cls, int upper_count, cu
 template <typename V, bool LOW>
 int class_variants_half(int cls) {
     if constexpr (LOW) return variants_range<V, 1, kSplitN>(cls);
-    else return cls <= kGroupMaxN ? variants_range<V, kSplitN + 1, kGroupMaxN>(cls) : 1;
+    else if (cls <= kGroupMaxN) return variants_range<V, kSplitN + 1, kGroupMaxN>(cls);
+    else return (std::is_same<V, float>::value && cls >= kWideMinN) ? 2 : 1;
 }
 
 }  // namespace cholinv

@@ -128,6 +128,30 @@ static cudaError_t launch_refine_t(const BatchParams& p, int steps, int automati
     return cudaGetLastError();
 }
 
+// The FP64-pivot pass of CHOL_FLAG_PIVOT64_AUTO over the whole batch (k_redo
+// in batched.cuh): one warp per matrix, most of which exit at once.
+template <typename V>
+static cudaError_t launch_redo_t(const BatchParams& p, cudaStream_t s, bool dry) {
+    static std::once_flag once;
+    static cudaError_t setup = cudaSuccess;
+    std::call_once(once, [&] {
+        setup = cudaFuncSetAttribute(k_redo<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
+    if (setup != cudaSuccess || dry) return setup;
+    const int smax = p.max_n;
+    const size_t per = (size_t)smax * (smax + 1) * sizeof(V);
+    const int warps = (int)std::max<size_t>(1, std::min<size_t>(8, 98304 / per));
+    const int grid = std::max(1, std::min((p.batch + warps - 1) / warps, device_info().sms * 4));
+    k_redo<V><<<grid, 32 * warps, per * warps, s>>>(p, smax, warps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_redo(int dtype, const BatchParams& p, cudaStream_t s, bool dry) {
+    if (dtype == CHOL_F32) return launch_redo_t<float>(p, s, dry);
+    if (dtype == CHOL_C64) return launch_redo_t<cpx<float>>(p, s, dry);
+    return cudaSuccess;  // FP64 value types form Eq. 3 in FP64 already
+}
+
 cudaError_t launch_refine(int dtype, const BatchParams& p, int steps, int automatic, cudaStream_t s, bool dry) {
     if (dtype == CHOL_F32) return launch_refine_t<float>(p, steps, automatic, s, dry);
     if (dtype == CHOL_C64) return launch_refine_t<cpx<float>>(p, steps, automatic, s, dry);

@@ -146,6 +146,7 @@ chol_status_t chol_autotune(chol_dtype_t dt, int32_t max_n, int32_t layout, int3
         p.want_inv = 1;
         p.A = A;
         p.X = X;
+        p.aligned16 = 1;  // cudaMalloc'd
         float best_ms = 1e30f;
         int best = 0;
         std::string times;

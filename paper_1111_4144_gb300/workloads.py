@@ -198,3 +198,59 @@ def gaussian(shape, seed, complex_=False):
     if complex_:
         return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) * np.sqrt(0.5)
     return rng.standard_normal(shape)
+
+
+def bordered_cancellation(batch, N, ratio=16.0, seed=1005, layout=LAYOUT_PACKED, complex_=False):
+    """Hermitian PD matrices whose last pivot cancels: A = D [[I, c], [c^*, d]] D.
+
+    c (N-1 entries, iid N(0,1), complex: CN(0,1)) is drawn exactly
+    representable in FP32 (each part rounded to float32), d = |c|^2 (1 + ratio
+    2^-24) in float64, and D = diag(2^e_i) with e_i uniform on {-2..2} (an
+    exact scaling).  The Schur complement of the identity block,
+    d - |c|^2 (times the scaling), is about `ratio` FP32 ulps of d: the
+    argument of the last pivot is a difference of two nearly equal numbers,
+    while every other pivot and every entry above it is exact in FP32.
+    The caller casts to the working precision (only d is rounded then).
+    """
+    rng = np.random.default_rng(seed)
+    dt = np.complex128 if complex_ else np.float64
+    dense = np.zeros((batch, N, N), dtype=dt)
+    for b in range(batch):
+        c = rng.standard_normal(N - 1)
+        if complex_:
+            c = (c + 1j * rng.standard_normal(N - 1)) * np.sqrt(0.5)
+            c = c.real.astype(np.float32).astype(np.float64) + 1j * c.imag.astype(np.float32).astype(np.float64)
+        else:
+            c = c.astype(np.float32).astype(np.float64)
+        M = np.eye(N, dtype=dt)
+        M[:N - 1, N - 1] = c
+        M[N - 1, :N - 1] = np.conj(c)
+        s = float(np.sum(np.abs(c) ** 2))
+        M[N - 1, N - 1] = s * (1.0 + ratio * 2.0 ** -24)
+        e = 2.0 ** rng.integers(-2, 3, size=N)
+        dense[b] = (e[:, None] * M) * e[None, :]
+    n = np.full(batch, N, dtype=np.int32)
+    flat, off = pack({N: (np.arange(batch), dense)}, n, layout, dt)
+    return Batch(flat, n, off, layout, meta={"kind": "bordered_cancellation", "N": N, "ratio": ratio, "seed": seed})
+
+
+def rotated_log_spaced_torch(N, decades=4.0, seed=1004, reflections=8, device="cuda"):
+    """A = H_r ... H_1 diag(lam) H_1 ... H_r, lam_i = 10^(decades (i-1)/(N-1)),
+    H_k = I - 2 v_k v_k^T with v_k a normalised Gaussian vector (torch's
+    generator on `device`, seeded): the spectrum of log_spaced without a QR
+    factorisation, for orders too large to factor on the host (another,
+    non-Haar eigenbasis).  Each reflection is applied as the rank-2 update
+    A <- A - 2 v w^T - 2 w v^T + 4 (v^T w) v v^T, w = A v.  Returns the float64
+    N x N tensor on `device`, symmetrised."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(seed)
+    lam = 10.0 ** (decades * torch.arange(N, dtype=torch.float64, device=device) / max(N - 1, 1))
+    A = torch.diag(lam)
+    for _ in range(reflections):
+        v = torch.randn(N, dtype=torch.float64, device=device, generator=g)
+        v /= v.norm()
+        w = A @ v
+        A += 4.0 * (v @ w) * torch.outer(v, v)
+        A -= 2.0 * torch.outer(v, w)
+        A -= 2.0 * torch.outer(w, v)
+    return (A + A.T) / 2

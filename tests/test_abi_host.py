@@ -67,6 +67,8 @@ FAKE = 0x100000  # a non-null pointer value; never dereferenced because validati
     (dict(prec=7), "ARG"),
     (dict(refine=3), "ARG"),
     (dict(flags=0x80), "ARG"),
+    (dict(flags=0x40), "ARG"),               # automatic FP64 pivots keep their redo list in info
+    (dict(flags=0x60), "UNSUPPORTED"),       # not with the LDL form
     (dict(prec=1, dt=1), "UNSUPPORTED"),
     (dict(prec=2), "UNSUPPORTED"),
     (dict(n=FAKE), "WORKSPACE"),
@@ -93,4 +95,5 @@ def test_factor_and_plan_argument_checks(L):
     assert L.chol_plan_inv_create(ctypes.byref(h), L.CHOL_F32, 1, None, None, 99, FAKE, None, FAKE, None, o,
                                   None, 0) == L.CHOL_ERR_UNSUPPORTED
     assert L.chol_plan_launch(None, None) == L.CHOL_ERR_ARG
+    assert L.chol_pivot64_redo_count(None, None) == L.CHOL_ERR_ARG
     assert L.chol_plan_destroy(None) == L.CHOL_ERR_ARG

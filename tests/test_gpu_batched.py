@@ -299,3 +299,48 @@ def test_autotune_and_cache(tmp_path):
     assert {n: L.chol_tune_get(L.CHOL_C64, n) for n in chosen} == chosen
     for n in chosen:
         L.chol_tune_set(L.CHOL_C64, n, 0)
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_wide_kernel_every_order(orc, layout):
+    """FP32 orders 33..64: the register-resident one-warp-per-matrix kernel
+    (variant 0) and the shared-memory warp kernel (variant 1), each against
+    the oracle at every order, with a ragged last chunk (CTAs take four
+    matrices), R written and, in the dense layout, the lower half of X
+    filled."""
+    from paper_1111_4144_gb300 import _lib as L
+    try:
+        for N in range(33, 65):
+            assert L.chol_tune_variants(L.CHOL_F32, N) == 2
+            b = make_batch("f32", N, 37 + N % 4, layout, seed=600 + N)
+            Ro, Xo, info_o, A_wide = oracle_inv(orc, b, "f32", fill_lower=(layout == 0))
+            for v in (0, 1):
+                assert L.chol_tune_set(L.CHOL_F32, N, v) == L.CHOL_OK
+                X, info, R = run_inv(b, "f32", mixed=False, want_R=True, fill_lower=(layout == 0))
+                assert np.array_equal(info, info_o)
+                check_errors("f32", b, A_wide, upper_errors(b, X, Xo), f"X (N={N}, variant {v})")
+                check_errors("f32", b, A_wide, upper_errors(b, R, Ro), f"R (N={N}, variant {v})")
+                if layout == 0:
+                    for k in (0, b.batch - 1):
+                        M = X[b.off[k]:b.off[k] + N * N].reshape(N, N)
+                        assert np.array_equal(M, M.T)
+    finally:
+        for N in range(33, 65):
+            L.chol_tune_set(L.CHOL_F32, N, 0)
+
+
+@pytest.mark.parametrize("N", [33, 47, 64])
+def test_wide_kernel_in_place_and_factor_only(orc, N):
+    import torch
+    from paper_1111_4144_gb300 import api
+    b = make_batch("f32", N, 45, 1, seed=700 + N)
+    A_np, _ = cast_batch(b, "f32")
+    Ro, Xo, info_o, A_wide = oracle_inv(orc, b, "f32")
+    A = torch.from_numpy(A_np).cuda()
+    R, info = api.factor(A, max_n=N, layout=1)
+    torch.cuda.synchronize()
+    assert np.array_equal(info.cpu().numpy(), info_o)
+    check_errors("f32", b, A_wide, upper_errors(b, R.cpu().numpy(), Ro), "R (factor only)")
+    api.inv(A, max_n=N, layout=1, X=A)  # X == A
+    torch.cuda.synchronize()
+    check_errors("f32", b, A_wide, upper_errors(b, A.cpu().numpy(), Xo), "X (in place)")

@@ -30,7 +30,7 @@ def env():
     return torch, _lib
 
 
-def _run(torch, L, b, entry):
+def _run(torch, L, b, entry, prec=0, refine_steps=0):
     """Invert batch b (complex64, per-matrix sizes) through one C entry point."""
     dev = torch.device("cuda", 0)
     A = torch.from_numpy(b.A.astype(np.complex64)).to(dev)
@@ -39,7 +39,7 @@ def _run(torch, L, b, entry):
     X = torch.zeros_like(A)
     info = torch.full((b.batch,), -7, dtype=torch.int32, device=dev)
     max_n = int(b.n.max())
-    o = L.opts(layout=b.layout)
+    o = L.opts(prec, refine_steps, 0, b.layout, 0)
     stream = torch.cuda.current_stream().cuda_stream
     if entry == "workspace":
         nbytes = L.chol_workspace_bytes(L.CHOL_CALL_INV, L.CHOL_C64, b.batch, max_n, 1, o)
@@ -57,17 +57,30 @@ def _run(torch, L, b, entry):
 def test_noalloc_matches_workspace_entry_two_calls_in_a_row(env):
     torch, L = env
     # two different batches back to back: the second call reuses the scratch
-    # array left by the first (different class counts and permutation)
+    # array left by the first (different class counts and permutation); the
+    # third has 12 orders, whose class kernels run on forked side streams
     b1 = wl.mimo_covariance(6001, sizes=(4, 8, 16), seed=501, layout=1)
     b2 = wl.mimo_covariance(2500, sizes=(3, 11, 16, 2), seed=502, layout=1)
-    for b in (b1, b2):
+    b3 = wl.mimo_covariance(3000, sizes=tuple(range(1, 13)), seed=503, layout=1)
+    for b in (b1, b2, b3):
         Xw, iw = _run(torch, L, b, "workspace")
         Xn, i_n = _run(torch, L, b, "noalloc")
+        # the same kernels on the same inputs: the same bits
         assert np.array_equal(iw, i_n) and np.all(i_n == 0)
-        A_wide = b.A.astype(np.complex64).astype(np.complex128)
-        err = upper_errors(b, Xn, Xw.astype(np.complex128))
-        tol = tol32(kappas(b, A_wide))
-        assert np.all(err <= tol), f"max err/tol {np.max(err / tol)}"
+        assert np.array_equal(Xn, Xw)
+
+
+def test_noalloc_refinement_matches_workspace_entry(env, orc):
+    torch, L = env
+    b = wl.mimo_covariance(1200, sizes=(5, 9, 16), seed=504, layout=1)
+    Xw, iw = _run(torch, L, b, "workspace", prec=L.CHOL_PREC_FP32_REFINE, refine_steps=1)
+    Xn, i_n = _run(torch, L, b, "noalloc", prec=L.CHOL_PREC_FP32_REFINE, refine_steps=1)
+    assert np.array_equal(iw, i_n) and np.all(i_n == 0)
+    assert np.array_equal(Xn, Xw)
+    A_wide = b.A.astype(np.complex64).astype(np.complex128)
+    _, Xo, _ = orc.inv_batch(A_wide, b.n, b.off, 1, True)
+    err = upper_errors(b, Xn, Xo)
+    assert np.all(err <= tol32(kappas(b, A_wide)))
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch(env):
