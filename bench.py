@@ -38,6 +38,9 @@ SEED = 1001
 METRIC = "inverses/s"
 WORKLOAD = "mimo_covariance_c64_N4-8-16_x1048576_packed"
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+FALLBACK_BF16_TFLOPS_SUSTAINED = 1700.0
+TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 tensor rates
 
 
 def parse():
@@ -58,7 +61,9 @@ def parse():
                          "[1, 1e4], tensor-core products (prints one JSON line)")
     ap.add_argument("--blocked-prec", default="tf32", choices=["tf32", "fp32", "fp64"])
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the other batched workloads (FP64 order 8, uneven FP32, forward + adjoint)")
+                    help="skip the other workloads (FP64 order 8, uneven FP32, forward + adjoint, refinement, "
+                         "large blocked)")
+    ap.add_argument("--no-blocked", action="store_true", help="skip the large blocked workloads (N = 4096, 16384)")
     return ap.parse_args()
 
 
@@ -435,6 +440,164 @@ def extra_workloads(dev, stream, steps):
     return out
 
 
+def _rel_upper(Xg, Xref):
+    """Relative Frobenius error of the upper triangle (numpy, float64)."""
+    G = np.triu(np.asarray(Xg, dtype=np.float64))
+    R = np.triu(np.asarray(Xref, dtype=np.float64))
+    return float(np.linalg.norm(G - R) / np.linalg.norm(R))
+
+
+def blocked_workloads(dev, stream, sizes=(4096, 16384)):
+    """The large single-matrix workload: lambda log-spaced over [1, 1e4],
+    FP32 storage, tensor-core (3xTF32) trailing updates and inverse products,
+    FP64 pivots, two refinement steps with the residual accumulated in FP64;
+    beside it the same library's plain FP64 form on the same (FP32-rounded)
+    matrix.  Times by CUDA events on `stream` (one warm-up call first); the
+    products' times from the library's event pairs (chol_blocked_timing) in a
+    separate call; error against the oracle at 4096 (the whole upper
+    triangle) and against the FP64 form at 16384 (which the GPU tests check
+    against the oracle on sampled columns)."""
+    import ctypes
+    import torch
+    import oracle
+    from paper_1111_4144_gb300 import _lib as L, api, workloads as wl
+    peaks, peak_kind = measured_peaks()
+    tf32_peak = peaks.get("bf16_tflops_sustained", FALLBACK_BF16_TFLOPS_SUSTAINED) * TF32_OVER_BF16
+    out = {}
+    kinds = {"trailing_update": L.CHOL_BLK_TRAILING_UPDATE, "inverse_product": L.CHOL_BLK_INVERSE_PRODUCT,
+             "refine_residual": L.CHOL_BLK_RESIDUAL, "refine_correction": L.CHOL_BLK_CORRECTION,
+             "whole_call": L.CHOL_BLK_WHOLE_CALL}
+    with torch.cuda.stream(stream):
+        for N in sizes:
+            if N <= 8192:
+                A64 = torch.from_numpy(wl.log_spaced(N, decades=4.0, seed=1004).A.reshape(N, N)).to(dev)
+                gen = "log_spaced (Householder QR of a Gaussian, numpy)"
+            else:
+                A64 = wl.rotated_log_spaced_torch(N, decades=4.0, seed=1004, device=dev)
+                gen = "rotated_log_spaced_torch (8 Householder reflections of diag(lambda), on the GPU)"
+            A32 = A64.float().contiguous().view(1, N, N)
+            del A64
+            A64r = A32.double()  # the FP32-rounded matrix, widened
+            X32 = torch.empty_like(A32)
+            X64 = torch.empty_like(A64r)
+            info = torch.empty(1, dtype=torch.int32, device=dev)
+            reps = 3 if N <= 8192 else 1
+            modes = {
+                "tf32_split_pivot64_refine2": (A32, X32, dict(prec=L.CHOL_PREC_TF32_REFINE, refine_steps=2,
+                                                              flags=L.CHOL_FLAG_PIVOT64)),
+                "tf32_split_pivot64_refine0": (A32, X32, dict(prec=L.CHOL_PREC_TF32_REFINE, refine_steps=0,
+                                                              flags=L.CHOL_FLAG_PIVOT64)),
+                "fp64": (A64r, X64, {}),
+            }
+            res = {}
+            Xkeep = {}
+            for name, (Ain, Xout, kw) in modes.items():
+                call = lambda: api.inv(Ain, X=Xout, info=info, stream=stream, **kw)
+                call()
+                torch.cuda.synchronize()
+                ms = _event_ms(stream, call, reps)
+                torch.cuda.synchronize()
+                r = {"ms_per_inverse": ms, "alg_tflops": N ** 3 / (ms / 1e3) / 1e12, "info": int(info.item()),
+                     "device_error": L.chol_last_device_error(None), "reps": reps}
+                if name != "fp64":
+                    # the products' own times, from event pairs in a separate call
+                    L.check(L.chol_blocked_timing(1), "chol_blocked_timing")
+                    call()
+                    torch.cuda.synchronize()
+                    prod = {}
+                    for kn, kc in kinds.items():
+                        f_ms, f_fl, f_n = ctypes.c_float(), ctypes.c_double(), ctypes.c_int32()
+                        L.check(L.chol_blocked_timing_read(kc, ctypes.byref(f_ms), ctypes.byref(f_fl),
+                                                           ctypes.byref(f_n)), "chol_blocked_timing_read")
+                        if f_n.value:
+                            prod[kn] = {"ms": f_ms.value, "launches": f_n.value, "alg_flops": f_fl.value,
+                                        "alg_tflops": f_fl.value / (f_ms.value / 1e3) / 1e12 if f_ms.value else None}
+                    L.check(L.chol_blocked_timing(0), "chol_blocked_timing")
+                    r["products"] = prod
+                    tc = {k: v for k, v in prod.items() if k in ("trailing_update", "inverse_product")}
+                    if tc:
+                        dom = max(tc, key=lambda k: tc[k]["ms"])
+                        ach = tc[dom]["alg_tflops"]
+                        r["tensor_roofline"] = {
+                            "bound": "tensor", "kernel": dom, "achieved": ach, "unit": "TFLOP/s",
+                            "peak": tf32_peak, "frac": ach / tf32_peak,
+                            "mma_frac": 3 * ach / tf32_peak,
+                            "peak_source": peak_kind + " bf16_tflops_sustained x 1.1/2.25 (nominal TF32:BF16)",
+                            "rule": "achieved = algorithmic 2MNK flops of that product kind / its summed event "
+                                    "time; the 3xTF32 split issues three MMA products per FP32 product "
+                                    "(mma_frac = 3 x frac)"}
+                Xkeep[name] = Xout[0].cpu().numpy().copy()
+                res[name] = r
+            entry = {"order": N, "generator": gen, "lambda": "log-spaced over [1, 1e4]", "modes": res,
+                     "speedup_refine2_over_fp64": res["fp64"]["ms_per_inverse"] /
+                     res["tf32_split_pivot64_refine2"]["ms_per_inverse"]}
+            kap = 1e4
+            entry["tolerance"] = {"fp32": max(1e-7 * kap, 2.4e-7), "fp64": 1e-11,
+                                  "rule": "relative Frobenius error of the upper triangle"}
+            if N <= 8192:
+                Aw = A32[0].cpu().numpy().astype(np.float64)
+                threads = os.cpu_count() or 1
+                t0 = time.perf_counter()
+                Ro, inf_o = oracle.chol_mt(Aw, threads)
+                Xo = oracle.inv_rows_mt(Ro, threads)
+                t_orc = time.perf_counter() - t0
+                for name in res:
+                    res[name]["err_vs_oracle"] = _rel_upper(Xkeep[name], Xo)
+                entry["cpu_baseline"] = {"value": 1.0 / t_orc, "unit": "inverses/s", "cores": threads,
+                                         "kind": "oracle", "sample": f"one {N} x {N} inverse (Cholesky + the "
+                                                                     f"Sec. IV.A recurrence, FP64, threads over "
+                                                                     f"each row's entries)"}
+            else:
+                for name in res:
+                    if name != "fp64":
+                        res[name]["err_vs_fp64_form"] = _rel_upper(Xkeep[name], Xkeep["fp64"])
+            out[f"blocked_f32_N{N}_kappa1e4"] = entry
+            del A32, A64r, X32, X64, Xkeep
+            torch.cuda.empty_cache()
+    return out
+
+
+def refine_workload(dev, stream, steps):
+    """FP32 + refinement against the plain FP64 form at the error each
+    reaches: 65,536 FP32 matrices of order 32 with kappa = 1e4 (the
+    differentiation workload's generator), refinement steps 0, 1 and 2 with
+    the residual accumulated in FP64, and the FP64 form of the same library
+    on the same (FP32-rounded) matrices; error against the oracle on 64
+    evenly spaced matrices."""
+    import torch
+    from paper_1111_4144_gb300 import _lib as L, api, workloads as wl
+    batch, N = 1 << 16, 32
+    b = wl.fixed_kappa(batch, N, 1e4, seed=1006, layout=wl.LAYOUT_DENSE)
+    A = torch.from_numpy(b.A.astype(np.float32)).to(dev).view(batch, N, N)
+    A64 = A.double()
+    X = torch.zeros_like(A)
+    X64 = torch.zeros_like(A64)
+    info = torch.empty(batch, dtype=torch.int32, device=dev)
+    reps = max(5, min(steps, 20))
+    idx = np.arange(0, batch, batch // 64)
+    sb, Xo, cpu_v, thr, _ = _oracle_sample(b, idx, "f32")
+    res = {}
+    with torch.cuda.stream(stream):
+        runs = {f"fp32_refine{k}": (A, X, dict(prec=L.CHOL_PREC_FP32_REFINE, refine_steps=k)) for k in (0, 1, 2)}
+        runs["fp64"] = (A64, X64, {})
+        for name, (Ain, Xout, kw) in runs.items():
+            call = lambda: api.inv(Ain, X=Xout, info=info, stream=stream, **kw)
+            for _ in range(3):
+                call()
+            ms = _event_ms(stream, call, reps)
+            torch.cuda.synchronize()
+            Xs = Xout.cpu().numpy()[idx].reshape(-1)
+            r = _dense_err_ratio(sb, Xs, Xo, fp64=False)
+            res[name] = {"ms_per_step": ms, "value": batch / (ms / 1e3), "unit": METRIC,
+                         "max_rel_err_vs_oracle": r[1], "max_err_over_fp32_tol": r[0],
+                         "info_nonzero": int(torch.count_nonzero(info).item())}
+    del A, A64, X, X64
+    return {"matrices": batch, "order": N, "kappa": 1e4, "layout": "dense row-major", "modes": res,
+            "tolerance": "FP32 max(1e-7 kappa, 2.4e-7) = 1e-3; FP64 1e-11 (relative Frobenius, upper triangle)",
+            "cpu_baseline": {"value": cpu_v, "unit": METRIC, "cores": thr, "kind": "oracle",
+                             "sample": f"{len(idx)} evenly spaced matrices of the batch"}}
+
+
 def run_blocked(args, local_rank):
     """One large matrix through the blocked path (the large-order workload)."""
     import torch
@@ -449,17 +612,8 @@ def run_blocked(args, local_rank):
         A = torch.from_numpy(wl.log_spaced(N, decades=4.0, seed=1004).A.reshape(1, N, N)).to(dev).to(dt)
     else:
         # the same spectrum rotated by eight random Householder reflections
-        # H = I - 2 v v^T (applied as rank-2 updates, no factorisation needed)
-        g = torch.Generator(device=dev).manual_seed(1004)
-        lam = 10.0 ** (4.0 * torch.arange(N, dtype=torch.float64, device=dev) / max(N - 1, 1))
-        A64 = torch.diag(lam)
-        for _ in range(8):
-            v = torch.randn(N, dtype=torch.float64, device=dev, generator=g)
-            v /= v.norm()
-            w = A64 @ v
-            A64 += 4.0 * (v @ w) * torch.outer(v, v) - 2.0 * (torch.outer(v, w) + torch.outer(w, v))
-        A = ((A64 + A64.T) / 2).to(dt).reshape(1, N, N)
-        del A64
+        from paper_1111_4144_gb300 import workloads as wl
+        A = wl.rotated_log_spaced_torch(N, decades=4.0, seed=1004, device=dev).to(dt).reshape(1, N, N)
     A = A.contiguous()
     kw = {}
     if args.blocked_prec == "tf32":
@@ -654,6 +808,9 @@ def run_ours(args, rank, world, local_rank):
     # the other workloads last, so that nothing they leave allocated affects the legs above
     if rank == 0 and not args.no_extra:
         out["configs"] = extra_workloads(dev, stream, args.steps)
+        out["configs"]["refine_f32_N32_x65536_kappa1e4"] = refine_workload(dev, stream, args.steps)
+        if not args.no_blocked:
+            out["configs"].update(blocked_workloads(dev, stream))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
