@@ -481,25 +481,32 @@ def blocked_workloads(dev, stream, sizes=(4096, 16384)):
             X32 = torch.empty_like(A32)
             X64 = torch.empty_like(A64r)
             info = torch.empty(1, dtype=torch.int32, device=dev)
-            reps = 3 if N <= 8192 else 1
+            small = N <= 8192
+            reps = 3 if small else 1
+            tf = dict(prec=L.CHOL_PREC_TF32_REFINE, flags=L.CHOL_FLAG_PIVOT64)
+            # the residual of the refinement steps: compensated FP32 pairs (the
+            # library's default) and IEEE FP64 (CHOL_FLAG_RESIDUAL_FP64)
             modes = {
-                "tf32_split_pivot64_refine2": (A32, X32, dict(prec=L.CHOL_PREC_TF32_REFINE, refine_steps=2,
-                                                              flags=L.CHOL_FLAG_PIVOT64)),
-                "tf32_split_pivot64_refine0": (A32, X32, dict(prec=L.CHOL_PREC_TF32_REFINE, refine_steps=0,
-                                                              flags=L.CHOL_FLAG_PIVOT64)),
+                "tf32_split_pivot64_refine2": (A32, X32, dict(tf, refine_steps=2)),
+                "tf32_split_pivot64_refine2_resid64": (A32, X32, dict(prec=L.CHOL_PREC_TF32_REFINE, refine_steps=2,
+                                                                      flags=L.CHOL_FLAG_PIVOT64 |
+                                                                      L.CHOL_FLAG_RESIDUAL_FP64)),
+                "tf32_split_pivot64_refine0": (A32, X32, dict(tf, refine_steps=0)),
                 "fp64": (A64r, X64, {}),
             }
             res = {}
             Xkeep = {}
             for name, (Ain, Xout, kw) in modes.items():
                 call = lambda: api.inv(Ain, X=Xout, info=info, stream=stream, **kw)
-                call()
+                if small:
+                    call()  # warm-up (first-call set-up, workspace)
                 torch.cuda.synchronize()
                 ms = _event_ms(stream, call, reps)
                 torch.cuda.synchronize()
                 r = {"ms_per_inverse": ms, "alg_tflops": N ** 3 / (ms / 1e3) / 1e12, "info": int(info.item()),
                      "device_error": L.chol_last_device_error(None), "reps": reps}
-                if name != "fp64":
+                if name in ("tf32_split_pivot64_refine2", "tf32_split_pivot64_refine0") or \
+                        (small and name != "fp64"):
                     # the products' own times, from event pairs in a separate call
                     L.check(L.chol_blocked_timing(1), "chol_blocked_timing")
                     call()
@@ -530,7 +537,9 @@ def blocked_workloads(dev, stream, sizes=(4096, 16384)):
                 res[name] = r
             entry = {"order": N, "generator": gen, "lambda": "log-spaced over [1, 1e4]", "modes": res,
                      "speedup_refine2_over_fp64": res["fp64"]["ms_per_inverse"] /
-                     res["tf32_split_pivot64_refine2"]["ms_per_inverse"]}
+                     res["tf32_split_pivot64_refine2"]["ms_per_inverse"],
+                     "speedup_refine2_resid64_over_fp64": res["fp64"]["ms_per_inverse"] /
+                     res["tf32_split_pivot64_refine2_resid64"]["ms_per_inverse"]}
             kap = 1e4
             entry["tolerance"] = {"fp32": max(1e-7 * kap, 2.4e-7), "fp64": 1e-11,
                                   "rule": "relative Frobenius error of the upper triangle"}
@@ -561,9 +570,9 @@ def refine_workload(dev, stream, steps):
     """FP32 + refinement against the plain FP64 form at the error each
     reaches: 65,536 FP32 matrices of order 32 with kappa = 1e4 (the
     differentiation workload's generator), refinement steps 0, 1 and 2 with
-    the residual accumulated in FP64, and the FP64 form of the same library
-    on the same (FP32-rounded) matrices; error against the oracle on 64
-    evenly spaced matrices."""
+    the residual in compensated FP32 pairs, one step with it in FP64, and the
+    FP64 form of the same library on the same (FP32-rounded) matrices; error
+    against the oracle on 64 evenly spaced matrices."""
     import torch
     from paper_1111_4144_gb300 import _lib as L, api, workloads as wl
     batch, N = 1 << 16, 32
@@ -579,6 +588,8 @@ def refine_workload(dev, stream, steps):
     res = {}
     with torch.cuda.stream(stream):
         runs = {f"fp32_refine{k}": (A, X, dict(prec=L.CHOL_PREC_FP32_REFINE, refine_steps=k)) for k in (0, 1, 2)}
+        runs["fp32_refine1_resid64"] = (A, X, dict(prec=L.CHOL_PREC_FP32_REFINE, refine_steps=1,
+                                                   flags=L.CHOL_FLAG_RESIDUAL_FP64))
         runs["fp64"] = (A64, X64, {})
         for name, (Ain, Xout, kw) in runs.items():
             call = lambda: api.inv(Ain, X=Xout, info=info, stream=stream, **kw)
@@ -596,6 +607,57 @@ def refine_workload(dev, stream, steps):
             "tolerance": "FP32 max(1e-7 kappa, 2.4e-7) = 1e-3; FP64 1e-11 (relative Frobenius, upper triangle)",
             "cpu_baseline": {"value": cpu_v, "unit": METRIC, "cores": thr, "kind": "oracle",
                              "sample": f"{len(idx)} evenly spaced matrices of the batch"}}
+
+
+def methods_workload(dev, stream, steps):
+    """Table 1 on GPU time: the proposed inverse (Sec. IV.A) against the
+    existing Equation Solving (Sec. III.A) and Triangular Matrix Operations
+    (Sec. III.B) methods, all three on the same one-matrix-per-warp kernel,
+    on 32,768 FP32 matrices each of orders 48 and 64 (lambda log-uniform in
+    [1, 1e3]); beside them the proposed method on the register-resident
+    kernel the library runs by default.  Multiply counts from the closed
+    forms of the oracle's counter (the paper's accounting)."""
+    import torch
+    import oracle
+    from paper_1111_4144_gb300 import _lib as L, api, workloads as wl
+    reps = max(5, min(steps, 20))
+    out = {}
+    with torch.cuda.stream(stream):
+        for N in (48, 64):
+            batch = 32768
+            b = wl.qr_spectrum(batch, lambda rng, m: np.full(m, N),
+                               lambda rng, m, NN: 10.0 ** rng.uniform(0.0, 3.0, size=(m, NN)), 1007 + N,
+                               wl.LAYOUT_PACKED)
+            A = torch.from_numpy(b.A.astype(np.float32)).to(dev)
+            X = torch.zeros_like(A)
+            info = torch.empty(batch, dtype=torch.int32, device=dev)
+            res = {}
+            runs = {"proposed_wide_kernel": (0, 0), "proposed_warp_kernel": (0, 1),
+                    "equation_solving_warp_kernel": (L.CHOL_FLAG_METHOD_ES, 1),
+                    "triangular_matrix_ops_warp_kernel": (L.CHOL_FLAG_METHOD_TMO, 1)}
+            try:
+                for name, (flag, variant) in runs.items():
+                    L.check(L.chol_tune_set(L.CHOL_F32, N, variant), "chol_tune_set")
+                    call = lambda: api.inv(A, max_n=N, layout=wl.LAYOUT_PACKED, X=X, info=info, flags=flag,
+                                           stream=stream)
+                    for _ in range(3):
+                        call()
+                    ms = _event_ms(stream, call, reps)
+                    torch.cuda.synchronize()
+                    res[name] = {"ms": ms, "value": batch / (ms / 1e3), "unit": METRIC,
+                                 "info_nonzero": int(torch.count_nonzero(info).item())}
+            finally:
+                L.chol_tune_set(L.CHOL_F32, N, 0)
+            c = oracle.count_closed_form(N)
+            out[f"order{N}"] = {"matrices": batch, "modes": res, "multiplies_per_matrix": {
+                "proposed": c["proposed"], "equation_solving": c["es"], "triangular_matrix_ops": c["tmo"],
+                "triangular_matrix_ops_structure_exploiting": c["tmo_exploit"]},
+                "ratio_es_over_proposed_ms": res["equation_solving_warp_kernel"]["ms"] /
+                res["proposed_warp_kernel"]["ms"],
+                "ratio_tmo_over_proposed_ms": res["triangular_matrix_ops_warp_kernel"]["ms"] /
+                res["proposed_warp_kernel"]["ms"]}
+            del A, X
+    return out
 
 
 def run_blocked(args, local_rank):
@@ -809,6 +871,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_extra:
         out["configs"] = extra_workloads(dev, stream, args.steps)
         out["configs"]["refine_f32_N32_x65536_kappa1e4"] = refine_workload(dev, stream, args.steps)
+        out["configs"]["table1_methods_f32_x32768"] = methods_workload(dev, stream, args.steps)
         if not args.no_blocked:
             out["configs"].update(blocked_workloads(dev, stream))
 

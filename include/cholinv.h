@@ -101,7 +101,8 @@ typedef enum {
 typedef enum {
     CHOL_PREC_NATIVE = 0,       /* all arithmetic in the dtype's precision */
     CHOL_PREC_FP32_REFINE = 1,  /* F32/C64: FP32 body, then refine_steps Newton-Schulz steps
-                                   X <- X + X (I - A X) with the residual accumulated in FP64 */
+                                   X <- X + X (I - A X) with the residual accumulated in compensated FP32
+                                   pairs, or in FP64 with CHOL_FLAG_RESIDUAL_FP64 */
     CHOL_PREC_TF32_REFINE = 2,  /* blocked large-N path (F32): the trailing updates and the inverse-assembly
                                    products on tcgen05 tensor cores as error-corrected TF32 (three TF32
                                    products per FP32 product, FP32-level accuracy), then refine_steps
@@ -133,6 +134,22 @@ typedef enum {
                                      is counted on the device (chol_pivot64_redo_count).  FP64 value types
                                      ignore the flag; the blocked path (max_n > 64) takes it as
                                      CHOL_FLAG_PIVOT64.  Not with CHOL_FLAG_LDL */
+#define CHOL_FLAG_RESIDUAL_FP64 0x80 /* refinement (CHOL_PREC_FP32_REFINE / CHOL_PREC_TF32_REFINE): accumulate the
+                                     residual I - A X in IEEE FP64.  Without it the residual's sums run in
+                                     compensated FP32 pairs (Ogita-Rump-Oishi Dot2: exact products, error-free
+                                     sums, about 48 significant bits) and no FP64 arithmetic is used; GPUs
+                                     whose FP64 rate is a small fraction of FP32's run that several times
+                                     faster */
+#define CHOL_FLAG_METHOD_ES 0x100  /* batched path, for comparison: the upper half of X by the existing method
+                                     "Equation Solving" (Sec. III.A, Eq. 15) instead of the proposed one: for
+                                     each column j the forward solve R^* b = e_j, then the back substitution
+                                     R x_j = b for x_ij, i <= j.  Same results as the proposed method (its
+                                     b_i, i <= j, are the s_ij of Eq. 24); the forward solves are its extra
+                                     work.  One matrix per warp; not with CHOL_FLAG_LDL */
+#define CHOL_FLAG_METHOD_TMO 0x200 /* batched path, for comparison: the existing method "Triangular Matrix
+                                     Operations" (Sec. III.B, Eqs. 16-19): M = R^{-1} from R m_i = e_i, then
+                                     the upper half of X = M M^*.  One matrix per warp; not with
+                                     CHOL_FLAG_LDL or CHOL_FLAG_METHOD_ES */
 #define CHOL_FLAG_PLAN_ORDERS 0x10 /* chol_plan_inv_create only, batches with per-matrix sizes: read n once
                                      at creation (synchronously) and record kernels only for the orders
                                      present then, instead of one per order 1..max_n.  At every replay a
@@ -152,6 +169,7 @@ typedef struct {
 #define CHOL_CALL_INV 1
 #define CHOL_CALL_BACKWARD 2
 #define CHOL_CALL_INV_HOST 3
+#define CHOL_CALL_MMSE 4
 
 /*
  * chol_factor_batched — Cholesky factor R of each matrix (Sec. II, Eqs. 3-4).
@@ -169,8 +187,9 @@ chol_status_t chol_factor_batched(chol_dtype_t dt, int32_t batch, const int32_t*
  *   A: input; R: optional output of the factor (NULL = not written);
  *   X: output.  With opts->prec = CHOL_PREC_FP32_REFINE (F32 / C64) the
  *   result is refined by refine_steps Newton-Schulz steps
- *   X <- X + X (I - A X), the residual accumulated in FP64 from exact
- *   products of the FP32 operands.  refine_steps = -1 (automatic) refines a
+ *   X <- X + X (I - A X), the residual formed from exact products of the
+ *   FP32 operands and accumulated in compensated FP32 pairs (about 48
+ *   bits) or, with CHOL_FLAG_RESIDUAL_FP64, in FP64.  refine_steps = -1 (automatic) refines a
  *   matrix once when gamma = max_i a_ii x_ii > 4096; gamma lies in
  *   [1, (1 + kappa)^2 / (4 kappa)] with kappa = kappa_2(A), so only
  *   matrices with kappa above about 16,382 can be refined.
@@ -267,6 +286,30 @@ chol_status_t chol_inv_batched_host(chol_dtype_t dt, int32_t batch, const int32_
 chol_status_t chol_inv_batched_noalloc(chol_dtype_t dt, int32_t batch, const int32_t* n, const int64_t* off,
                                        int32_t max_n, const void* A, void* R, void* X, int32_t* info,
                                        const chol_opts_t* opts, void* stream);
+
+/*
+ * chol_mmse_batched — linear MMSE filters W = (H^* H + sigma2 I)^{-1} H^*
+ * of a batch of channel matrices, the usual consumer of the MIMO
+ * covariances A = H^* H + sigma2 I; with sigma2 = 0 and square H (H = D^*)
+ * it gives the inverse of a non-Hermitian D, D^{-1} = D^* (D D^*)^{-1}
+ * (Sec. III.C).  The Hermitian inverse is the proposed method (Sec. II
+ * Eqs. 3-4 and Sec. IV.A, as chol_inv_batched).  Three steps on `stream`:
+ * A = H^* H + sigma2 I (packed, in the workspace), X = A^{-1} (the batched
+ * kernels), W = X H^*.
+ *   H: matrix b is m[b] x n[b] row-major at element hoff[b] (m == NULL:
+ *   every m[b] = max_m; hoff == NULL: b * max_m * max_n).  W: n[b] x m[b]
+ *   row-major at element woff[b] (woff == NULL: b * max_n * max_m).
+ *   n == NULL: every order is max_n (<= 64).  sigma2 >= 0.  opts: precision,
+ *   refinement and flags as for chol_inv_batched (layout and fill_lower do
+ *   not apply).  info as for chol_inv_batched; W of a failed matrix is NaN.
+ *   ws: chol_workspace_bytes(CHOL_CALL_MMSE, dt, batch, max_n, n != NULL,
+ *   opts) bytes, 256-byte aligned.  (max_m max_n + max_n (max_n + 1))
+ *   elements must fit 96 KB (CHOL_ERR_UNSUPPORTED otherwise).
+ */
+chol_status_t chol_mmse_batched(chol_dtype_t dt, int32_t batch, const int32_t* n, const int32_t* m,
+                                const int64_t* hoff, const int64_t* woff, int32_t max_n, int32_t max_m, const void* H,
+                                double sigma2, void* W, int32_t* info, const chol_opts_t* opts, void* ws,
+                                size_t ws_bytes, void* stream);
 
 /* Bytes of device workspace that a call with these arguments needs (0 = none). */
 size_t chol_workspace_bytes(int32_t call, chol_dtype_t dt, int32_t batch, int32_t max_n, int32_t has_sizes,

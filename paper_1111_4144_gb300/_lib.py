@@ -30,7 +30,10 @@ CHOL_FLAG_TF32_SINGLE = 0x8
 CHOL_FLAG_PLAN_ORDERS = 0x10
 CHOL_FLAG_LDL = 0x20
 CHOL_FLAG_PIVOT64_AUTO = 0x40
-CHOL_CALL_FACTOR, CHOL_CALL_INV, CHOL_CALL_BACKWARD, CHOL_CALL_INV_HOST = 0, 1, 2, 3
+CHOL_FLAG_RESIDUAL_FP64 = 0x80
+CHOL_FLAG_METHOD_ES = 0x100
+CHOL_FLAG_METHOD_TMO = 0x200
+CHOL_CALL_FACTOR, CHOL_CALL_INV, CHOL_CALL_BACKWARD, CHOL_CALL_INV_HOST, CHOL_CALL_MMSE = 0, 1, 2, 3, 4
 CHOL_BLK_TRAILING_UPDATE, CHOL_BLK_INVERSE_PRODUCT, CHOL_BLK_RESIDUAL, CHOL_BLK_CORRECTION, CHOL_BLK_WHOLE_CALL = \
     0, 1, 2, 3, 4
 CHOL_NOALLOC_MAX_BATCH = 1048576
@@ -53,6 +56,8 @@ SIGNATURES = {
                                          ctypes.POINTER(chol_opts_t), c_vp]),
     "chol_inv_batched_host": (c_i32, [c_i32, c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp,
                                       ctypes.POINTER(chol_opts_t), c_vp, c_size, c_vp]),
+    "chol_mmse_batched": (c_i32, [c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_i32, c_i32, c_vp, ctypes.c_double, c_vp,
+                                  c_vp, ctypes.POINTER(chol_opts_t), c_vp, c_size, c_vp]),
     "chol_workspace_bytes": (c_size, [c_i32, c_i32, c_i32, c_i32, c_i32, ctypes.POINTER(chol_opts_t)]),
     "chol_status_string": (ctypes.c_char_p, [c_i32]),
     "chol_last_device_error": (c_i32, [c_vp]),
@@ -135,6 +140,10 @@ def chol_inv_batched_noalloc(*args):
 
 def chol_inv_batched_host(*args):
     return load().chol_inv_batched_host(*args)
+
+
+def chol_mmse_batched(*args):
+    return load().chol_mmse_batched(*args)
 
 
 def chol_workspace_bytes(*args):

@@ -156,6 +156,39 @@ class HostInv:
         return X_host, info_host
 
 
+def mmse(H, n=None, m=None, hoff=None, woff=None, max_n=None, max_m=None, *, sigma2=0.0,
+         prec=L.CHOL_PREC_NATIVE, refine_steps=0, flags=0, W=None, info=None, stream=None):
+    """W = (H^* H + sigma2 I)^{-1} H^* for every channel matrix H (Sec. III.C's
+    D^{-1} = D^* (D D^*)^{-1} with H = D^* and sigma2 = 0).
+
+    H: a (batch, M, N) tensor (uniform), or a flat buffer with per-matrix
+    n (orders), m (rows), hoff / woff (element offsets of H and W) as device
+    tensors, max_n and max_m, and W supplied.  Returns (W, info); W is
+    (batch, N, M) for the uniform form."""
+    _need_cuda(H, W, info, n, m, hoff, woff)
+    dt = dtype_code(H)
+    if n is None and m is None and hoff is None and H.dim() == 3:
+        batch, max_m, max_n = H.shape
+        if W is None:
+            W = torch.empty((batch, max_n, max_m), dtype=H.dtype, device=H.device)
+    else:
+        if n is None or max_n is None or max_m is None or W is None:
+            raise ValueError("a flat H needs n, max_n, max_m and W")
+        batch = n.numel()
+    _like("W", W, W)
+    if W.dtype != H.dtype:
+        raise ValueError(f"W must have dtype {H.dtype}")
+    _per_matrix(info, hoff, batch)
+    if info is None:
+        info = torch.empty(batch, dtype=torch.int32, device=H.device)
+    o = L.opts(prec, refine_steps, 0, LAYOUT_PACKED, flags)
+    ws, nbytes = workspace(L.CHOL_CALL_MMSE, dt, batch, max_n, n is not None, o, H.device)
+    st = L.chol_mmse_batched(dt, batch, _p(n), _p(m), _p(hoff), _p(woff), int(max_n), int(max_m), _p(H),
+                             float(sigma2), _p(W), _p(info), o, _p(ws), nbytes, _s(stream))
+    L.check(st, "chol_mmse_batched")
+    return W, info
+
+
 def factor(A, n=None, off=None, max_n=None, *, layout=LAYOUT_DENSE, flags=0, R=None, info=None, stream=None):
     """Cholesky factor R (Eqs. 3-4).  Returns (R, info)."""
     _need_cuda(A, R, info)

@@ -2,6 +2,7 @@
 // argument validation, size-class bucketing, kernel dispatch, plans (CUDA
 // graphs) and the device error word.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -80,9 +81,13 @@ chol_status_t check_common(chol_dtype_t dt, int32_t batch, int32_t max_n, const 
     if (o.layout != 0 && o.layout != 1) return CHOL_ERR_ARG;
     if (o.prec < CHOL_PREC_NATIVE || o.prec > CHOL_PREC_BF16_REFINE) return CHOL_ERR_ARG;
     if (o.refine_steps < -1 || o.refine_steps > 2) return CHOL_ERR_ARG;
-    if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER | CHOL_FLAG_LDL | CHOL_FLAG_PIVOT64_AUTO))
+    if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER | CHOL_FLAG_LDL | CHOL_FLAG_PIVOT64_AUTO |
+                    CHOL_FLAG_RESIDUAL_FP64 | CHOL_FLAG_METHOD_ES | CHOL_FLAG_METHOD_TMO))
         return CHOL_ERR_ARG;
     if ((o.flags & CHOL_FLAG_LDL) && (o.flags & (CHOL_FLAG_PIVOT64 | CHOL_FLAG_PIVOT64_AUTO)))
+        return CHOL_ERR_UNSUPPORTED;
+    if ((o.flags & CHOL_FLAG_METHOD_ES) && (o.flags & CHOL_FLAG_METHOD_TMO)) return CHOL_ERR_ARG;
+    if ((o.flags & (CHOL_FLAG_METHOD_ES | CHOL_FLAG_METHOD_TMO)) && (o.flags & CHOL_FLAG_LDL))
         return CHOL_ERR_UNSUPPORTED;
     if (max_n > kBatchedMaxN) return CHOL_ERR_UNSUPPORTED;
     if (o.prec == CHOL_PREC_TF32_REFINE || o.prec == CHOL_PREC_BF16_REFINE) return CHOL_ERR_UNSUPPORTED;
@@ -322,7 +327,8 @@ chol_status_t blocked_validate(chol_dtype_t dt, int32_t batch, const int32_t* n,
     if (o.prec < CHOL_PREC_NATIVE || o.prec > CHOL_PREC_BF16_REFINE) return CHOL_ERR_ARG;
     if (o.refine_steps < -1 || o.refine_steps > 2) return CHOL_ERR_ARG;
     if (o.flags & CHOL_FLAG_LDL) return CHOL_ERR_UNSUPPORTED;
-    if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER | CHOL_FLAG_TF32_SINGLE | CHOL_FLAG_PIVOT64_AUTO))
+    if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER | CHOL_FLAG_TF32_SINGLE | CHOL_FLAG_PIVOT64_AUTO |
+                    CHOL_FLAG_RESIDUAL_FP64))
         return CHOL_ERR_ARG;
     if (n != nullptr || off != nullptr || o.layout != 0) return CHOL_ERR_UNSUPPORTED;
     if (dt != CHOL_F32 && dt != CHOL_F64) return CHOL_ERR_UNSUPPORTED;
@@ -333,6 +339,12 @@ chol_status_t blocked_validate(chol_dtype_t dt, int32_t batch, const int32_t* n,
     if (batch > 0 && (ws == nullptr || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256 != 0))
         return CHOL_ERR_WORKSPACE;
     return CHOL_OK;
+}
+
+// Bytes of one packed matrix array (A or X) of an MMSE call in the workspace.
+size_t mmse_ws_matrices(chol_dtype_t dt, int32_t batch, int32_t max_n) {
+    const size_t es = dt == CHOL_F32 ? 4 : dt == CHOL_C128 ? 16 : 8;
+    return align_up((size_t)batch * tri(max_n) * es, 256);
 }
 
 // ---------------------------------------------------------------------------
@@ -453,7 +465,7 @@ chol_status_t chol_factor_batched(chol_dtype_t dt, int32_t batch, const int32_t*
         if (sb != CHOL_OK || batch == 0) return sb;
         if (A == nullptr || R == nullptr) return CHOL_ERR_ARG;
         // the factor is formed in R itself (R is the working storage)
-        return blocked_run(dt, batch, max_n, A, nullptr, R, info, blocked_pivot64(o), 0, 0, blocked_tc(o),
+        return blocked_run(dt, batch, max_n, A, nullptr, R, info, blocked_pivot64(o), 0, 0, 0, blocked_tc(o),
                            device_error_word(), ws, static_cast<cudaStream_t>(stream));
     }
     chol_status_t st = check_common(dt, batch, max_n, o);
@@ -478,7 +490,8 @@ chol_status_t chol_inv_batched(chol_dtype_t dt, int32_t batch, const int32_t* n,
         if (sb != CHOL_OK || batch == 0) return sb;
         if (A == nullptr || X == nullptr) return CHOL_ERR_ARG;
         if (X == A || (R != nullptr && (R == A || R == X))) return CHOL_ERR_ARG;
-        return blocked_run(dt, batch, max_n, A, R, X, info, blocked_pivot64(o), rs, 1, blocked_tc(o),
+        return blocked_run(dt, batch, max_n, A, R, X, info, blocked_pivot64(o), rs,
+                           (o.flags & CHOL_FLAG_RESIDUAL_FP64) ? 1 : 0, 1, blocked_tc(o),
                            device_error_word(), ws, static_cast<cudaStream_t>(stream));
     }
     chol_status_t st = inv_validate(dt, batch, n, max_n, A, X, info, o, ws, ws_bytes);
@@ -621,6 +634,10 @@ chol_status_t chol_inv_batched_host(chol_dtype_t dt, int32_t batch, const int32_
 size_t chol_workspace_bytes(int32_t call, chol_dtype_t dt, int32_t batch, int32_t max_n, int32_t has_sizes,
                             const chol_opts_t* opts) {
     const chol_opts_t o = opts_or_default(opts);
+    if (call == CHOL_CALL_MMSE) {
+        if (batch <= 0 || max_n < 1 || max_n > kBatchedMaxN || dt < CHOL_F32 || dt > CHOL_C128) return 0;
+        return 2 * mmse_ws_matrices(dt, batch, max_n) + ws_need_batched(batch, has_sizes);
+    }
     if (max_n > kBatchedMaxN && (call == CHOL_CALL_FACTOR || call == CHOL_CALL_INV))
         return blocked_workspace_bytes(dt, max_n, call == CHOL_CALL_INV ? blocked_refine_steps(o) : 0);
     if (call == CHOL_CALL_FACTOR || call == CHOL_CALL_INV) return ws_need_batched(batch, has_sizes);
@@ -654,6 +671,47 @@ chol_status_t chol_last_device_error(void* stream) {
         if (cudaMemcpy(ds->err, &z, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return CHOL_ERR_CUDA;
     }
     return static_cast<chol_status_t>(v);
+}
+
+chol_status_t chol_mmse_batched(chol_dtype_t dt, int32_t batch, const int32_t* n, const int32_t* m,
+                                const int64_t* hoff, const int64_t* woff, int32_t max_n, int32_t max_m, const void* H,
+                                double sigma2, void* W, int32_t* info, const chol_opts_t* opts, void* ws,
+                                size_t ws_bytes, void* stream) {
+    chol_opts_t o = opts_or_default(opts);
+    o.layout = 1;  // A and X live packed in the workspace
+    o.fill_lower = 0;
+    chol_status_t st = check_common(dt, batch, max_n, o);
+    if (st != CHOL_OK || batch == 0) return st;
+    if (max_m < 1 || !(sigma2 >= 0.0) || !std::isfinite(sigma2)) return CHOL_ERR_ARG;
+    if (H == nullptr || W == nullptr) return CHOL_ERR_ARG;
+    if ((o.flags & CHOL_FLAG_PIVOT64_AUTO) && info == nullptr) return CHOL_ERR_ARG;
+    const size_t es = dt == CHOL_F32 ? 4 : dt == CHOL_C128 ? 16 : 8;
+    if (((size_t)max_m * max_n + (size_t)max_n * (max_n + 1)) * es > 98304) return CHOL_ERR_UNSUPPORTED;
+    const size_t mats = mmse_ws_matrices(dt, batch, max_n);
+    const size_t need = 2 * mats + ws_need_batched(batch, n != nullptr);
+    if (ws == nullptr || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256 != 0) return CHOL_ERR_WORKSPACE;
+    char* w = static_cast<char*>(ws);
+    MmseParams mp;
+    std::memset(&mp, 0, sizeof(mp));
+    mp.batch = batch;
+    mp.n = n;
+    mp.m = m;
+    mp.hoff = hoff;
+    mp.woff = woff;
+    mp.max_n = max_n;
+    mp.max_m = max_m;
+    mp.H = H;
+    mp.A = w;
+    mp.X = w + mats;
+    mp.W = W;
+    mp.info = info;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (launch_mmse(dt, 0, mp, sigma2, s, false) != cudaSuccess) return CHOL_ERR_CUDA;
+    BatchParams p = make_params(batch, n, nullptr, max_n, mp.A, nullptr, mp.X, info, o, 1);
+    st = enqueue_inv(dt, p, w + 2 * mats, s, false, o);
+    if (st != CHOL_OK) return st;
+    if (launch_mmse(dt, 1, mp, sigma2, s, false) != cudaSuccess) return CHOL_ERR_CUDA;
+    return CHOL_OK;
 }
 
 chol_status_t chol_blocked_timing(int32_t enable) {

@@ -48,6 +48,24 @@ struct BatchParams {
 constexpr int kInfoRedo = -2;
 template <typename R> CHOL_D bool pivot_cancels(R t, R aii) { return !(t >= aii * R(0.0009765625)); }
 
+// Arguments of the MMSE-filter kernels (mmse.cu): H_b is m_b x n_b
+// row-major at element hoff[b] (NULL: b * max_m * max_n); W_b = X_b H_b^* is
+// n_b x m_b row-major at woff[b] (NULL: b * max_n * max_m); A and X are the
+// packed Gram matrices and their inverses at b * T(max_n) in the workspace.
+struct MmseParams {
+    int32_t batch;
+    const int32_t* n;
+    const int32_t* m;
+    const int64_t* hoff;
+    const int64_t* woff;
+    int32_t max_n, max_m;
+    const void* H;
+    void* A;
+    void* X;
+    void* W;
+    const int32_t* info;
+};
+
 // Arguments of the adjoint kernel.
 struct BwdParams {
     int32_t batch;
@@ -77,8 +95,10 @@ CHOL_D int64_t member_index(const BatchParams& p, int N, int k) {
     return k;
 }
 CHOL_D int64_t matrix_offset(const BatchParams& p, int N, int64_t b) {
+    (void)N;
     if (p.off) return p.off[b];
-    return b * (p.layout ? tri64(N) : (int64_t)N * N);
+    // without offsets every matrix takes the room of one of order max_n
+    return b * (p.layout ? tri64(p.max_n) : (int64_t)p.max_n * p.max_n);
 }
 CHOL_D int class_count(const BatchParams& p, int N) {
     return p.cls_count ? p.cls_count[N] : p.batch;
@@ -468,6 +488,13 @@ k_lane(BatchParams p) {
     }
 }
 
+// Shared-memory elements of one warp of the warp kernel: the padded square
+// (N x (N+1)), and a second one for the comparison methods' B or M.
+CHOL_HD size_t warp_elems(const BatchParams& p, int N) {
+    const size_t sq = (size_t)N * (N + 1);
+    return (p.flags & (CHOL_FLAG_METHOD_ES | CHOL_FLAG_METHOD_TMO)) ? 2 * sq : sq;
+}
+
 // ---------------------------------------------------------------------------
 // Warp kernel: one matrix per warp, runtime order N (<= 64), lanes own the
 // columns j = lane and j = lane + 32.  The matrix is a padded dense square
@@ -559,7 +586,75 @@ CHOL_D void warp_one(const BatchParams& p, int N, int64_t b, int64_t o, V* S, in
                 }
             }
     }
-    if (p.want_inv && !redo) {
+    const int method = (p.flags & CHOL_FLAG_METHOD_ES) ? 1 : (p.flags & CHOL_FLAG_METHOD_TMO) ? 2 : 0;
+    if (p.want_inv && !redo && method == 1) {
+        // ---- existing method "Equation Solving" (Sec. III.A, Eq. 15): for
+        // every column j the forward solve R^* b = e_j (b_k = 0 for k < j;
+        // lanes own right-hand sides), then the back substitution
+        // x_ij = (b_i - sum_{k>i} r_ik x~_kj) / r_ii for i <= j, rows N..1,
+        // with b_i taken from the forward solve.  B (row j = b for e_j) sits
+        // after the matrix in this warp's shared memory.
+        V* B = S + (size_t)N * LD;
+        for (int jj = lane; jj < N; jj += 32) {
+            for (int k = jj; k < N; ++k) {
+                V t = (k == jj) ? from_real<V>(R(1)) : zero_v<V>();
+                for (int l = jj; l < k; ++l) t = fnma_conj(S[l * LD + k], B[jj * LD + l], t);
+                B[jj * LD + k] = scale_v(t, R(1) / re_of(S[k * LD + k]));
+            }
+        }
+        __syncwarp();
+        for (int i = N - 1; i >= 0; --i) {
+            const R inv = R(1) / re_of(S[i * LD + i]);
+            V x[2] = {zero_v<V>(), zero_v<V>()};
+            R sd = R(0);
+            for (int h = 0; h < 2; ++h) {
+                const int j = lane + 32 * h;
+                if (j > i && j < N) {
+                    V a = zero_v<V>();  // b_i = 0 for i < j
+                    for (int k = i + 1; k < N; ++k) {
+                        const V xt = (k <= j) ? S[k * LD + j] : conj_v(S[j * LD + k]);
+                        a = fma_v(S[i * LD + k], xt, a);
+                    }
+                    x[h] = scale_v(a, -inv);
+                    sd = fma_re_conjb(S[i * LD + j], x[h], sd);
+                }
+            }
+            __syncwarp();
+            for (int h = 0; h < 2; ++h) {
+                const int j = lane + 32 * h;
+                if (j > i && j < N) S[i * LD + j] = x[h];
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, d);
+            __syncwarp();
+            // the diagonal: (b_i - sum_k r_ik x~_ki) / r_ii with b_i = B[i][i] from the forward solve
+            if (lane == 0) S[i * LD + i] = from_real<V>((re_of(B[i * LD + i]) - sd) * inv);
+            __syncwarp();
+        }
+    } else if (p.want_inv && !redo && method == 2) {
+        // ---- existing method "Triangular Matrix Operations" (Sec. III.B,
+        // Eqs. 16-19): M = R^{-1} column by column from R m_i = e_i (lanes
+        // own columns), then the upper half of X = M M^*,
+        // x_ij = sum_{l>=j} m_il conj(m_jl).  M sits after the matrix.
+        V* Mm = S + (size_t)N * LD;
+        for (int ii = lane; ii < N; ii += 32) {
+            Mm[ii * LD + ii] = from_real<V>(R(1) / re_of(S[ii * LD + ii]));
+            for (int k = ii - 1; k >= 0; --k) {
+                V t = zero_v<V>();
+                for (int l = k + 1; l <= ii; ++l) t = fma_v(S[k * LD + l], Mm[l * LD + ii], t);
+                Mm[k * LD + ii] = scale_v(t, -R(1) / re_of(S[k * LD + k]));
+            }
+        }
+        __syncwarp();
+        for (int jj = lane; jj < N; jj += 32) {
+            for (int i = 0; i <= jj; ++i) {
+                V t = zero_v<V>();
+                for (int l = jj; l < N; ++l) t = fma_conjb(Mm[i * LD + l], Mm[jj * LD + l], t);
+                S[i * LD + jj] = (i == jj) ? from_real<V>(re_of(t)) : t;
+            }
+        }
+        __syncwarp();
+    } else if (p.want_inv && !redo) {
         // ---- proposed inverse, rows N..1
         for (int i = N - 1; i >= 0; --i) {
             const int j0 = lane, j1 = lane + 32;
@@ -594,6 +689,8 @@ CHOL_D void warp_one(const BatchParams& p, int N, int64_t b, int64_t o, V* S, in
             if (lane == 0) S[i * LD + i] = from_real<V>(ldl ? inv - sd : (inv - sd) * inv);
             __syncwarp();
         }
+    }
+    if (p.want_inv && !redo) {
         // store X
         for (int i = 0; i < N; ++i)
             for (int j = i + lane; j < N; j += 32) {
@@ -615,7 +712,7 @@ __global__ void k_warp(BatchParams p, int N, int warps_per_cta) {
     using R = typename traits<V>::real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    V* S = reinterpret_cast<V*>(smem_raw) + (size_t)w * N * (N + 1);
+    V* S = reinterpret_cast<V*>(smem_raw) + (size_t)w * warp_elems(p, N);
     const int count = class_count(p, N);
     const bool pivot64 = (p.flags & CHOL_FLAG_PIVOT64) != 0;
     const bool gate = sizeof(R) == 4 && (p.flags & CHOL_FLAG_PIVOT64_AUTO) && !pivot64;
@@ -633,7 +730,7 @@ template <typename V>
 __global__ void k_redo(BatchParams p, int smax, int warps_per_cta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    V* S = reinterpret_cast<V*>(smem_raw) + (size_t)w * smax * (smax + 1);
+    V* S = reinterpret_cast<V*>(smem_raw) + (size_t)w * warp_elems(p, smax);
     for (int64_t b = (int64_t)blockIdx.x * warps_per_cta + w; b < p.batch; b += (int64_t)gridDim.x * warps_per_cta) {
         if (p.info[b] != kInfoRedo) continue;  // warp-uniform
         const int N = p.n ? p.n[b] : p.max_n;

@@ -114,6 +114,66 @@ k_gemm(int M, int N, int K, Tacc alpha, const Tin* __restrict__ A, int64_t lda, 
     }
 }
 
+// Refinement residual E = I - A X for n x n FP32 A (full) and X, each entry
+// a compensated FP32 dot product (f2acc: exact products, error-free sums,
+// about 48 bits) started at delta_ij, rounded to FP32 once at the end.  The
+// tiling is k_gemm's (128 x 128 tiles, 8 x 8 entries per thread).
+__global__ void __launch_bounds__(GB_THREADS)
+k_resid_f2(int n, const float* __restrict__ A, const float* __restrict__ X, float* E) {
+    __shared__ float As[2][GB_K][GB_M + 4];
+    __shared__ float Bs[2][GB_K][GB_N + 4];
+    const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
+    const int t = threadIdx.x;
+    const int tm = (t / 16) * 8, tn = (t % 16) * 8;
+    f2acc acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = f2_init(m0 + tm + i == n0 + tn + j ? 1.f : 0.f);
+    auto load = [&](int buf, int k0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int f = t + r * GB_THREADS;
+            const int mm = f / GB_K, kk = f % GB_K;
+            const int gm = m0 + mm, gk = k0 + kk;
+            As[buf][kk][mm] = (gm < n && gk < n) ? A[(int64_t)gm * n + gk] : 0.f;
+            const int k2 = f / GB_N, nn = f % GB_N;
+            const int gn = n0 + nn, gk2 = k0 + k2;
+            Bs[buf][k2][nn] = (gn < n && gk2 < n) ? X[(int64_t)gk2 * n + gn] : 0.f;
+        }
+    };
+    int buf = 0;
+    load(0, 0);
+    __syncthreads();
+    for (int k0 = 0; k0 < n; k0 += GB_K) {
+        if (k0 + GB_K < n) load(buf ^ 1, k0 + GB_K);
+#pragma unroll
+        for (int kk = 0; kk < GB_K; ++kk) {
+            float a[8], b[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = -As[buf][kk][tm + i];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) b[j] = Bs[buf][kk][tn + j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) f2_fma(acc[i][j], a[i], b[j]);
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int gm = m0 + tm + i;
+        if (gm >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int gn = n0 + tn + j;
+            if (gn < n) E[(int64_t)gm * n + gn] = f2_value(acc[i][j]);
+        }
+    }
+}
+
 // C = alpha * sum_z partial[z] + beta * C, z ascending (deterministic split-K).
 template <typename Tacc, typename Tout>
 __global__ void k_splitk_reduce(int M, int N, int splits, Tacc alpha, const Tacc* partial, Tacc beta, Tout* C,
@@ -919,7 +979,7 @@ size_t blocked_workspace_bytes(int dtype, int n, int refine) {
 
 template <typename T>
 static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, int pivot64, int refine_steps,
-                                 int want_inv, int tc, int* err_word, char* ws, cudaStream_t s) {
+                                 int resid64, int want_inv, int tc, int* err_word, char* ws, cudaStream_t s) {
     using Tacc = T;
     const int b = kblk(sizeof(T) == 8 ? CHOL_F64 : CHOL_F32);
     const int nb = (n + b - 1) / b;
@@ -1091,13 +1151,25 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
         float* X32 = reinterpret_cast<float*>(X);
         k_sym_full<float><<<g1, 256, 0, s>>>(Af, A32, n);
         for (int st = 0; st < refine_steps; ++st) {
-            k_identity<double><<<g1, 256, 0, s>>>(E, n);
-            cudaError_t e = timed(kBlkResidual, gemm_flops(n, n, n, 0), s, [&] {
-                return gemm<float, double, double, false, false>(n, n, n, -1.0, Af, n, X32, n, 1.0, E, n, 0, nullptr,
-                                                                 0, s);
-            });
-            if (e != cudaSuccess) return CHOL_ERR_CUDA;
-            k_narrow<<<g1, 256, 0, s>>>(E32, E, (int64_t)n * n);
+            cudaError_t e;
+            if (resid64) {
+                // IEEE FP64 accumulation of the exact FP64 products of the FP32 values
+                k_identity<double><<<g1, 256, 0, s>>>(E, n);
+                e = timed(kBlkResidual, gemm_flops(n, n, n, 0), s, [&] {
+                    return gemm<float, double, double, false, false>(n, n, n, -1.0, Af, n, X32, n, 1.0, E, n, 0,
+                                                                     nullptr, 0, s);
+                });
+                if (e != cudaSuccess) return CHOL_ERR_CUDA;
+                k_narrow<<<g1, 256, 0, s>>>(E32, E, (int64_t)n * n);
+            } else {
+                // compensated FP32 pairs (about 48 bits), no FP64 arithmetic
+                e = timed(kBlkResidual, gemm_flops(n, n, n, 0), s, [&] {
+                    const dim3 grid((n + GB_N - 1) / GB_N, (n + GB_M - 1) / GB_M);
+                    k_resid_f2<<<grid, GB_THREADS, 0, s>>>(n, Af, X32, E32);
+                    return cudaGetLastError();
+                });
+                if (e != cudaSuccess) return CHOL_ERR_CUDA;
+            }
             // the correction X E goes to a separate buffer (the FP64 one, now free): the
             // product reads X while it runs
             float* Cx = reinterpret_cast<float*>(E);
@@ -1108,13 +1180,16 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
             if (e != cudaSuccess) return CHOL_ERR_CUDA;
             k_axpy<<<g1, 256, 0, s>>>(X32, Cx, (int64_t)n * n);
         }
+        // X E is not exactly symmetric in floating point: the upper half is
+        // the result, mirrored into the lower half (in place)
+        k_sym_full<float><<<g1, 256, 0, s>>>(X32, X32, n);
         if (cudaGetLastError() != cudaSuccess) return CHOL_ERR_CUDA;
     }
     return CHOL_OK;
 }
 
 chol_status_t blocked_run(int dtype, int32_t batch, int32_t n, const void* A, void* R, void* X, int32_t* info,
-                          int pivot64, int refine_steps, int want_inv, int tc, int* err_word, void* ws,
+                          int pivot64, int refine_steps, int resid64, int want_inv, int tc, int* err_word, void* ws,
                           cudaStream_t s) {
     for (int32_t bi = 0; bi < batch; ++bi) {
         const int64_t o = (int64_t)bi * n * n;
@@ -1125,10 +1200,10 @@ chol_status_t blocked_run(int dtype, int32_t batch, int32_t n, const void* A, vo
         if (dtype == CHOL_F32)
             st = blocked_one<float>(static_cast<const float*>(A) + o, R ? static_cast<float*>(R) + o : nullptr,
                                     static_cast<float*>(X) + o, n, info ? info + bi : nullptr, pivot64,
-                                    refine_steps, want_inv, tc, err_word, static_cast<char*>(ws), s);
+                                    refine_steps, resid64, want_inv, tc, err_word, static_cast<char*>(ws), s);
         else if (dtype == CHOL_F64)
             st = blocked_one<double>(static_cast<const double*>(A) + o, R ? static_cast<double*>(R) + o : nullptr,
-                                     static_cast<double*>(X) + o, n, info ? info + bi : nullptr, 0, 0, want_inv,
+                                     static_cast<double*>(X) + o, n, info ? info + bi : nullptr, 0, 0, 0, want_inv,
                                      0, err_word, static_cast<char*>(ws), s);
         else
             return CHOL_ERR_UNSUPPORTED;

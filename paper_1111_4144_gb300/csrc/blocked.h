@@ -16,10 +16,12 @@ size_t blocked_workspace_bytes(int dtype, int n, int refine);
 // to back.  X is the working storage and receives the full Hermitian
 // inverse; R (optional) receives the factor.  Real types only.
 // tc: 0 CUDA-core products; 1 tensor-core TF32; 2 tensor-core TF32 with the
-// three-product split (FP32-level accuracy).  err_word receives
-// CHOL_ERR_TIMEOUT if a tensor-core kernel gave up waiting.
+// three-product split (FP32-level accuracy).  refine_steps (FP32): steps of
+// X <- X + X (I - A X), the residual in compensated FP32 pairs, or in FP64
+// with resid64.  err_word receives CHOL_ERR_TIMEOUT if a tensor-core kernel
+// gave up waiting.
 chol_status_t blocked_run(int dtype, int32_t batch, int32_t n, const void* A, void* R, void* X, int32_t* info,
-                          int pivot64, int refine_steps, int want_inv, int tc, int* err_word, void* ws,
+                          int pivot64, int refine_steps, int resid64, int want_inv, int tc, int* err_word, void* ws,
                           cudaStream_t s);
 
 // Kernel timing (chol_blocked_timing): kinds of recorded products.

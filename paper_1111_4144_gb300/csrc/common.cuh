@@ -126,6 +126,32 @@ CHOL_D void pivot_root(double t, double& rii, double& inv) {
 }
 
 // ---------------------------------------------------------------------------
+// Compensated FP32 accumulation (Ogita, Rump & Oishi, "Accurate sum and dot
+// product", 2005, Algorithm Dot2): a dot product carried as an unevaluated
+// pair s + c.  Each product a b is split exactly into p = fl(a b) and its
+// rounding error fma(a, b, -p); each sum s + p into fl(s + p) and its
+// rounding error (Knuth's TwoSum); the errors accumulate in c.  The result
+// is as accurate as a dot product in twice FP32's precision (about 48
+// bits).  The _rn intrinsics keep the compiler from contracting or
+// reassociating any of the steps.
+// ---------------------------------------------------------------------------
+struct f2acc {
+    float s, c;
+};
+CHOL_D f2acc f2_init(float v) { return {v, 0.f}; }
+// r += a b
+CHOL_D void f2_fma(f2acc& r, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float t = __fadd_rn(r.s, p);
+    const float z = __fsub_rn(t, r.s);
+    const float err = __fadd_rn(__fsub_rn(r.s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    r.s = t;
+    r.c = __fadd_rn(r.c, __fadd_rn(err, e));
+}
+CHOL_D float f2_value(const f2acc& r) { return __fadd_rn(r.s, r.c); }
+
+// ---------------------------------------------------------------------------
 // Index helpers.  Packed upper, row by row: row i holds columns i..n-1.
 // ---------------------------------------------------------------------------
 CHOL_CX int pidx(int n, int i, int j) { return i * n - (i * (i - 1)) / 2 + (j - i); }

@@ -7,6 +7,7 @@ namespace cholinv {
 
 struct BatchParams;
 struct BwdParams;
+struct MmseParams;
 
 struct DeviceInfo {
     int sms = 0;
@@ -40,6 +41,9 @@ cudaError_t launch_refine(int dtype, const BatchParams& p, int steps, int automa
 // FP64-pivot pass of CHOL_FLAG_PIVOT64_AUTO (refine.cu): redoes the matrices
 // whose info the FP32 pass set to kInfoRedo; a no-op for FP64 value types.
 cudaError_t launch_redo(int dtype, const BatchParams& p, cudaStream_t s, bool dry);
+
+// MMSE filters (mmse.cu): stage 0 forms A = H^* H + s2 I, stage 1 W = X H^*.
+cudaError_t launch_mmse(int dtype, int stage, const MmseParams& p, double s2, cudaStream_t s, bool dry);
 
 // Adjoint dA = -X (G + G^H)/2 X (adjoint.cu).
 cudaError_t launch_backward(int dtype, const BwdParams& p, cudaStream_t s, bool dry);

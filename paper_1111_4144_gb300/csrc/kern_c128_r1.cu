@@ -1,0 +1,12 @@
+// Batched kernels for element type complex double, matrix orders 15..20.
+#include "launch.cuh"
+
+namespace cholinv {
+
+cudaError_t launch_class_c128_r1(const BatchParams& p, int cls, int upper, cudaStream_t s, bool dry) {
+    return launch_class_range<cpx<double>, 15, 20>(p, cls, upper, s, dry);
+}
+
+int class_variants_c128_r1(int cls) { return class_variants_range<cpx<double>, 15, 20>(cls); }
+
+}  // namespace cholinv

@@ -64,7 +64,7 @@ static cudaError_t launch_lane(const BatchParams& p, int upper_count, cudaStream
 
 template <typename V>
 static cudaError_t launch_warp(const BatchParams& p, int N, int upper_count, cudaStream_t s, bool dry) {
-    const size_t per_warp = (size_t)N * (N + 1) * sizeof(V);
+    const size_t per_warp = warp_elems(p, N) * sizeof(V);
     int warps = (int)std::max<size_t>(1, std::min<size_t>(4, 98304 / per_warp));
     const size_t smem = per_warp * warps;
     static std::once_flag once;
@@ -169,39 +169,39 @@ template <> constexpr int dtype_code<double>() { return CHOL_F64; }
 template <> constexpr int dtype_code<cpx<float>>() { return CHOL_C64; }
 template <> constexpr int dtype_code<cpx<double>>() { return CHOL_C128; }
 
-// Orders are split over two translation units per element type (compiled
-// in parallel): [1, kSplitN] and (kSplitN, kGroupMaxN] plus the warp kernel.
-constexpr int kSplitN = 14;
-
-// Launch the kernel of one size class (cls) whose member count is at most
-// upper_count, in the variant the tuning table holds for it; LOW selects
-// which half of the orders this translation unit instantiates.
+// The orders of each element type are split over translation units that
+// compile in parallel: [1, 14], [15, 20], [21, 25], [26, 29] and [30, 32]
+// (kClassRanges; the last also takes the orders above 32).
 // FP32 orders 33..64 (kWideLo..kWideHi in wide.cuh): variant 0 is the
 // register-resident one-warp-per-matrix kernel (k_wide, in its own
 // translation units), variant 1 the shared-memory warp kernel.  FP64 pivots
 // on request (CHOL_FLAG_PIVOT64) run on the warp kernel.
 constexpr int kWideMinN = 33;
 
-template <typename V, bool LOW>
-cudaError_t launch_class_half(const BatchParams& p, int cls, int upper_count, cudaStream_t s, bool dry) {
-    if (p.flags & CHOL_FLAG_LDL) return launch_warp<V>(p, cls, upper_count, s, dry);  // LDL form: warp kernel
-    const int v = variant_of(dtype_code<V>(), cls);
-    if constexpr (LOW) {
-        return launch_fixed_range<V, 1, kSplitN>(p, cls, v, upper_count, s, dry);
-    } else {
-        if (cls <= kGroupMaxN) return launch_fixed_range<V, kSplitN + 1, kGroupMaxN>(p, cls, v, upper_count, s, dry);
-        if constexpr (std::is_same<V, float>::value)
-            if (cls >= kWideMinN && (v == 0 || gate_on<V>(p)) && !(p.flags & CHOL_FLAG_PIVOT64))
-                return launch_wide_f32(p, cls, upper_count, s, dry);
+// Launch the kernel of one size class (cls, in [LO, HI], or above
+// kGroupMaxN when HI == kGroupMaxN) whose member count is at most
+// upper_count, in the variant the tuning table holds for it.
+template <typename V, int LO, int HI>
+cudaError_t launch_class_range(const BatchParams& p, int cls, int upper_count, cudaStream_t s, bool dry) {
+    // the LDL form and the comparison methods run on the warp kernel
+    if (p.flags & (CHOL_FLAG_LDL | CHOL_FLAG_METHOD_ES | CHOL_FLAG_METHOD_TMO))
         return launch_warp<V>(p, cls, upper_count, s, dry);
+    const int v = variant_of(dtype_code<V>(), cls);
+    if constexpr (HI == kGroupMaxN) {
+        if (cls > kGroupMaxN) {
+            if constexpr (std::is_same<V, float>::value)
+                if (cls >= kWideMinN && (v == 0 || gate_on<V>(p)) && !(p.flags & CHOL_FLAG_PIVOT64))
+                    return launch_wide_f32(p, cls, upper_count, s, dry);
+            return launch_warp<V>(p, cls, upper_count, s, dry);
+        }
     }
+    return launch_fixed_range<V, LO, HI>(p, cls, v, upper_count, s, dry);
 }
 
-template <typename V, bool LOW>
-int class_variants_half(int cls) {
-    if constexpr (LOW) return variants_range<V, 1, kSplitN>(cls);
-    else if (cls <= kGroupMaxN) return variants_range<V, kSplitN + 1, kGroupMaxN>(cls);
-    else return (std::is_same<V, float>::value && cls >= kWideMinN) ? 2 : 1;
+template <typename V, int LO, int HI>
+int class_variants_range(int cls) {
+    if (cls > kGroupMaxN) return (std::is_same<V, float>::value && cls >= kWideMinN) ? 2 : 1;
+    return variants_range<V, LO, HI>(cls);
 }
 
 }  // namespace cholinv

@@ -1,0 +1,134 @@
+// MMSE filters W = (H^* H + s2 I)^{-1} H^* of a batch of channel matrices H
+// (chol_mmse_batched; the Hermitian inverse by Sec. II + Sec. IV.A, the
+// usual consumer of the MIMO covariances), and with s2 = 0 and a square H,
+// the inverse of a non-Hermitian matrix D = H^*: D^{-1} = D^* (D D^*)^{-1}
+// (Sec. III.C).
+//
+// Three steps on the caller's stream:
+//   k_gram   A = H^* H + s2 I, packed upper, one warp per matrix (H staged
+//            in shared memory, lanes over the entries of A's triangle);
+//   the batched inverse of A (the size-class kernels of chol_inv_batched);
+//   k_apply  W = X H^*, X the full Hermitian inverse (its upper half
+//            mirrored in shared memory), lanes over the entries of W.
+#include <algorithm>
+#include <mutex>
+
+#include "batched.cuh"
+#include "dispatch.h"
+
+namespace cholinv {
+
+template <typename V>
+CHOL_HD size_t mmse_warp_elems(int max_n, int max_m) {
+    return (size_t)max_m * max_n + (size_t)max_n * (max_n + 1);
+}
+
+// Order and rows of matrix b, and its offsets in H, W and the packed A / X.
+CHOL_D void mmse_geom(const MmseParams& p, int64_t b, int& n, int& m, int64_t& oh, int64_t& ow, int64_t& oa) {
+    n = p.n ? p.n[b] : p.max_n;
+    m = p.m ? p.m[b] : p.max_m;
+    oh = p.hoff ? p.hoff[b] : b * (int64_t)p.max_m * p.max_n;
+    ow = p.woff ? p.woff[b] : b * (int64_t)p.max_n * p.max_m;
+    oa = b * tri64(p.max_n);
+}
+
+template <typename V>
+__global__ void k_gram(MmseParams p, typename traits<V>::real s2) {
+    using R = typename traits<V>::real;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    V* Hs = reinterpret_cast<V*>(smem_raw) + (size_t)w * mmse_warp_elems<V>(p.max_n, p.max_m);
+    const V* H = static_cast<const V*>(p.H);
+    V* A = static_cast<V*>(p.A);
+    for (int64_t b = (int64_t)blockIdx.x * wpc + w; b < p.batch; b += (int64_t)gridDim.x * wpc) {
+        int n, m;
+        int64_t oh, ow, oa;
+        mmse_geom(p, b, n, m, oh, ow, oa);
+        if (n < 1 || n > p.max_n || m < 0 || m > p.max_m) continue;  // invalid orders are flagged by the inverse
+        for (int e = lane; e < m * n; e += 32) Hs[e] = H[oh + e];
+        __syncwarp();
+        const int T = tri(n);
+        for (int e = lane; e < T; e += 32) {
+            int i = 0;
+            while (pidx(n, i + 1, i + 1) <= e && i + 1 < n) ++i;
+            const int j = e - pidx(n, i, i) + i;
+            // a_ij = sum_r conj(h_ri) h_rj (+ s2 on the diagonal)
+            V acc = zero_v<V>();
+            for (int r = 0; r < m; ++r) acc = fma_v(conj_v(Hs[r * n + i]), Hs[r * n + j], acc);
+            if (i == j) acc = from_real<V>(re_of(acc) + s2);
+            A[oa + e] = acc;
+        }
+        __syncwarp();
+    }
+}
+
+template <typename V>
+__global__ void k_apply(MmseParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    V* Hs = reinterpret_cast<V*>(smem_raw) + (size_t)w * mmse_warp_elems<V>(p.max_n, p.max_m);
+    V* Xs = Hs + (size_t)p.max_m * p.max_n;
+    const V* H = static_cast<const V*>(p.H);
+    const V* X = static_cast<const V*>(p.X);
+    V* W = static_cast<V*>(p.W);
+    for (int64_t b = (int64_t)blockIdx.x * wpc + w; b < p.batch; b += (int64_t)gridDim.x * wpc) {
+        int n, m;
+        int64_t oh, ow, oa;
+        mmse_geom(p, b, n, m, oh, ow, oa);
+        if (n < 1 || n > p.max_n || m < 0 || m > p.max_m) continue;
+        const bool bad = p.info && p.info[b] != 0;
+        for (int e = lane; e < m * n; e += 32) Hs[e] = H[oh + e];
+        const int LD = n + 1;
+        const int T = tri(n);
+        for (int e = lane; e < T; e += 32) {
+            int i = 0;
+            while (pidx(n, i + 1, i + 1) <= e && i + 1 < n) ++i;
+            const int j = e - pidx(n, i, i) + i;
+            const V x = X[oa + e];
+            Xs[i * LD + j] = x;
+            Xs[j * LD + i] = conj_v(x);
+        }
+        __syncwarp();
+        // w_ik = sum_j x_ij conj(h_kj), W row-major n x m
+        for (int e = lane; e < n * m; e += 32) {
+            const int i = e / m, k = e - i * m;
+            V acc = zero_v<V>();
+            for (int j = 0; j < n; ++j) acc = fma_conjb(Xs[i * LD + j], Hs[k * n + j], acc);
+            W[ow + e] = bad ? nan_v<V>() : acc;
+        }
+        __syncwarp();
+    }
+}
+
+template <typename V>
+static cudaError_t launch_mmse_t(int stage, const MmseParams& p, double s2, cudaStream_t s, bool dry) {
+    using R = typename traits<V>::real;
+    static std::once_flag once;
+    static cudaError_t setup = cudaSuccess;
+    std::call_once(once, [&] {
+        setup = cudaFuncSetAttribute(k_gram<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (setup == cudaSuccess)
+            setup = cudaFuncSetAttribute(k_apply<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
+    if (setup != cudaSuccess || dry) return setup;
+    const size_t per = mmse_warp_elems<V>(p.max_n, p.max_m) * sizeof(V);
+    const int warps = (int)std::max<size_t>(1, std::min<size_t>(8, 98304 / per));
+    const int grid = std::max(1, std::min((p.batch + warps - 1) / warps, device_info().sms * 8));
+    if (stage == 0)
+        k_gram<V><<<grid, 32 * warps, per * warps, s>>>(p, (R)s2);
+    else
+        k_apply<V><<<grid, 32 * warps, per * warps, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mmse(int dtype, int stage, const MmseParams& p, double s2, cudaStream_t s, bool dry) {
+    switch (dtype) {
+        case CHOL_F32: return launch_mmse_t<float>(stage, p, s2, s, dry);
+        case CHOL_F64: return launch_mmse_t<double>(stage, p, s2, s, dry);
+        case CHOL_C64: return launch_mmse_t<cpx<float>>(stage, p, s2, s, dry);
+        case CHOL_C128: return launch_mmse_t<cpx<double>>(stage, p, s2, s, dry);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace cholinv

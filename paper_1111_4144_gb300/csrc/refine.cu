@@ -1,6 +1,8 @@
 // Iterative refinement of a single-precision inverse (FP32 / complex64):
-//   E  = I - A X        (residual: each product of two FP32 numbers is exact
-//                        in FP64, and the sums are accumulated in FP64)
+//   E  = I - A X        (residual: each product of two FP32 numbers exact,
+//                        the sums accumulated in compensated FP32 pairs
+//                        (about 48 bits) or, with CHOL_FLAG_RESIDUAL_FP64,
+//                        in FP64)
 //   X <- X + X E        (Newton-Schulz correction, FP32, upper half of X)
 // The paper states the method's accuracy only for well-conditioned inputs
 // (Sec. II); refinement recovers what FP32 arithmetic loses on harder ones.
@@ -43,7 +45,34 @@ CHOL_HD size_t refine_warp_bytes(int N) {
     return (b + 15) / 16 * 16;
 }
 
-template <typename V>
+// Entry (i, j) of E = I - A X from row i of A and column j of X (shared
+// memory, leading dimension LD): FP64 accumulation (R64), or compensated
+// FP32 pairs (f2acc), rounded to FP32 at the end.
+template <typename V, bool R64>
+CHOL_D V resid_entry(const V* Arow, const V* Xcol, int LD, int n, bool diag) {
+    if constexpr (R64) {
+        using W = typename wide<V>::type;
+        W acc = zero_v<W>();
+        for (int k = 0; k < n; ++k) acc = fma_v(widen(Arow[k]), widen(Xcol[(size_t)k * LD]), acc);
+        return narrow(diag ? from_real<W>(1.0) - acc : zero_v<W>() - acc);
+    } else if constexpr (traits<V>::cplx) {
+        f2acc re = f2_init(diag ? 1.f : 0.f), im = f2_init(0.f);
+        for (int k = 0; k < n; ++k) {
+            const V a = Arow[k], x = Xcol[(size_t)k * LD];
+            f2_fma(re, -a.re, x.re);
+            f2_fma(re, a.im, x.im);
+            f2_fma(im, -a.re, x.im);
+            f2_fma(im, -a.im, x.re);
+        }
+        return V{f2_value(re), f2_value(im)};
+    } else {
+        f2acc r = f2_init(diag ? 1.f : 0.f);
+        for (int k = 0; k < n; ++k) f2_fma(r, -Arow[k], Xcol[(size_t)k * LD]);
+        return f2_value(r);
+    }
+}
+
+template <typename V, bool R64>
 __global__ void k_refine(BatchParams p, int steps, int automatic) {
     using W = typename wide<V>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -53,7 +82,7 @@ __global__ void k_refine(BatchParams p, int steps, int automatic) {
     unsigned char* base = smem_raw + (size_t)w * refine_warp_bytes<V>(N);
     V* Af = reinterpret_cast<V*>(base);
     V* Xf = Af + (size_t)N * LD;
-    W* ec = reinterpret_cast<W*>(Xf + (size_t)N * LD);
+    V* ec = reinterpret_cast<V*>(Xf + (size_t)N * LD);  // column j of E
     const V* A = static_cast<const V*>(p.A);
     V* X = static_cast<V*>(p.X);
 
@@ -91,15 +120,11 @@ __global__ void k_refine(BatchParams p, int steps, int automatic) {
             }
             if (s == todo) break;
             for (int j = 0; j < n; ++j) {
-                for (int i = lane; i < n; i += 32) {
-                    W acc = zero_v<W>();
-                    for (int k = 0; k < n; ++k) acc = fma_v(widen(Af[i * LD + k]), widen(Xf[k * LD + j]), acc);
-                    ec[i] = (i == j) ? from_real<W>(1.0) - acc : zero_v<W>() - acc;
-                }
+                for (int i = lane; i < n; i += 32) ec[i] = resid_entry<V, R64>(Af + i * LD, Xf + j, LD, n, i == j);
                 __syncwarp();
                 for (int i = lane; i <= j; i += 32) {
                     V acc = Xf[i * LD + j];
-                    for (int k = 0; k < n; ++k) acc = fma_v(Xf[i * LD + k], narrow(ec[k]), acc);
+                    for (int k = 0; k < n; ++k) acc = fma_v(Xf[i * LD + k], ec[k], acc);
                     if (i == j) acc = from_real<V>(re_of(acc));
                     X[o + gidx(i, j)] = acc;
                 }
@@ -110,22 +135,29 @@ __global__ void k_refine(BatchParams p, int steps, int automatic) {
     }
 }
 
-template <typename V>
-static cudaError_t launch_refine_t(const BatchParams& p, int steps, int automatic, cudaStream_t s, bool dry) {
+template <typename V, bool R64>
+static cudaError_t launch_refine_r(const BatchParams& p, int steps, int automatic, cudaStream_t s, bool dry) {
+    auto kern = k_refine<V, R64>;
     static std::once_flag once;
     static cudaError_t setup = cudaSuccess;
     std::call_once(once, [&] {
-        setup = cudaFuncSetAttribute(k_refine<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        setup = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     });
     if (setup != cudaSuccess || dry) return setup;
     const size_t per = refine_warp_bytes<V>(p.max_n);
     const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, 98304 / per));
     int per_sm = 1;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine<V>, 32 * warps, per * warps);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, per * warps);
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, std::min((p.batch + warps - 1) / warps, device_info().sms * std::max(per_sm, 1)));
-    k_refine<V><<<grid, 32 * warps, per * warps, s>>>(p, steps, automatic);
+    kern<<<grid, 32 * warps, per * warps, s>>>(p, steps, automatic);
     return cudaGetLastError();
+}
+
+template <typename V>
+static cudaError_t launch_refine_t(const BatchParams& p, int steps, int automatic, cudaStream_t s, bool dry) {
+    if (p.flags & CHOL_FLAG_RESIDUAL_FP64) return launch_refine_r<V, true>(p, steps, automatic, s, dry);
+    return launch_refine_r<V, false>(p, steps, automatic, s, dry);
 }
 
 // The FP64-pivot pass of CHOL_FLAG_PIVOT64_AUTO over the whole batch (k_redo
@@ -139,7 +171,7 @@ static cudaError_t launch_redo_t(const BatchParams& p, cudaStream_t s, bool dry)
     });
     if (setup != cudaSuccess || dry) return setup;
     const int smax = p.max_n;
-    const size_t per = (size_t)smax * (smax + 1) * sizeof(V);
+    const size_t per = warp_elems(p, smax) * sizeof(V);
     const int warps = (int)std::max<size_t>(1, std::min<size_t>(8, 98304 / per));
     const int grid = std::max(1, std::min((p.batch + warps - 1) / warps, device_info().sms * 4));
     k_redo<V><<<grid, 32 * warps, per * warps, s>>>(p, smax, warps);

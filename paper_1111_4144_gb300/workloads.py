@@ -254,3 +254,25 @@ def rotated_log_spaced_torch(N, decades=4.0, seed=1004, reflections=8, device="c
         A -= 2.0 * torch.outer(v, w)
         A -= 2.0 * torch.outer(w, v)
     return (A + A.T) / 2
+
+
+def mimo_channels(batch, sizes=(4, 8, 16), rows_per_col=2, seed=1008, shuffle=True):
+    """Channel matrices H (m = rows_per_col * N rows, N columns, iid CN(0,1)),
+    the orders in equal shares, shuffled with the seed: the inputs of the
+    MMSE filters W = (H^* H + s2 I)^{-1} H^*.  Returns (H flat complex128,
+    n int32, m int32, hoff int64, woff int64): H_b row-major m x n at
+    hoff[b], W_b row-major n x m at woff[b] (both packed back to back)."""
+    rng = np.random.default_rng(seed)
+    k = len(sizes)
+    counts = [batch // k + (1 if i < batch % k else 0) for i in range(k)]
+    n = np.concatenate([np.full(c, s, dtype=np.int32) for s, c in zip(sizes, counts)])
+    if shuffle:
+        n = n[rng.permutation(batch)]
+    m = (rows_per_col * n).astype(np.int32)
+    per = m.astype(np.int64) * n
+    off = np.zeros(batch, dtype=np.int64)
+    if batch > 1:
+        off[1:] = np.cumsum(per)[:-1]
+    total = int(per.sum())
+    H = (rng.standard_normal(total) + 1j * rng.standard_normal(total)) * np.sqrt(0.5)
+    return H, n, m, off, off.copy()

@@ -344,3 +344,48 @@ def test_wide_kernel_in_place_and_factor_only(orc, N):
     api.inv(A, max_n=N, layout=1, X=A)  # X == A
     torch.cuda.synchronize()
     check_errors("f32", b, A_wide, upper_errors(b, A.cpu().numpy(), Xo), "X (in place)")
+
+
+@pytest.mark.parametrize("method", ["es", "tmo"])
+@pytest.mark.parametrize("tag", TAGS)
+def test_comparison_methods_match_oracle(orc, tag, method):
+    """The paper's existing methods on the GPU (Sec. III.A Equation Solving,
+    Sec. III.B Triangular Matrix Operations), one matrix per warp, mixed
+    orders 1..64: X within the tolerance of the oracle's own ES / TMO (and so
+    of the proposed method's X, which both pins tie to the same inverse)."""
+    from paper_1111_4144_gb300 import _lib as L
+    flag = L.CHOL_FLAG_METHOD_ES if method == "es" else L.CHOL_FLAG_METHOD_TMO
+    b = wl.uneven_loguniform(200, nmin=1, nmax=64, seed=2200 if method == "es" else 2201, layout=1)
+    if tag in ("c64", "c128"):
+        mc = wl.mimo_covariance(200, sizes=(3, 17, 40, 64), seed=2202, layout=1)
+        b = mc
+    X, info, _ = run_inv(b, tag, mixed=True, flags=flag)
+    _, Xo, info_o, A_wide = oracle_inv(orc, b, tag)
+    assert np.array_equal(info, info_o) and np.all(info == 0)
+    # the oracle's ES / TMO on every matrix
+    bb = wl.Batch(A_wide, b.n, b.off, b.layout)
+    ref = np.zeros_like(Xo)
+    for k in range(b.batch):
+        N = int(b.n[k])
+        M = bb.matrix(k)
+        M = np.triu(M) + np.conj(np.triu(M, 1)).T
+        Rk, inf = orc.chol(M)
+        Xk = orc.es(Rk) if method == "es" else orc.tmo(Rk)
+        iu = np.triu_indices(N)
+        ref[b.off[k]:b.off[k] + N * (N + 1) // 2] = Xk[iu]
+    check_errors(tag, b, A_wide, upper_errors(b, X, ref), f"X ({method})")
+    check_errors(tag, b, A_wide, upper_errors(b, X, Xo), f"X ({method}) vs proposed")
+
+
+@pytest.mark.parametrize("tag", ["f64", "c128"])
+def test_equation_solving_equals_proposed_bits(tag):
+    """ES's forward solve gives b_i = 0 (i < j) and b_j = 1/r_jj, the s_ij of
+    Eq. 24, after which its back substitution takes the proposed method's
+    steps: on the same one-matrix-per-warp kernel (FP64 orders above 32 run
+    it by default) the two agree bit for bit, as they do in the oracle."""
+    from paper_1111_4144_gb300 import _lib as L
+    b = make_batch(tag, 41, 70, 1, seed=2203)
+    Xp, ip, _ = run_inv(b, tag, mixed=False)
+    Xe, ie, _ = run_inv(b, tag, mixed=False, flags=L.CHOL_FLAG_METHOD_ES)
+    assert np.all(ip == 0) and np.array_equal(ip, ie)
+    assert np.array_equal(Xp, Xe)

@@ -64,14 +64,17 @@ def test_blocked_fp32_parity(orc, N):
         assert _rel(np.triu(X[k]), np.triu(Xo)) <= tol32(kap)
 
 
+@pytest.mark.parametrize("resid64", [False, True])
 @pytest.mark.parametrize("N", [160, 400])
-def test_blocked_fp32_refined(orc, N):
+def test_blocked_fp32_refined(orc, N, resid64):
     from paper_1111_4144_gb300 import _lib as L
     b = wl.log_spaced(N, decades=4.0, seed=5 + N)
     A = b.A.reshape(1, N, N).astype(np.float32)
     _, Xo, _ = _oracle(orc, A[0].astype(np.float64))
     X0, _ = _run(A)
-    X2, info = _run(A, prec=L.CHOL_PREC_FP32_REFINE, refine_steps=2)
+    X2, info = _run(A, prec=L.CHOL_PREC_FP32_REFINE, refine_steps=2,
+                    flags=L.CHOL_FLAG_RESIDUAL_FP64 if resid64 else 0)
+    assert np.array_equal(np.tril(X2[0], -1), np.triu(X2[0], 1).T)
     e0 = _rel(np.triu(X0[0]), np.triu(Xo))
     e2 = _rel(np.triu(X2[0]), np.triu(Xo))
     assert info[0] == 0
@@ -157,6 +160,8 @@ def _large_modes():
     # the large workload's configuration: split TF32 on the tensor cores, FP64
     # pivots, two refinement steps with the residual accumulated in FP64
     return {"tf32_refine2": dict(prec=L.CHOL_PREC_TF32_REFINE, refine_steps=2, flags=L.CHOL_FLAG_PIVOT64),
+            "tf32_refine2_resid64": dict(prec=L.CHOL_PREC_TF32_REFINE, refine_steps=2,
+                                         flags=L.CHOL_FLAG_PIVOT64 | L.CHOL_FLAG_RESIDUAL_FP64),
             "tf32_refine0": dict(prec=L.CHOL_PREC_TF32_REFINE, refine_steps=0, flags=L.CHOL_FLAG_PIVOT64)}
 
 
@@ -183,7 +188,8 @@ def test_blocked_4096_against_oracle(orc):
         assert np.array_equal(np.tril(X, -1), np.triu(X, 1).T)
         errs[name] = _rel(np.triu(X).astype(np.float64), np.triu(Xo))
         assert errs[name] <= tol, (name, errs[name], tol)
-    assert errs["tf32_refine2"] <= 64 * U32 and errs["tf32_refine2"] < errs["tf32_refine0"] / 10, errs
+    for name in ("tf32_refine2", "tf32_refine2_resid64"):
+        assert errs[name] <= 64 * U32 and errs[name] < errs["tf32_refine0"] / 10, errs
     X64, info = api.inv(A32.double())
     torch.cuda.synchronize()
     assert info.item() == 0

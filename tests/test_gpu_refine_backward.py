@@ -23,14 +23,19 @@ def _full(Xu):
     return np.triu(Xu) + np.conj(np.triu(Xu, 1)).T
 
 
+@pytest.mark.parametrize("resid64", [False, True])
 @pytest.mark.parametrize("N", [8, 16, 40])
-def test_refinement_steps_reduce_error(orc, N):
+def test_refinement_steps_reduce_error(orc, N, resid64):
+    """Refinement with the residual in compensated FP32 pairs (default) or
+    in FP64 (CHOL_FLAG_RESIDUAL_FP64): each step cuts the error tenfold or
+    reaches FP32 accuracy."""
     from paper_1111_4144_gb300 import _lib as L
     b = wl.fixed_kappa(60, N, 1e4, seed=70 + N, layout=0)
     _, Xo, _, A_wide = oracle_inv(orc, b, "f32")
     errs = []
+    flags = L.CHOL_FLAG_RESIDUAL_FP64 if resid64 else 0
     for steps in (0, 1, 2):
-        X, info, _ = run_inv(b, "f32", mixed=False, prec=L.CHOL_PREC_FP32_REFINE, refine_steps=steps)
+        X, info, _ = run_inv(b, "f32", mixed=False, prec=L.CHOL_PREC_FP32_REFINE, refine_steps=steps, flags=flags)
         assert np.all(info == 0)
         errs.append(upper_errors(b, X, Xo))
     k = kappas(b, A_wide)
@@ -168,3 +173,18 @@ def test_autograd_fp32_against_fp64_central_differences(orc):
             # the upper-parameter gradient pairs with the upper triangle of E
             an = float(np.sum(np.triu(g_upper[k]) * np.triu(E)))
             assert abs(fd - an) <= (2 * tol32(1e2) + 32 * U32) * max(abs(fd), 1.0), (fd, an)
+
+
+@pytest.mark.parametrize("N", [6, 16, 33])
+def test_refinement_complex_both_residuals(orc, N):
+    """Complex64 refinement, both residual forms, against the oracle."""
+    from paper_1111_4144_gb300 import _lib as L
+    b = wl.mimo_covariance(48, sizes=(N,), sigma2=1e-3, seed=80 + N, layout=1, shuffle=False)
+    _, Xo, _, A_wide = oracle_inv(orc, b, "c64")
+    X0, _, _ = run_inv(b, "c64", mixed=False)
+    e0 = upper_errors(b, X0, Xo)
+    for flags in (0, L.CHOL_FLAG_RESIDUAL_FP64):
+        X, info, _ = run_inv(b, "c64", mixed=False, prec=L.CHOL_PREC_FP32_REFINE, refine_steps=2, flags=flags)
+        assert np.all(info == 0)
+        e = upper_errors(b, X, Xo)
+        assert np.all(e <= np.maximum(e0 / 10, 64 * U32)), (flags, e.max(), e0.max())
