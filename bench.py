@@ -660,6 +660,54 @@ def methods_workload(dev, stream, steps):
     return out
 
 
+def mmse_workload(dev, stream, steps):
+    """MMSE filters W = (H^* H + 0.1 I)^{-1} H^* of 262,144 MIMO channels
+    (N in {4, 8, 16}, 2N x N, iid CN(0,1), complex64): the Gram matrix, the
+    batched inverse and W = X H^* (chol_mmse_batched), against the oracle's
+    mmse_filter on 256 sampled channels."""
+    import torch
+    import oracle
+    from paper_1111_4144_gb300 import api, workloads as wl
+    peaks, peak_kind = measured_peaks()
+    hbm = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
+    batch = 1 << 18
+    H, n, m, hoff, woff = wl.mimo_channels(batch, sizes=SIZES, seed=1008)
+    H64 = H.astype(np.complex64)
+    del H
+    with torch.cuda.stream(stream):
+        Ht = torch.from_numpy(H64).to(dev)
+        W = torch.empty_like(Ht)
+        nt, mt = torch.from_numpy(n).to(dev), torch.from_numpy(m).to(dev)
+        ht, wt = torch.from_numpy(hoff).to(dev), torch.from_numpy(woff).to(dev)
+        info = torch.empty(batch, dtype=torch.int32, device=dev)
+        call = lambda: api.mmse(Ht, nt, mt, ht, wt, max(SIZES), 2 * max(SIZES), sigma2=SIGMA2, W=W, info=info,
+                                stream=stream)
+        for _ in range(3):
+            call()
+        ms = _event_ms(stream, call, max(5, min(steps, 20)))
+        torch.cuda.synchronize()
+        Wg = W.cpu().numpy()
+        nz = int(torch.count_nonzero(info).item())
+    rng = np.random.default_rng(13)
+    worst, worst_ratio = 0.0, 0.0
+    for b in rng.choice(batch, 256, replace=False):
+        N, M = int(n[b]), int(m[b])
+        Hb = H64[hoff[b]:hoff[b] + M * N].reshape(M, N).astype(np.complex128)
+        Wo, _ = oracle.mmse_filter(Hb, SIGMA2)
+        e = np.linalg.norm(Wg[woff[b]:woff[b] + N * M].reshape(N, M) - Wo) / np.linalg.norm(Wo)
+        A = np.conj(Hb).T @ Hb + SIGMA2 * np.eye(N)
+        worst, worst_ratio = max(worst, e), max(worst_ratio, e / max(1e-7 * np.linalg.cond(A), 2.4e-7))
+    nbytes = 2 * int((m.astype(np.int64) * n).sum()) * 8
+    del Ht, W
+    return {"channels": batch, "sizes": list(SIZES), "rows": "2N", "sigma2": SIGMA2, "ms_per_step": ms,
+            "value": batch / (ms / 1e3), "unit": "filters/s", "info_nonzero": nz,
+            "achieved_gbs": nbytes / (ms / 1e3) / 1e9, "frac": nbytes / (ms / 1e3) / 1e9 / hbm,
+            "bytes_rule": "H read + W written (2 x 2N^2 x 8 B per channel); the Gram matrix and inverse "
+                          "(packed, in the workspace) are extra traffic",
+            "max_rel_err_vs_oracle": worst, "max_err_over_fp32_tol": worst_ratio,
+            "steps": "A = H^* H + s2 I, the batched inverse (Sec. II + IV.A), W = X H^*"}
+
+
 def run_blocked(args, local_rank):
     """One large matrix through the blocked path (the large-order workload)."""
     import torch
@@ -872,6 +920,7 @@ def run_ours(args, rank, world, local_rank):
         out["configs"] = extra_workloads(dev, stream, args.steps)
         out["configs"]["refine_f32_N32_x65536_kappa1e4"] = refine_workload(dev, stream, args.steps)
         out["configs"]["table1_methods_f32_x32768"] = methods_workload(dev, stream, args.steps)
+        out["configs"]["mmse_c64_N4-8-16_x262144"] = mmse_workload(dev, stream, args.steps)
         if not args.no_blocked:
             out["configs"].update(blocked_workloads(dev, stream))
 

@@ -290,9 +290,10 @@ chol_status_t chol_inv_batched_noalloc(chol_dtype_t dt, int32_t batch, const int
 /*
  * chol_mmse_batched — linear MMSE filters W = (H^* H + sigma2 I)^{-1} H^*
  * of a batch of channel matrices, the usual consumer of the MIMO
- * covariances A = H^* H + sigma2 I; with sigma2 = 0 and square H (H = D^*)
- * it gives the inverse of a non-Hermitian D, D^{-1} = D^* (D D^*)^{-1}
- * (Sec. III.C).  The Hermitian inverse is the proposed method (Sec. II
+ * covariances A = H^* H + sigma2 I.  With sigma2 = 0 and a square H it
+ * inverts a non-Hermitian matrix through a Hermitian one (Sec. III.C): for
+ * H = D^*, W = (D D^*)^{-1} D and W^* = D^* (D D^*)^{-1} = D^{-1}, the
+ * paper's form; for H = D, W = (D^* D)^{-1} D^* = D^{-1} directly.  The Hermitian inverse is the proposed method (Sec. II
  * Eqs. 3-4 and Sec. IV.A, as chol_inv_batched).  Three steps on `stream`:
  * A = H^* H + sigma2 I (packed, in the workspace), X = A^{-1} (the batched
  * kernels), W = X H^*.

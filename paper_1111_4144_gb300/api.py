@@ -158,8 +158,8 @@ class HostInv:
 
 def mmse(H, n=None, m=None, hoff=None, woff=None, max_n=None, max_m=None, *, sigma2=0.0,
          prec=L.CHOL_PREC_NATIVE, refine_steps=0, flags=0, W=None, info=None, stream=None):
-    """W = (H^* H + sigma2 I)^{-1} H^* for every channel matrix H (Sec. III.C's
-    D^{-1} = D^* (D D^*)^{-1} with H = D^* and sigma2 = 0).
+    """W = (H^* H + sigma2 I)^{-1} H^* for every channel matrix H (with
+    sigma2 = 0 and H = D^* square, W^* = D^* (D D^*)^{-1} = D^{-1}, Sec. III.C).
 
     H: a (batch, M, N) tensor (uniform), or a flat buffer with per-matrix
     n (orders), m (rows), hoff / woff (element offsets of H and W) as device

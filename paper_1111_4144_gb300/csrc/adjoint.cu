@@ -3,12 +3,14 @@
 // the gradient of a real loss L(X) with respect to a Hermitian A when
 // X = A^{-1} and G = dL/dX.  It reuses the forward X (no refactorisation).
 //
-// One warp per matrix.  X (expanded from its stored upper half) and S are
-// squares in shared memory; T = S X is formed column by column (lane j owns
-// columns j and j+32), then the upper half of -X T, mirrored to keep dA
-// exactly Hermitian.
+// Orders up to 32: a register-tiled warp per matrix (k_backward_tiled).
+// Larger orders (and complex128): one warp per matrix with X (expanded from
+// its stored upper half) and S as squares in shared memory; T = S X is
+// formed column by column (lane j owns columns j and j+32), then the upper
+// half of -X T, mirrored to keep dA exactly Hermitian.
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "batched.cuh"
 #include "dispatch.h"
@@ -82,8 +84,159 @@ __global__ void k_backward(BwdParams p) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Register-tiled form for orders up to 32 (zero-padded to 32): one warp per
+// matrix, lane l computes the 4 x 8 block at rows 4 (l / 4).., columns
+// 8 (l % 4).. of each 32 x 32 product, from shared-memory row slices (a
+// 4-wide slice of the left operand, stored transposed, and an 8-wide slice
+// of the right one per k).
+//   Xs: X in full (Xs[k][r] = x_kr), the right operand of T = S X and,
+//       conjugated, the transposed left operand of X T;
+//   St: S^T (St[k][r] = s_rk), S = (G + G^H)/2, G first staged in Ts;
+//   Ts: T = S X; then -X T is staged in St and its upper half written,
+//       mirrored, so that dA is exactly Hermitian.
+// ---------------------------------------------------------------------------
+constexpr int kTB = 32;          // padded order
+constexpr int kTLD = kTB + 4;    // row stride
+
+template <typename V>
+CHOL_HD size_t bwd_tiled_warp_bytes() {
+    return (size_t)3 * kTB * kTLD * sizeof(V);
+}
+
+// acc[r][c] += sum_k op(Lt[k][r0 + r]) Rm[k][c0 + c], k = 0..31; op is the
+// conjugate when CONJ
+template <typename V, bool CONJ>
+CHOL_D void tile_product(const V* Lt, const V* Rm, int r0, int c0, V (&acc)[4][8]) {
+#pragma unroll 4
+    for (int k = 0; k < kTB; ++k) {
+        V a[4], b[8];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a[r] = CONJ ? conj_v(Lt[k * kTLD + r0 + r]) : Lt[k * kTLD + r0 + r];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) b[c] = Rm[k * kTLD + c0 + c];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] = fma_v(a[r], b[c], acc[r][c]);
+    }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(128) k_backward_tiled(BwdParams p) {
+    using R = typename traits<V>::real;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    V* Xs = reinterpret_cast<V*>(smem_raw + (size_t)w * bwd_tiled_warp_bytes<V>());
+    V* St = Xs + kTB * kTLD;
+    V* Ts = St + kTB * kTLD;
+    const V* X = static_cast<const V*>(p.X);
+    const V* G = static_cast<const V*>(p.G);
+    V* dA = static_cast<V*>(p.dA);
+    const int r0 = (lane / 4) * 4, c0 = (lane % 4) * 8;
+    const int N = p.max_n;
+    for (int b = blockIdx.x * wpc + w; b < p.batch; b += gridDim.x * wpc) {
+        const int n = p.n ? p.n[b] : N;
+        if (n <= 0 || n > N) continue;
+        const int64_t og = p.off ? p.off[b] : (int64_t)b * N * N;
+        const int64_t ox = p.xoff ? p.xoff[b] : (int64_t)b * (p.layout ? tri64(N) : (int64_t)N * N);
+        // zero padding beyond n; G staged in Ts
+        for (int e = lane; e < kTB * kTLD; e += 32) {
+            Xs[e] = zero_v<V>();
+            St[e] = zero_v<V>();
+        }
+        for (int e = lane; e < n * n; e += 32) {
+            const int k = e / n, r = e - k * n;
+            Ts[k * kTLD + r] = G[og + e];
+        }
+        __syncwarp();
+        // X in full from its upper half
+        if (p.layout) {
+            for (int e = lane; e < tri(n); e += 32) {
+                int i = 0;
+                while (pidx(n, i + 1, i + 1) <= e && i + 1 < n) ++i;
+                const int j = e - pidx(n, i, i) + i;
+                V x = X[ox + e];
+                if (i == j) x = from_real<V>(re_of(x));
+                Xs[i * kTLD + j] = x;
+                Xs[j * kTLD + i] = conj_v(x);
+            }
+        } else {
+            for (int e = lane; e < n * n; e += 32) {
+                const int i = e / n, j = e - i * n;
+                if (j < i) continue;
+                V x = X[ox + e];
+                if (i == j) x = from_real<V>(re_of(x));
+                Xs[i * kTLD + j] = x;
+                Xs[j * kTLD + i] = conj_v(x);
+            }
+        }
+        // St[k][r] = s_rk = (g_rk + conj(g_kr)) / 2
+        for (int e = lane; e < n * n; e += 32) {
+            const int k = e / n, r = e - k * n;
+            V sv = scale_v(Ts[r * kTLD + k] + conj_v(Ts[k * kTLD + r]), R(0.5));
+            if (k == r) sv = from_real<V>(re_of(sv));
+            St[k * kTLD + r] = sv;
+        }
+        __syncwarp();
+        V acc[4][8];
+        // T = S X
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] = zero_v<V>();
+        tile_product<V, false>(St, Xs, r0, c0, acc);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) Ts[(r0 + r) * kTLD + c0 + c] = acc[r][c];
+        __syncwarp();
+        // X T: the transposed left operand is conj(X) (X Hermitian): conj(Xs[k][r]) = x_rk
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] = zero_v<V>();
+        tile_product<V, traits<V>::cplx>(Xs, Ts, r0, c0, acc);
+        // -X T staged in St (S is no longer read), then dA row by row
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) St[(r0 + r) * kTLD + c0 + c] = zero_v<V>() - acc[r][c];
+        __syncwarp();
+        for (int e = lane; e < n * n; e += 32) {
+            const int i = e / n, j = e - i * n;
+            V d = (i <= j) ? St[i * kTLD + j] : conj_v(St[j * kTLD + i]);
+            if (i == j) d = from_real<V>(re_of(d));
+            if (p.flags & CHOL_FLAG_GRAD_UPPER) d = (i < j) ? scale_v(d, R(2)) : (i == j) ? d : zero_v<V>();
+            dA[og + e] = d;
+        }
+        __syncwarp();
+    }
+}
+
+template <typename V>
+static cudaError_t launch_bwd_tiled(const BwdParams& p, cudaStream_t s, bool dry) {
+    static std::once_flag once;
+    static cudaError_t setup = cudaSuccess;
+    constexpr int warps = 4;
+    const size_t smem = bwd_tiled_warp_bytes<V>() * warps;
+    std::call_once(once, [&] {
+        setup = cudaFuncSetAttribute(k_backward_tiled<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (setup != cudaSuccess || dry) return setup;
+    int per_sm = 1;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_tiled<V>, 32 * warps, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min((p.batch + warps - 1) / warps, device_info().sms * std::max(per_sm, 1)));
+    k_backward_tiled<V><<<grid, 32 * warps, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
 template <typename V>
 static cudaError_t launch_bwd_t(const BwdParams& p, cudaStream_t s, bool dry) {
+    // orders up to 32 (complex128 excepted: its register tile is too large)
+    if constexpr (!std::is_same<V, cpx<double>>::value)
+        if (p.max_n <= kTB) return launch_bwd_tiled<V>(p, s, dry);
     static std::once_flag once;
     static cudaError_t setup = cudaSuccess;
     std::call_once(once, [&] {

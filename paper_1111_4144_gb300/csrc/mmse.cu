@@ -1,8 +1,8 @@
 // MMSE filters W = (H^* H + s2 I)^{-1} H^* of a batch of channel matrices H
 // (chol_mmse_batched; the Hermitian inverse by Sec. II + Sec. IV.A, the
-// usual consumer of the MIMO covariances), and with s2 = 0 and a square H,
-// the inverse of a non-Hermitian matrix D = H^*: D^{-1} = D^* (D D^*)^{-1}
-// (Sec. III.C).
+// usual consumer of the MIMO covariances).  With s2 = 0 and a square H = D^*
+// it gives W = (D D^*)^{-1} D, whose conjugate transpose is the inverse of
+// the non-Hermitian D in Sec. III.C's form, D^{-1} = D^* (D D^*)^{-1}.
 //
 // Three steps on the caller's stream:
 //   k_gram   A = H^* H + s2 I, packed upper, one warp per matrix (H staged

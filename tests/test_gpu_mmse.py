@@ -76,8 +76,9 @@ def test_mmse_uniform_tensor_form(orc):
 
 @pytest.mark.parametrize("tag", ["c128", "f64", "c64"])
 def test_nonhermitian_inverse_through_d_dstar(orc, tag):
-    """Sec. III.C: D^{-1} = D^* (D D^*)^{-1}; with H = D^* (square) and s2 = 0
-    the filter is D^{-1}."""
+    """Sec. III.C: D^{-1} = D^* (D D^*)^{-1}.  With H = D^* (square) and
+    s2 = 0 the filter is W = (D D^*)^{-1} D, whose conjugate transpose is
+    D^* (D D^*)^{-1} = D^{-1} ((D D^*)^{-1} is Hermitian)."""
     import torch
     from paper_1111_4144_gb300 import api
     rng = np.random.default_rng(3102)
@@ -86,9 +87,9 @@ def test_nonhermitian_inverse_through_d_dstar(orc, tag):
     D = D + 2 * np.sqrt(N) * np.eye(N)  # well conditioned
     D = D.astype(NP[tag])
     Hs = np.conj(np.transpose(D, (0, 2, 1))).copy()
-    Dinv, info = api.mmse(torch.from_numpy(Hs).cuda(), sigma2=0.0)
+    W, info = api.mmse(torch.from_numpy(Hs).cuda(), sigma2=0.0)
     torch.cuda.synchronize()
-    Dinv = Dinv.cpu().numpy()
+    Dinv = np.conj(np.transpose(W.cpu().numpy(), (0, 2, 1)))
     assert np.all(info.cpu().numpy() == 0)
     wide = np.complex128 if tag.startswith("c") else np.float64
     for b in range(batch):
