@@ -60,10 +60,17 @@ def parse():
                     help="time the blocked path instead: one FP32 matrix of this order, lambda log-spaced over "
                          "[1, 1e4], tensor-core products (prints one JSON line)")
     ap.add_argument("--blocked-prec", default="tf32", choices=["tf32", "fp32", "fp64"])
+    ap.add_argument("--blocked-refine", type=int, default=2,
+                    help="refinement steps of the FP32 / TF32 blocked run (the large workload takes 2, with FP64 "
+                         "pivots)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads (FP64 order 8, uneven FP32, forward + adjoint, refinement, "
                          "large blocked)")
     ap.add_argument("--no-blocked", action="store_true", help="skip the large blocked workloads (N = 4096, 16384)")
+    ap.add_argument("--profile-case", default="",
+                    help="profiling case DTYPE:N:BATCH (e.g. f32:64:32768): a uniform packed batch of real SPD "
+                         "(lambda log-uniform in [1, 1e3]) or complex MIMO matrices through the default kernel of "
+                         "that order, --steps launches inside an NVTX range 'step'; prints the mean time")
     return ap.parse_args()
 
 
@@ -255,6 +262,39 @@ def measured_traffic(order, count):
             if hashlib.sha256(src.read()).hexdigest() != digest:
                 return None
     return rec["dram_bytes_per_matrix"] * count
+
+
+def host_link_ceiling(dev, A_h, X_h, A, X, reps=5):
+    """The host link alone: pinned cudaMemcpyAsync of the step's input (host to
+    device) and of its output (device to host), each direction alone and
+    both at once on two streams, timed with CUDA events (the copies of the
+    end-to-end step with no kernel).  Returns ms and GB/s."""
+    import torch
+    s1, s2 = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def run(h2d, d2h):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s1)
+        s2.wait_event(e0)
+        for _ in range(reps):
+            if h2d:
+                with torch.cuda.stream(s1):
+                    A.copy_(A_h, non_blocking=True)
+            if d2h:
+                with torch.cuda.stream(s2):
+                    X_h.copy_(X, non_blocking=True)
+        s1.wait_stream(s2)
+        e1.record(s1)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    run(True, True)
+    h, d, both = run(True, False), run(False, True), run(True, True)
+    nb_in, nb_out = A_h.numel() * A_h.element_size(), X_h.numel() * X_h.element_size()
+    return {"h2d_ms": h, "h2d_gbs": nb_in / h / 1e6, "d2h_ms": d, "d2h_gbs": nb_out / d / 1e6,
+            "both_directions_ms": both, "both_gbs": (nb_in + nb_out) / both / 1e6,
+            "bytes_in": nb_in, "bytes_out": nb_out, "reps": reps}
 
 
 def _event_ms(stream, fn, reps, flush=None):
@@ -708,6 +748,43 @@ def mmse_workload(dev, stream, steps):
             "steps": "A = H^* H + s2 I, the batched inverse (Sec. II + IV.A), W = X H^*"}
 
 
+def run_profile_case(args, local_rank):
+    """One order's default kernel on a uniform packed batch (profiling case)."""
+    import torch
+    from paper_1111_4144_gb300 import api, workloads as wl
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    tag, N, batch = args.profile_case.split(":")
+    N, batch = int(N), int(batch)
+    npd = {"f32": np.float32, "f64": np.float64, "c64": np.complex64, "c128": np.complex128}[tag]
+    base = 1024
+    if tag.startswith("c"):
+        b = wl.mimo_covariance(base, sizes=(N,), seed=1009, layout=wl.LAYOUT_PACKED, shuffle=False)
+    else:
+        b = wl.qr_spectrum(base, lambda rng, m: np.full(m, N),
+                           lambda rng, m, NN: 10.0 ** rng.uniform(0.0, 3.0, size=(m, NN)), 1009, wl.LAYOUT_PACKED)
+    A = torch.from_numpy(np.tile(b.A.astype(npd), (batch + base - 1) // base)[:batch * (N * (N + 1) // 2)]).to(dev)
+    X = torch.zeros_like(A)
+    info = torch.empty(batch, dtype=torch.int32, device=dev)
+    call = lambda: api.inv(A, max_n=N, layout=wl.LAYOUT_PACKED, X=X, info=info)
+    for _ in range(max(args.warmup, 1)):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("step")
+    e0.record()
+    for _ in range(args.steps):
+        call()
+    e1.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    es = np.dtype(npd).itemsize
+    print(json.dumps({"profile_case": args.profile_case, "ms": ms, "inverses_per_s": batch / (ms / 1e3),
+                      "alg_gbs": 2 * (N * (N + 1) // 2) * es * batch / (ms / 1e3) / 1e9,
+                      "info_nonzero": int(torch.count_nonzero(info).item())}), flush=True)
+
+
 def run_blocked(args, local_rank):
     """One large matrix through the blocked path (the large-order workload)."""
     import torch
@@ -727,7 +804,9 @@ def run_blocked(args, local_rank):
     A = A.contiguous()
     kw = {}
     if args.blocked_prec == "tf32":
-        kw = dict(prec=L.CHOL_PREC_TF32_REFINE, refine_steps=0)
+        kw = dict(prec=L.CHOL_PREC_TF32_REFINE, refine_steps=args.blocked_refine, flags=L.CHOL_FLAG_PIVOT64)
+    elif args.blocked_prec == "fp32":
+        kw = dict(prec=L.CHOL_PREC_FP32_REFINE, refine_steps=args.blocked_refine, flags=L.CHOL_FLAG_PIVOT64)
     X, info = api.inv(A, **kw)
     torch.cuda.synchronize()
     for _ in range(max(args.warmup - 1, 0)):
@@ -742,7 +821,8 @@ def run_blocked(args, local_rank):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"blocked_order": N, "prec": args.blocked_prec, "ms_per_inverse": ms,
+    print(json.dumps({"blocked_order": N, "prec": args.blocked_prec, "refine_steps": kw.get("refine_steps", 0),
+                      "ms_per_inverse": ms,
                       "alg_tflops": N ** 3 / (ms / 1e3) / 1e12, "info": int(info.item()),
                       "device_error": L.chol_last_device_error(None)}), flush=True)
 
@@ -914,6 +994,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_step()
         ms_e2e = timed(e2e_step, max(3, min(args.steps, 20)), "e2e")
     h2d = A_h.numel() * 8 + n_h.numel() * 4 + off_h.numel() * 8
+    link = host_link_ceiling(dev, A_h, X_h, A, X)
     d2h = X_h.numel() * 8 + info_h.numel() * 4
     # the other workloads last, so that nothing they leave allocated affects the legs above
     if rank == 0 and not args.no_extra:
@@ -950,6 +1031,8 @@ def run_ours(args, rank, world, local_rank):
                              "per_order_kernel_ms": {str(N): kern_ms[N] for N in orders}},
                 "gflops": alg_flops(b.n) / (ms / 1e3) / 1e9,
                 "e2e": {"value": job_value(world, b.batch, ms_e2e), "unit": METRIC, "h2d_bytes_per_step": h2d,
+                        "host_link": link,
+                        "frac_of_copy_only": link["both_directions_ms"] / ms_e2e if link else None,
                         "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
                 "gpu_launches": kernels_per_step * args.steps,
                 "clocks": clocks}
@@ -969,6 +1052,9 @@ def main():
         return
     if args.blocked:
         run_blocked(args, local_rank)
+        return
+    if args.profile_case:
+        run_profile_case(args, local_rank)
         return
     if world > 1:
         import torch

@@ -115,9 +115,10 @@ k_gemm(int M, int N, int K, Tacc alpha, const Tin* __restrict__ A, int64_t lda, 
 }
 
 // Refinement residual E = I - A X for n x n FP32 A (full) and X, each entry
-// a compensated FP32 dot product (f2acc: exact products, error-free sums,
-// about 48 bits) started at delta_ij, rounded to FP32 once at the end.  The
-// tiling is k_gemm's (128 x 128 tiles, 8 x 8 entries per thread).
+// a compensated FP32 dot product (exact products, error-free sums, about 48
+// bits) started at delta_ij, rounded to FP32 once at the end; two entries
+// of a row per paired FP32 instruction (f2acc2).  The tiling is k_gemm's
+// (128 x 128 tiles, 8 x 8 entries per thread).
 __global__ void __launch_bounds__(GB_THREADS)
 k_resid_f2(int n, const float* __restrict__ A, const float* __restrict__ X, float* E) {
     __shared__ float As[2][GB_K][GB_M + 4];
@@ -125,11 +126,16 @@ k_resid_f2(int n, const float* __restrict__ A, const float* __restrict__ X, floa
     const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
     const int t = threadIdx.x;
     const int tm = (t / 16) * 8, tn = (t % 16) * 8;
-    f2acc acc[8][8];
+    // acc[i][jj] holds entries (tm + i, tn + 2 jj) and (tm + i, tn + 2 jj + 1)
+    f2acc2 acc[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = f2_init(m0 + tm + i == n0 + tn + j ? 1.f : 0.f);
+        for (int jj = 0; jj < 4; ++jj) {
+            const int gi = m0 + tm + i, gj = n0 + tn + 2 * jj;
+            acc[i][jj].s = make_float2(gi == gj ? 1.f : 0.f, gi == gj + 1 ? 1.f : 0.f);
+            acc[i][jj].c = make_float2(0.f, 0.f);
+        }
     auto load = [&](int buf, int k0) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -149,15 +155,18 @@ k_resid_f2(int n, const float* __restrict__ A, const float* __restrict__ X, floa
         if (k0 + GB_K < n) load(buf ^ 1, k0 + GB_K);
 #pragma unroll
         for (int kk = 0; kk < GB_K; ++kk) {
-            float a[8], b[8];
+            float2 a[8], b[4];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) a[i] = -As[buf][kk][tm + i];
+            for (int i = 0; i < 8; ++i) {
+                const float v = -As[buf][kk][tm + i];
+                a[i] = make_float2(v, v);
+            }
 #pragma unroll
-            for (int j = 0; j < 8; ++j) b[j] = Bs[buf][kk][tn + j];
+            for (int jj = 0; jj < 4; ++jj) b[jj] = make_float2(Bs[buf][kk][tn + 2 * jj], Bs[buf][kk][tn + 2 * jj + 1]);
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) f2_fma(acc[i][j], a[i], b[j]);
+                for (int jj = 0; jj < 4; ++jj) f2_fma2(acc[i][jj], a[i], b[jj]);
         }
         __syncthreads();
         buf ^= 1;
@@ -167,9 +176,10 @@ k_resid_f2(int n, const float* __restrict__ A, const float* __restrict__ X, floa
         const int gm = m0 + tm + i;
         if (gm >= n) continue;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int gn = n0 + tn + j;
-            if (gn < n) E[(int64_t)gm * n + gn] = f2_value(acc[i][j]);
+        for (int jj = 0; jj < 4; ++jj) {
+            const int gn = n0 + tn + 2 * jj;
+            if (gn < n) E[(int64_t)gm * n + gn] = __fadd_rn(acc[i][jj].s.x, acc[i][jj].c.x);
+            if (gn + 1 < n) E[(int64_t)gm * n + gn + 1] = __fadd_rn(acc[i][jj].s.y, acc[i][jj].c.y);
         }
     }
 }

@@ -151,6 +151,23 @@ CHOL_D void f2_fma(f2acc& r, float a, float b) {
 }
 CHOL_D float f2_value(const f2acc& r) { return __fadd_rn(r.s, r.c); }
 
+// The same on two independent dot products at once (paired FP32
+// instructions, sm_100 and later): lanes x and y of every float2.
+struct f2acc2 {
+    float2 s, c;
+};
+CHOL_D float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+// r += a b, lane by lane
+CHOL_D void f2_fma2(f2acc2& r, float2 a, float2 b) {
+    const float2 p = __fmul2_rn(a, b);
+    const float2 e = __ffma2_rn(a, b, neg2(p));
+    const float2 t = __fadd2_rn(r.s, p);
+    const float2 z = __fadd2_rn(t, neg2(r.s));
+    const float2 err = __fadd2_rn(__fadd2_rn(r.s, neg2(__fadd2_rn(t, neg2(z)))), __fadd2_rn(p, neg2(z)));
+    r.s = t;
+    r.c = __fadd2_rn(r.c, __fadd2_rn(err, e));
+}
+
 // ---------------------------------------------------------------------------
 // Index helpers.  Packed upper, row by row: row i holds columns i..n-1.
 // ---------------------------------------------------------------------------

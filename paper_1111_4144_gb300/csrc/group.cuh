@@ -56,22 +56,85 @@ struct GroupCfg {
         return w * (int)(sizeof(V) / 4);
     }
     static constexpr int COLW = colw();
-    static constexpr size_t SMEM = (size_t)MPC * STRIDE + (size_t)MPC * (sizeof(int64_t) + sizeof(int)) +
-                                   (size_t)MPC * N * sizeof(typename traits<V>::real) + 2 * (size_t)TN + 16;
+    // the mbarrier of the bulk copies (8-byte aligned) after the other arrays
+    static constexpr size_t BAR_OFF = ((size_t)MPC * STRIDE + (size_t)MPC * (sizeof(int64_t) + sizeof(int)) +
+                                       (size_t)MPC * N * sizeof(typename traits<V>::real) + 2 * (size_t)TN + 7) / 8 * 8;
+    static constexpr size_t SMEM = BAR_OFF + 16;  // the mbarrier and its phase
 };
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (the untiled TMA form) of whole packed matrices
+// between global memory and the mirrors: one copy per matrix instead of one
+// cp.async per 16-byte unit.  Loads complete on an mbarrier whose wait is
+// bounded (about one second of %globaltimer); both ends of every copy are
+// 16-byte aligned and its size a multiple of 16 (the vectorised path only).
+// ---------------------------------------------------------------------------
+CHOL_D void mbar_init1(uint64_t* b) {
+    asm volatile("mbarrier.init.shared.b64 [%0], 1;" ::"r"(smem_u32(b)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+CHOL_D void mbar_arrive_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+CHOL_D bool mbar_done(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+CHOL_D uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// true once the phase with this parity has completed; false after ~1 s
+CHOL_D bool mbar_wait_bounded(uint64_t* b, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_done(b, parity))
+        if (global_ns() - t0 > 1000000000ull) return false;
+    return true;
+}
+CHOL_D void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+CHOL_D void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// the shared-memory source of this thread's bulk stores may be reused
+CHOL_D void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// order this thread's generic shared-memory accesses before later async-proxy ones
+CHOL_D void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Copy the chunk's matrices into the mirrors (cp.async, not waited on).
 // C supplies THREADS, TN, U (elements per 16-byte unit) and STRIDE.
+// bar (optional): the vectorised path copies each matrix's whole units with
+// one bulk copy completing on *bar (the caller waits on it); the remaining
+// elements, and every element without bar, by cp.async.
 template <typename V, int N, class C>
 CHOL_D void group_stage(const BatchParams& p, const V* A, unsigned char* mir, const int64_t* s_off,
-                        const uint8_t* s_i, const uint8_t* s_j, int m, bool vec) {
+                        const uint8_t* s_i, const uint8_t* s_j, int m, bool vec, uint64_t* bar = nullptr) {
     const int t = threadIdx.x;
     if (vec) {
         constexpr int FULL = C::TN / C::U;  // whole units per matrix
         constexpr int TAIL = C::TN - FULL * C::U;
-        for (int f = t; f < m * FULL; f += C::THREADS) {
-            const int q = f / FULL, u = f - q * FULL;
-            cp_async<16>(mir + (size_t)q * C::STRIDE + u * 16, A + s_off[q] + u * C::U);
+        if (bar != nullptr && FULL > 0) {
+            if (t == 0) mbar_arrive_tx(bar, (uint32_t)m * FULL * 16);
+            if (t < m) bulk_g2s(mir + (size_t)t * C::STRIDE, A + s_off[t], FULL * 16, bar);
+        } else {
+            for (int f = t; f < m * FULL; f += C::THREADS) {
+                const int q = f / FULL, u = f - q * FULL;
+                cp_async<16>(mir + (size_t)q * C::STRIDE + u * 16, A + s_off[q] + u * C::U);
+            }
         }
         if constexpr (TAIL > 0) {
             for (int f = t; f < m * TAIL; f += C::THREADS) {
@@ -92,15 +155,33 @@ CHOL_D void group_stage(const BatchParams& p, const V* A, unsigned char* mir, co
 
 // Store the mirrors (X, or R when factoring) to global memory.  GATE:
 // matrices marked kInfoRedo are skipped (CHOL_FLAG_PIVOT64_AUTO).
+// bulk (optional): the vectorised path stores each matrix's whole units
+// with one bulk copy (a failed matrix's mirror is first filled with NaN);
+// the caller has synchronised the CTA after the mirror's last write.
 template <typename V, int N, class C, bool GATE = false>
-CHOL_D void group_store(const BatchParams& p, V* out, const unsigned char* mir, const int64_t* s_off,
+CHOL_D void group_store(const BatchParams& p, V* out, unsigned char* mir, const int64_t* s_off,
                         const int* s_info, const uint8_t* s_i, const uint8_t* s_j, int m, bool vec, bool is_factor,
-                        bool fill_lower) {
+                        bool fill_lower, bool bulk = false) {
     const int t = threadIdx.x;
     if (vec) {
         constexpr int FULL = C::TN / C::U;
         constexpr int TAIL = C::TN - FULL * C::U;
-        for (int f = t; f < m * FULL; f += C::THREADS) {
+        if (bulk && FULL > 0) {
+            const bool skip = t >= m || (GATE && s_info[t] == kInfoRedo);
+            if (!skip && s_info[t] != 0) {
+                uint4 qn;
+#pragma unroll
+                for (int r = 0; r < C::U; ++r) reinterpret_cast<V*>(&qn)[r] = nan_v<V>();
+                for (int u = 0; u < FULL; ++u) *reinterpret_cast<uint4*>(mir + (size_t)t * C::STRIDE + u * 16) = qn;
+            }
+            fence_async_smem();
+            __syncthreads();
+            if (!skip) {
+                bulk_s2g(out + s_off[t], mir + (size_t)t * C::STRIDE, FULL * 16);
+                bulk_wait_read();
+            }
+        }
+        for (int f = t; f < ((bulk && FULL > 0) ? 0 : m * FULL); f += C::THREADS) {
             const int q = f / FULL, u = f - q * FULL;
             if constexpr (GATE)
                 if (s_info[q] == kInfoRedo) continue;  // left to the FP64-pivot pass
@@ -229,12 +310,19 @@ k_group(BatchParams p) {
     R* s_dinv = reinterpret_cast<R*>(s_info + MPC);                              // [MPC][N] (MINB > 1)
     uint8_t* s_i = reinterpret_cast<uint8_t*>(s_dinv + MPC * N);                 // [TN]
     uint8_t* s_j = s_i + TN;
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem_raw + C::BAR_OFF);  // bulk copies of the vectorised path
 
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int h = t & (G - 1);           // position in the group
     const int q = t / G;                 // matrix within the chunk
     const int gbase = lane & ~(G - 1);   // first lane of this group
+    // the phase of s_bar to wait for lives beside it (kept out of registers)
+    uint32_t* s_phase = reinterpret_cast<uint32_t*>(s_bar + 1);
+    if (t == 0) {
+        mbar_init1(s_bar);
+        *s_phase = 0;
+    }
     for (int e = t; e < TN; e += THREADS) {
         int i = 0;
         while (pidx(N, i + 1, i + 1) <= e && i + 1 < N) ++i;
@@ -259,9 +347,19 @@ k_group(BatchParams p) {
             ok = (o % C::U) == 0;
         }
         const bool vec = (__syncthreads_and(ok) != 0) && p.layout == 1 && p.aligned16;
-        group_stage<V, N, C>(p, A, mirs, s_off, s_i, s_j, m, vec);
+        group_stage<V, N, C>(p, A, mirs, s_off, s_i, s_j, m, vec, s_bar);
         cp_async_wait<0>();
-        __syncthreads();
+        bool late = false;
+        const bool bulk_in = vec && C::TN / C::U > 0;
+        if (bulk_in) late = !mbar_wait_bounded(s_bar, *s_phase);
+        if (__syncthreads_or(late)) {
+            // a bulk copy did not arrive within the bound: report, wait once
+            // more (bounded) for the copies in flight, and stop
+            if (t == 0) report_error(p.err, CHOL_ERR_TIMEOUT);
+            mbar_wait_bounded(s_bar, *s_phase);
+            return;
+        }
+        if (bulk_in && t == 0) *s_phase ^= 1u;  // read again only after later barriers
 
         if constexpr (ALG == 1 || ALG == 3) {
         // A complex product a b splits over the parts of a:
@@ -397,7 +495,7 @@ k_group(BatchParams p) {
         if (live && h == 0) s_info[q] = redo ? kInfoRedo : info;
         if (store_R || !p.want_inv) {
             __syncthreads();
-            group_store<V, N, C, GATE>(p, Ro, mirs, s_off, s_info, s_i, s_j, m, vec, true, false);
+            group_store<V, N, C, GATE>(p, Ro, mirs, s_off, s_info, s_i, s_j, m, vec, true, false, true);
             __syncthreads();
         }
         if (p.want_inv) {
@@ -510,7 +608,8 @@ k_group(BatchParams p) {
                 row_sync<ALG>();
             }
             __syncthreads();
-            group_store<V, N, C, GATE>(p, Xo, mirs, s_off, s_info, s_i, s_j, m, vec, false, p.fill_lower != 0);
+            group_store<V, N, C, GATE>(p, Xo, mirs, s_off, s_info, s_i, s_j, m, vec, false, p.fill_lower != 0,
+                                        true);
         }
         } else {
         const bool live = q < m;
@@ -639,6 +738,7 @@ k_group(BatchParams p) {
         }
         if (p.info)
             for (int k = t; k < m; k += THREADS) p.info[member_index(p, N, chunk * MPC + k)] = s_info[k];
+        fence_async_smem();  // the next chunk's bulk copies overwrite the mirrors
         __syncthreads();
     }
 }

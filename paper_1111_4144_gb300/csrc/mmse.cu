@@ -23,6 +23,19 @@ CHOL_HD size_t mmse_warp_elems(int max_n, int max_m) {
     return (size_t)max_m * max_n + (size_t)max_n * (max_n + 1);
 }
 
+// Row and column (i <= j) of element e of an order-n packed upper triangle:
+// i from the closed form of pidx's inverse, corrected by one step either way
+// against rounding.
+CHOL_D void tri_rc(int n, int e, int& i, int& j) {
+    const float b = 2.0f * n + 1.0f;
+    int r = (int)((b - sqrtf(b * b - 8.0f * (float)e)) * 0.5f);
+    r = max(0, min(r, n - 1));
+    if (pidx(n, r, r) > e) --r;
+    else if (r + 1 < n && pidx(n, r + 1, r + 1) <= e) ++r;
+    i = r;
+    j = e - pidx(n, r, r) + r;
+}
+
 // Order and rows of matrix b, and its offsets in H, W and the packed A / X.
 CHOL_D void mmse_geom(const MmseParams& p, int64_t b, int& n, int& m, int64_t& oh, int64_t& ow, int64_t& oa) {
     n = p.n ? p.n[b] : p.max_n;
@@ -49,9 +62,8 @@ __global__ void k_gram(MmseParams p, typename traits<V>::real s2) {
         __syncwarp();
         const int T = tri(n);
         for (int e = lane; e < T; e += 32) {
-            int i = 0;
-            while (pidx(n, i + 1, i + 1) <= e && i + 1 < n) ++i;
-            const int j = e - pidx(n, i, i) + i;
+            int i, j;
+            tri_rc(n, e, i, j);
             // a_ij = sum_r conj(h_ri) h_rj (+ s2 on the diagonal)
             V acc = zero_v<V>();
             for (int r = 0; r < m; ++r) acc = fma_v(conj_v(Hs[r * n + i]), Hs[r * n + j], acc);
@@ -81,9 +93,8 @@ __global__ void k_apply(MmseParams p) {
         const int LD = n + 1;
         const int T = tri(n);
         for (int e = lane; e < T; e += 32) {
-            int i = 0;
-            while (pidx(n, i + 1, i + 1) <= e && i + 1 < n) ++i;
-            const int j = e - pidx(n, i, i) + i;
+            int i, j;
+            tri_rc(n, e, i, j);
             const V x = X[oa + e];
             Xs[i * LD + j] = x;
             Xs[j * LD + i] = conj_v(x);

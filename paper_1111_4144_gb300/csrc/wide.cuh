@@ -91,10 +91,17 @@ __global__ void __launch_bounds__(128, MINB) k_wide(BatchParams p) {
     float* s_dinv = reinterpret_cast<float*>(s_info + MPC);                            // [MPC][N]
     uint8_t* s_i = reinterpret_cast<uint8_t*>(s_dinv + MPC * N);                       // [TN]
     uint8_t* s_j = s_i + TN;
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem_raw + C::BAR_OFF);  // bulk copies of the vectorised path
 
     const int t = threadIdx.x;
     const int h = t & 31;
     const int q = t >> 5;
+    // the phase of s_bar to wait for lives beside it (kept out of registers)
+    uint32_t* s_phase = reinterpret_cast<uint32_t*>(s_bar + 1);
+    if (t == 0) {
+        mbar_init1(s_bar);
+        *s_phase = 0;
+    }
     for (int e = t; e < TN; e += THREADS) {
         int i = 0;
         while (pidx(N, i + 1, i + 1) <= e && i + 1 < N) ++i;
@@ -120,9 +127,19 @@ __global__ void __launch_bounds__(128, MINB) k_wide(BatchParams p) {
             ok = (o % C::U) == 0;
         }
         const bool vec = (__syncthreads_and(ok) != 0) && p.layout == 1 && p.aligned16;
-        group_stage<float, N, C>(p, A, mirs, s_off, s_i, s_j, m, vec);
+        group_stage<float, N, C>(p, A, mirs, s_off, s_i, s_j, m, vec, s_bar);
         cp_async_wait<0>();
-        __syncthreads();
+        bool late = false;
+        const bool bulk_in = vec && C::TN / C::U > 0;
+        if (bulk_in) late = !mbar_wait_bounded(s_bar, *s_phase);
+        if (__syncthreads_or(late)) {
+            // a bulk copy did not arrive within the bound: report, wait once
+            // more (bounded) for the copies in flight, and stop
+            if (t == 0) report_error(p.err, CHOL_ERR_TIMEOUT);
+            mbar_wait_bounded(s_bar, *s_phase);
+            return;
+        }
+        if (bulk_in && t == 0) *s_phase ^= 1u;  // read again only after later barriers
 
         const bool live = q < m;
         float* M = reinterpret_cast<float*>(mirs + (size_t)(live ? q : 0) * C::STRIDE);
@@ -172,7 +189,7 @@ __global__ void __launch_bounds__(128, MINB) k_wide(BatchParams p) {
         if (live && h == 0) s_info[q] = redo ? kInfoRedo : info;
         if (store_R || !p.want_inv) {
             __syncthreads();
-            group_store<float, N, C, GATE>(p, Ro, mirs, s_off, s_info, s_i, s_j, m, vec, true, false);
+            group_store<float, N, C, GATE>(p, Ro, mirs, s_off, s_info, s_i, s_j, m, vec, true, false, true);
             __syncthreads();
         }
         if (p.want_inv) {
@@ -225,10 +242,12 @@ __global__ void __launch_bounds__(128, MINB) k_wide(BatchParams p) {
                 }
             });
             __syncthreads();
-            group_store<float, N, C, GATE>(p, Xo, mirs, s_off, s_info, s_i, s_j, m, vec, false, p.fill_lower != 0);
+            group_store<float, N, C, GATE>(p, Xo, mirs, s_off, s_info, s_i, s_j, m, vec, false, p.fill_lower != 0,
+                                        true);
         }
         if (p.info)
             for (int k = t; k < m; k += THREADS) p.info[member_index(p, N, chunk * MPC + k)] = s_info[k];
+        fence_async_smem();  // the next chunk's bulk copies overwrite the mirrors
         __syncthreads();
     }
 }
