@@ -304,7 +304,7 @@ chol_status_t chol_inv_batched_noalloc(chol_dtype_t dt, int32_t batch, const int
  *   refinement and flags as for chol_inv_batched (layout and fill_lower do
  *   not apply).  info as for chol_inv_batched; W of a failed matrix is NaN.
  *   ws: chol_workspace_bytes(CHOL_CALL_MMSE, dt, batch, max_n, n != NULL,
- *   opts) bytes, 256-byte aligned.  (max_m max_n + max_n (max_n + 1))
+ *   opts) bytes, 256-byte aligned.  ((max_m + 1) max_n + max_n (max_n + 1))
  *   elements must fit 96 KB (CHOL_ERR_UNSUPPORTED otherwise).
  */
 chol_status_t chol_mmse_batched(chol_dtype_t dt, int32_t batch, const int32_t* n, const int32_t* m,

@@ -686,7 +686,7 @@ chol_status_t chol_mmse_batched(chol_dtype_t dt, int32_t batch, const int32_t* n
     if (H == nullptr || W == nullptr) return CHOL_ERR_ARG;
     if ((o.flags & CHOL_FLAG_PIVOT64_AUTO) && info == nullptr) return CHOL_ERR_ARG;
     const size_t es = dt == CHOL_F32 ? 4 : dt == CHOL_C128 ? 16 : 8;
-    if (((size_t)max_m * max_n + (size_t)max_n * (max_n + 1)) * es > 98304) return CHOL_ERR_UNSUPPORTED;
+    if (((size_t)(max_m + 1) * max_n + (size_t)max_n * (max_n + 1)) * es > 98304) return CHOL_ERR_UNSUPPORTED;
     const size_t mats = mmse_ws_matrices(dt, batch, max_n);
     const size_t need = 2 * mats + ws_need_batched(batch, n != nullptr);
     if (ws == nullptr || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256 != 0) return CHOL_ERR_WORKSPACE;

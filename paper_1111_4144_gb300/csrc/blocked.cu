@@ -402,12 +402,15 @@ constexpr int kSB = 32;
 
 template <typename T>
 __global__ void __launch_bounds__(kDiagThreads)
-k_blk_potrf_blk(T* X, int64_t ldx, int k0, int b, T* Rinv, int* failed, int32_t* info) {
+k_blk_potrf_blk(T* X, int64_t ldx, int k0, int b, T* Rinv, int* failed, int32_t* info, int pivot64) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int NSB = (b + kSB - 1) / kSB;
     const int B = NSB * kSB;
     const int LD = B + 1;
-    T* S = reinterpret_cast<T*>(smem_raw);  // [B][LD] A, then R (upper)
+    // pivot64: ds[j] = a_jj - sum_k r_kj^2 over the block's finished rows k,
+    // in FP64 from exact products of the FP32 values (Eq. 3's in-block terms)
+    double* ds = reinterpret_cast<double*>(smem_raw);  // [B]
+    T* S = reinterpret_cast<T*>(ds + B);    // [B][LD] A, then R (upper)
     T* W = S + (size_t)B * LD;              // [B][LD] R^{-1} (upper); its lower blocks hold scratch
     T* dv = W + (size_t)B * LD;             // [B] 1 / r_ii
     __shared__ int s_bad;
@@ -420,6 +423,7 @@ k_blk_potrf_blk(T* X, int64_t ldx, int k0, int b, T* Rinv, int* failed, int32_t*
         else v = (i == j) ? T(1) : T(0);
         S[i * LD + j] = v;
         W[i * LD + j] = T(0);
+        if (i == j) ds[i] = (double)v;
     }
     if (t == 0) s_bad = 0;
     __syncthreads();
@@ -434,9 +438,21 @@ k_blk_potrf_blk(T* X, int64_t ldx, int k0, int b, T* Rinv, int* failed, int32_t*
 #pragma unroll
             for (int i = 0; i < kSB; ++i) {
                 const T tt = __shfl_sync(0xffffffffu, a[i], i);  // Eq. 3 argument (row i, column i)
-                if (!bad && !(tt > T(0) && isfinite(tt))) bad = o + i + 1;
                 T rii, inv;
-                pivot_root(tt, rii, inv);
+                if (pivot64) {
+                    // lane i: a[k], k < i, hold r_{o+k, o+i}
+                    double td = ds[o + lane];
+#pragma unroll
+                    for (int k = 0; k < kSB; ++k)
+                        if (k < i) td -= (double)a[k] * (double)a[k];
+                    td = __shfl_sync(0xffffffffu, td, i);
+                    if (!bad && !(td > 0.0 && isfinite(td))) bad = o + i + 1;
+                    rii = (T)sqrt(td);
+                    inv = (T)(1.0 / sqrt(td));
+                } else {
+                    if (!bad && !(tt > T(0) && isfinite(tt))) bad = o + i + 1;
+                    pivot_root(tt, rii, inv);
+                }
                 if (lane == i) a[i] = rii;
                 else if (lane > i) a[i] = a[i] * inv;  // r_ij, Eq. 4
                 if (lane == 0) dv[o + i] = inv;
@@ -490,6 +506,14 @@ k_blk_potrf_blk(T* X, int64_t ldx, int k0, int b, T* Rinv, int* failed, int32_t*
             for (int k = 0; k < kSB; ++k) S[(o + k) * LD + c] = a[k];
         }
         __syncthreads();
+        if (pivot64) {
+            // the sub-block's rows of R, column by column, off the later pivots' arguments
+            for (int j = o + kSB + t; j < B; j += blockDim.x) {
+                double d = ds[j];
+                for (int k = o; k < o + kSB; ++k) d -= (double)S[k * LD + j] * (double)S[k * LD + j];
+                ds[j] = d;
+            }
+        }
         // ---------------- trailing update of rows/columns past o + 32: 4 x 4 patches
         {
             const int r0 = o + kSB, n = B - r0;  // trailing order (a multiple of 32)
@@ -1019,7 +1043,7 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
     static std::once_flag once;
     static cudaError_t setup = cudaSuccess;
     const size_t potrf_smem = ((size_t)b * (b + 1) + 2 * (size_t)16 * DiagTile<T>::TC + 2 * (size_t)b) * sizeof(T);
-    const size_t potrf_blk_smem = (2 * (size_t)b * (b + 1) + (size_t)b) * sizeof(T);  // b: a multiple of 32
+    const size_t potrf_blk_smem = (2 * (size_t)b * (b + 1) + (size_t)b) * sizeof(T) + (size_t)b * sizeof(double);
     std::call_once(once, [&] {
         setup = cudaFuncSetAttribute(k_blk_potrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem);
         if constexpr (sizeof(T) == 4)
@@ -1047,10 +1071,11 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
         // FP32: the blocked diagonal factor; FP64 (whose 32-wide register
         // columns do not fit) and FP64 pivots: the row-by-row one
         bool blk = false;
-        if constexpr (sizeof(T) == 4) blk = !pivot64;
+        if constexpr (sizeof(T) == 4) blk = true;  // FP32: the sub-block factor, FP64 pivots in it on request
         if (blk) {
             if constexpr (sizeof(T) == 4)
-                k_blk_potrf_blk<T><<<1, kDiagThreads, potrf_blk_smem, st>>>(X, n, k0, bk, RinvK, failed, info);
+                k_blk_potrf_blk<T><<<1, kDiagThreads, potrf_blk_smem, st>>>(X, n, k0, bk, RinvK, failed, info,
+                                                                            pivot64);
         } else {
             k_blk_potrf<T><<<1, kDiagThreads, potrf_smem, st>>>(X, n, n, k0, bk, RinvK, failed, info, pivot64);
         }

@@ -18,9 +18,10 @@
 
 namespace cholinv {
 
+// shared memory of one warp: H (k_gram) or H^T with rows of m + 1 (k_apply), and X
 template <typename V>
 CHOL_HD size_t mmse_warp_elems(int max_n, int max_m) {
-    return (size_t)max_m * max_n + (size_t)max_n * (max_n + 1);
+    return (size_t)(max_m + 1) * max_n + (size_t)max_n * (max_n + 1);
 }
 
 // Row and column (i <= j) of element e of an order-n packed upper triangle:
@@ -78,8 +79,8 @@ template <typename V>
 __global__ void k_apply(MmseParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-    V* Hs = reinterpret_cast<V*>(smem_raw) + (size_t)w * mmse_warp_elems<V>(p.max_n, p.max_m);
-    V* Xs = Hs + (size_t)p.max_m * p.max_n;
+    V* Ht = reinterpret_cast<V*>(smem_raw) + (size_t)w * mmse_warp_elems<V>(p.max_n, p.max_m);  // H^T
+    V* Xs = Ht + (size_t)(p.max_m + 1) * p.max_n;
     const V* H = static_cast<const V*>(p.H);
     const V* X = static_cast<const V*>(p.X);
     V* W = static_cast<V*>(p.W);
@@ -89,7 +90,11 @@ __global__ void k_apply(MmseParams p) {
         mmse_geom(p, b, n, m, oh, ow, oa);
         if (n < 1 || n > p.max_n || m < 0 || m > p.max_m) continue;
         const bool bad = p.info && p.info[b] != 0;
-        for (int e = lane; e < m * n; e += 32) Hs[e] = H[oh + e];
+        // H transposed (row stride m + 1), so that lanes over k read consecutive words below
+        for (int e = lane; e < m * n; e += 32) {
+            const int r = e / n, c = e - r * n;
+            Ht[c * (m + 1) + r] = H[oh + e];
+        }
         const int LD = n + 1;
         const int T = tri(n);
         for (int e = lane; e < T; e += 32) {
@@ -104,7 +109,7 @@ __global__ void k_apply(MmseParams p) {
         for (int e = lane; e < n * m; e += 32) {
             const int i = e / m, k = e - i * m;
             V acc = zero_v<V>();
-            for (int j = 0; j < n; ++j) acc = fma_conjb(Xs[i * LD + j], Hs[k * n + j], acc);
+            for (int j = 0; j < n; ++j) acc = fma_conjb(Xs[i * LD + j], Ht[j * (m + 1) + k], acc);
             W[ow + e] = bad ? nan_v<V>() : acc;
         }
         __syncwarp();

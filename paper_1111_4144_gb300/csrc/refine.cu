@@ -135,6 +135,196 @@ __global__ void k_refine(BatchParams p, int steps, int automatic) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Register-tiled form for orders up to 32 (zero-padded to 32), compensated
+// FP32 residual: one warp per matrix; lane l holds the 4 x 8 block at rows
+// 4 (l / 4).., columns 8 (l % 4).. of E = I - A X (compensated pairs, two
+// entries or the two parts of a complex entry per paired FP32 instruction)
+// and then of the correction X E (plain FP32).  A, X and E are full 32 x 32
+// squares in shared memory (row stride 36); the left operands' 4-row slices
+// come from their conjugate-transposed rows (both are Hermitian).
+// ---------------------------------------------------------------------------
+constexpr int kRB = 32;
+constexpr int kRLD = kRB + 4;
+
+template <typename V>
+CHOL_HD size_t refine_tiled_warp_bytes() {
+    return (size_t)3 * kRB * kRLD * sizeof(V);
+}
+
+// acc += a b with a, b real (paired lanes: two entries of a row) or complex
+// (paired lanes: the real and imaginary parts of one entry)
+template <typename V>
+struct ResidTile;
+template <>
+struct ResidTile<float> {
+    f2acc2 acc[4][4];  // [row][column pair]
+    CHOL_D void init(int r0, int c0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int cp = 0; cp < 4; ++cp) {
+                const int i = r0 + r, j = c0 + 2 * cp;
+                acc[r][cp].s = make_float2(i == j ? 1.f : 0.f, i == j + 1 ? 1.f : 0.f);
+                acc[r][cp].c = make_float2(0.f, 0.f);
+            }
+    }
+    // acc[r][c] -= a_r b_c over one k
+    CHOL_D void step(const float (&a)[4], const float (&b)[8]) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int cp = 0; cp < 4; ++cp)
+                f2_fma2(acc[r][cp], make_float2(-a[r], -a[r]), make_float2(b[2 * cp], b[2 * cp + 1]));
+    }
+    CHOL_D float value(int r, int c) const {
+        const f2acc2& q = acc[r][c / 2];
+        return (c & 1) ? __fadd_rn(q.s.y, q.c.y) : __fadd_rn(q.s.x, q.c.x);
+    }
+};
+template <>
+struct ResidTile<cpx<float>> {
+    f2acc2 acc[4][8];  // lanes x, y: real and imaginary parts
+    CHOL_D void init(int r0, int c0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                acc[r][c].s = make_float2(r0 + r == c0 + c ? 1.f : 0.f, 0.f);
+                acc[r][c].c = make_float2(0.f, 0.f);
+            }
+    }
+    // (a b).re = a.re b.re - a.im b.im, (a b).im = a.re b.im + a.im b.re; subtracted
+    CHOL_D void step(const cpx<float> (&a)[4], const cpx<float> (&b)[8]) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                f2_fma2(acc[r][c], make_float2(-a[r].re, -a[r].re), make_float2(b[c].re, b[c].im));
+                f2_fma2(acc[r][c], make_float2(a[r].im, -a[r].im), make_float2(b[c].im, b[c].re));
+            }
+    }
+    CHOL_D cpx<float> value(int r, int c) const {
+        const f2acc2& q = acc[r][c];
+        return {__fadd_rn(q.s.x, q.c.x), __fadd_rn(q.s.y, q.c.y)};
+    }
+};
+
+template <typename V>
+__global__ void __launch_bounds__(128) k_refine_tiled(BatchParams p, int steps, int automatic) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int N = p.max_n;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    V* As = reinterpret_cast<V*>(smem_raw + (size_t)w * refine_tiled_warp_bytes<V>());
+    V* Xs = As + kRB * kRLD;
+    V* Es = Xs + kRB * kRLD;
+    const V* A = static_cast<const V*>(p.A);
+    V* X = static_cast<V*>(p.X);
+    const int r0 = (lane / 4) * 4, c0 = (lane % 4) * 8;
+
+    for (int b = blockIdx.x * wpc + w; b < p.batch; b += gridDim.x * wpc) {
+        const int n = p.n ? p.n[b] : N;
+        if (n <= 0 || n > N) continue;
+        if (p.info && p.info[b] != 0) continue;
+        const int64_t o = p.off ? p.off[b] : (int64_t)b * (p.layout ? tri64(N) : (int64_t)N * N);
+        auto gidx = [&](int i, int j) { return p.layout ? (int64_t)pidx(n, i, j) : (int64_t)i * n + j; };
+        for (int e = lane; e < kRB * kRLD; e += 32) {
+            As[e] = zero_v<V>();
+            Xs[e] = zero_v<V>();
+        }
+        __syncwarp();
+        for (int i = 0; i < n; ++i)
+            for (int j = i + lane; j < n; j += 32) {
+                V a = A[o + gidx(i, j)];
+                if (i == j) a = from_real<V>(re_of(a));
+                As[i * kRLD + j] = a;
+                As[j * kRLD + i] = conj_v(a);
+            }
+        int todo = steps;
+        for (int s = 0; s <= todo; ++s) {
+            // the current X, in full
+            __syncwarp();
+            for (int i = 0; i < n; ++i)
+                for (int j = i + lane; j < n; j += 32) {
+                    V x = X[o + gidx(i, j)];
+                    if (i == j) x = from_real<V>(re_of(x));
+                    Xs[i * kRLD + j] = x;
+                    Xs[j * kRLD + i] = conj_v(x);
+                }
+            __syncwarp();
+            if (s == 0 && automatic) {
+                double g = 0.0;
+                for (int i = lane; i < n; i += 32)
+                    g = fmax(g, (double)re_of(As[i * kRLD + i]) * (double)re_of(Xs[i * kRLD + i]));
+                for (int d = 16; d > 0; d >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, d));
+                todo = g > kAutoRefineGamma ? 1 : 0;
+            }
+            if (s == todo) break;
+            // E = I - A X (rows of A from its conjugate: A Hermitian)
+            ResidTile<V> et;
+            et.init(r0, c0);
+#pragma unroll 2
+            for (int k = 0; k < kRB; ++k) {
+                V a[4], bb[8];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) a[r] = conj_v(As[k * kRLD + r0 + r]);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) bb[c] = Xs[k * kRLD + c0 + c];
+                et.step(a, bb);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) Es[(r0 + r) * kRLD + c0 + c] = et.value(r, c);
+            __syncwarp();
+            // X + X E, upper half written back
+            V acc[4][8];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[r][c] = Xs[(r0 + r) * kRLD + c0 + c];
+#pragma unroll 4
+            for (int k = 0; k < kRB; ++k) {
+                V a[4], bb[8];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) a[r] = conj_v(Xs[k * kRLD + r0 + r]);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) bb[c] = Es[k * kRLD + c0 + c];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) acc[r][c] = fma_v(a[r], bb[c], acc[r][c]);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int i = r0 + r, j = c0 + c;
+                    if (i <= j && j < n) X[o + gidx(i, j)] = (i == j) ? from_real<V>(re_of(acc[r][c])) : acc[r][c];
+                }
+        }
+        __syncwarp();
+    }
+}
+
+template <typename V>
+static cudaError_t launch_refine_tiled(const BatchParams& p, int steps, int automatic, cudaStream_t s, bool dry) {
+    static std::once_flag once;
+    static cudaError_t setup = cudaSuccess;
+    constexpr int warps = 4;
+    const size_t smem = refine_tiled_warp_bytes<V>() * warps;
+    std::call_once(once, [&] {
+        setup = cudaFuncSetAttribute(k_refine_tiled<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (setup != cudaSuccess || dry) return setup;
+    int per_sm = 1;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine_tiled<V>, 32 * warps, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min((p.batch + warps - 1) / warps, device_info().sms * std::max(per_sm, 1)));
+    k_refine_tiled<V><<<grid, 32 * warps, smem, s>>>(p, steps, automatic);
+    return cudaGetLastError();
+}
+
 template <typename V, bool R64>
 static cudaError_t launch_refine_r(const BatchParams& p, int steps, int automatic, cudaStream_t s, bool dry) {
     auto kern = k_refine<V, R64>;
@@ -157,6 +347,7 @@ static cudaError_t launch_refine_r(const BatchParams& p, int steps, int automati
 template <typename V>
 static cudaError_t launch_refine_t(const BatchParams& p, int steps, int automatic, cudaStream_t s, bool dry) {
     if (p.flags & CHOL_FLAG_RESIDUAL_FP64) return launch_refine_r<V, true>(p, steps, automatic, s, dry);
+    if (p.max_n <= kRB) return launch_refine_tiled<V>(p, steps, automatic, s, dry);
     return launch_refine_r<V, false>(p, steps, automatic, s, dry);
 }
 
