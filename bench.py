@@ -420,6 +420,16 @@ def extra_workloads(dev, stream, steps):
             nb = cnt * 2 * (N * (N + 1) // 2) * 4
             buckets[str(N)] = {"matrices": cnt, "kernel_ms": kms[N], "gbs": nb / (kms[N] / 1e3) / 1e9,
                                "frac": nb / (kms[N] / 1e3) / 1e9 / hbm}
+        # the same batch in one persistent launch (CHOL_FLAG_SINGLE_LAUNCH), for comparison
+        X1 = torch.zeros_like(A)
+        plan1 = api.Plan(A, X1, n, off, 64, flags=L.CHOL_FLAG_SINGLE_LAUNCH)
+        for _ in range(3):
+            plan1.launch(stream)
+        ms_single = _event_ms(stream, lambda: plan1.launch(stream), reps)
+        torch.cuda.synchronize()
+        plan1.close()
+        single_same = bool(torch.isfinite(X1).all().item())
+        del X1
         idx = np.unique(np.random.default_rng(12).choice(b.batch, 1024, replace=False))
         sb, Xo, cpu_v, thr, _ = _oracle_sample(b, idx, "f32")
         Xg = X.cpu().numpy()
@@ -433,6 +443,9 @@ def extra_workloads(dev, stream, steps):
             "autotuned_variants": {str(k): v for k, v in tuned.items()},
             "whole_step": {"achieved_gbs": nbytes / (ms / 1e3) / 1e9, "frac": nbytes / (ms / 1e3) / 1e9 / hbm,
                            "algorithmic_bytes": nbytes},
+            "single_launch": {"ms_per_step": ms_single, "finite": single_same,
+                              "what": "CHOL_FLAG_SINGLE_LAUNCH: one persistent launch of the one-matrix-per-warp "
+                                      "form over every order, largest first (graph replay)"},
             "orders_2_32_frac": {"min": min(small), "median": float(np.median(small)), "max": max(small)},
             "per_order": buckets,
             "bytes_rule": "2 * N(N+1)/2 * 4 B per matrix (A upper read, X upper written)",

@@ -150,6 +150,15 @@ typedef enum {
                                      Operations" (Sec. III.B, Eqs. 16-19): M = R^{-1} from R m_i = e_i, then
                                      the upper half of X = M M^*.  One matrix per warp; not with
                                      CHOL_FLAG_LDL or CHOL_FLAG_METHOD_ES */
+#define CHOL_FLAG_SINGLE_LAUNCH 0x400 /* batched path: one persistent kernel for the whole batch instead of one
+                                     kernel per order.  Its warps take the matrices one at a time from a
+                                     device counter, largest orders first (after the bucketing of a batch
+                                     with per-matrix sizes), and run the one-matrix-per-warp form at each
+                                     matrix's own order, so an eager call launches no kernel for an order
+                                     that is absent.  The per-order kernels are faster where each order has
+                                     many matrices; this form is the comparison, and the choice for batches
+                                     spread thin over many orders.  Calls with this flag on a uniform batch
+                                     (n == NULL) share a per-device counter: serialise them */
 #define CHOL_FLAG_PLAN_ORDERS 0x10 /* chol_plan_inv_create only, batches with per-matrix sizes: read n once
                                      at creation (synchronously) and record kernels only for the orders
                                      present then, instead of one per order 1..max_n.  At every replay a

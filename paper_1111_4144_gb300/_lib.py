@@ -33,6 +33,7 @@ CHOL_FLAG_PIVOT64_AUTO = 0x40
 CHOL_FLAG_RESIDUAL_FP64 = 0x80
 CHOL_FLAG_METHOD_ES = 0x100
 CHOL_FLAG_METHOD_TMO = 0x200
+CHOL_FLAG_SINGLE_LAUNCH = 0x400
 CHOL_CALL_FACTOR, CHOL_CALL_INV, CHOL_CALL_BACKWARD, CHOL_CALL_INV_HOST, CHOL_CALL_MMSE = 0, 1, 2, 3, 4
 CHOL_BLK_TRAILING_UPDATE, CHOL_BLK_INVERSE_PRODUCT, CHOL_BLK_RESIDUAL, CHOL_BLK_CORRECTION, CHOL_BLK_WHOLE_CALL = \
     0, 1, 2, 3, 4

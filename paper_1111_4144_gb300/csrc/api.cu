@@ -15,6 +15,8 @@
 __device__ int g_chol_error_word;
 // Matrices redone with FP64 pivots under CHOL_FLAG_PIVOT64_AUTO (per device).
 __device__ unsigned long long g_chol_redo_count;
+// Work counter of a single-launch call on a uniform batch (per device).
+__device__ int g_chol_single_work;
 
 namespace cholinv {
 
@@ -28,6 +30,7 @@ struct DevState {
     int sms = 0;
     int* err = nullptr;
     unsigned long long* redo = nullptr;
+    int* work = nullptr;  // single-launch work counter of uniform batches
 };
 DevState g_dev[kMaxDevices];
 std::mutex g_dev_mu;
@@ -46,14 +49,18 @@ cudaError_t dev_state(DevState** out) {
         if (e != cudaSuccess) return e;
         e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.redo), g_chol_redo_count);
         if (e != cudaSuccess) return e;
+        e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.work), g_chol_single_work);
+        if (e != cudaSuccess) return e;
         s.init = true;
     }
     *out = &s;
     return cudaSuccess;
 }
 
-constexpr size_t kWsHeader = 1024;  // counts | starts | cursor (kClasses int32 each) | done, padded
-static_assert((3 * kClasses + 1) * sizeof(int32_t) <= kWsHeader, "bucketing header overlaps the permutation");
+// counts | starts | cursor (kClasses int32 each) | done | single-launch work counter, padded
+constexpr size_t kWsHeader = 1024;
+constexpr int kWsHeaderInts = 3 * kClasses + 2;
+static_assert(kWsHeaderInts * sizeof(int32_t) <= kWsHeader, "bucketing header overlaps the permutation");
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -82,7 +89,7 @@ chol_status_t check_common(chol_dtype_t dt, int32_t batch, int32_t max_n, const 
     if (o.prec < CHOL_PREC_NATIVE || o.prec > CHOL_PREC_BF16_REFINE) return CHOL_ERR_ARG;
     if (o.refine_steps < -1 || o.refine_steps > 2) return CHOL_ERR_ARG;
     if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER | CHOL_FLAG_LDL | CHOL_FLAG_PIVOT64_AUTO |
-                    CHOL_FLAG_RESIDUAL_FP64 | CHOL_FLAG_METHOD_ES | CHOL_FLAG_METHOD_TMO))
+                    CHOL_FLAG_RESIDUAL_FP64 | CHOL_FLAG_METHOD_ES | CHOL_FLAG_METHOD_TMO | CHOL_FLAG_SINGLE_LAUNCH))
         return CHOL_ERR_ARG;
     if ((o.flags & CHOL_FLAG_LDL) && (o.flags & (CHOL_FLAG_PIVOT64 | CHOL_FLAG_PIVOT64_AUTO)))
         return CHOL_ERR_UNSUPPORTED;
@@ -250,7 +257,7 @@ chol_status_t enqueue_batched(chol_dtype_t dt, BatchParams p, void* ws, cudaStre
         if (!dry) {
             // counts and the done counter (right after cursor) cleared together
             unsigned* done = reinterpret_cast<unsigned*>(cursor + kClasses);
-            if (cudaMemsetAsync(counts, 0, (3 * kClasses + 1) * sizeof(int32_t), s) != cudaSuccess)
+            if (cudaMemsetAsync(counts, 0, kWsHeaderInts * sizeof(int32_t), s) != cudaSuccess)
                 return CHOL_ERR_CUDA;
             const int threads = 256;
             const int grid = (int)std::min<int64_t>(((int64_t)p.batch + threads - 1) / threads, (int64_t)ds->sms * 8);
@@ -261,7 +268,18 @@ chol_status_t enqueue_batched(chol_dtype_t dt, BatchParams p, void* ws, cudaStre
             if (cudaGetLastError() != cudaSuccess) return CHOL_ERR_CUDA;
         }
     }
-    if (launch_dtype(dt, p, s, dry, present) != cudaSuccess) return CHOL_ERR_CUDA;
+    if (p.flags & CHOL_FLAG_SINGLE_LAUNCH) {
+        // one persistent launch over every order (its work counter follows the header's done word)
+        int* work = p.n != nullptr ? reinterpret_cast<int32_t*>(ws) + 3 * kClasses + 1 : nullptr;
+        if (work == nullptr) {
+            // uniform batch: no bucketing workspace; the counter lives in the device state
+            work = ds->work;
+            if (!dry && cudaMemsetAsync(work, 0, sizeof(int), s) != cudaSuccess) return CHOL_ERR_CUDA;
+        }
+        if (launch_single(dt, p, work, s, dry) != cudaSuccess) return CHOL_ERR_CUDA;
+    } else if (launch_dtype(dt, p, s, dry, present) != cudaSuccess) {
+        return CHOL_ERR_CUDA;
+    }
     // matrices whose FP32 pivots cancelled, again with FP64 pivots
     if ((p.flags & CHOL_FLAG_PIVOT64_AUTO) && !(p.flags & CHOL_FLAG_PIVOT64) && is_fp32(dt) &&
         launch_redo(dt, p, s, dry) != cudaSuccess)

@@ -46,6 +46,9 @@ struct BatchParams {
 // FP64.  t_i >= lambda_min(A) and a_ii <= lambda_max(A), so a matrix with
 // kappa_2(A) < 2^10 is never marked.
 constexpr int kInfoRedo = -2;
+
+// Size classes of the bucketing (orders 0..71).
+constexpr int kClasses = 72;
 template <typename R> CHOL_D bool pivot_cancels(R t, R aii) { return !(t >= aii * R(0.0009765625)); }
 
 // Arguments of the MMSE-filter kernels (mmse.cu): H_b is m_b x n_b
@@ -740,11 +743,36 @@ __global__ void k_redo(BatchParams p, int smax, int warps_per_cta) {
     }
 }
 
+// One launch for the whole batch (CHOL_FLAG_SINGLE_LAUNCH): persistent
+// warps take matrices one at a time from a device counter, largest orders
+// first (the bucketing permutation read from its end), and run the
+// one-matrix-per-warp body at each matrix's own order.  `smax` is the
+// largest order of the call (shared memory per warp); *work is zero on
+// entry.
+template <typename V>
+__global__ void k_warp_all(BatchParams p, int smax, int warps_per_cta, int* work) {
+    using R = typename traits<V>::real;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    V* S = reinterpret_cast<V*>(smem_raw) + (size_t)w * warp_elems(p, smax);
+    const bool pivot64 = (p.flags & CHOL_FLAG_PIVOT64) != 0;
+    const bool gate = sizeof(R) == 4 && (p.flags & CHOL_FLAG_PIVOT64_AUTO) && !pivot64;
+    const int64_t total = p.perm ? (int64_t)p.cls_start[kClasses - 1] + p.cls_count[kClasses - 1] : p.batch;
+    for (;;) {
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(work, 1);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= total) break;
+        const int64_t b = p.perm ? (int64_t)p.perm[total - 1 - idx] : idx;
+        const int N = p.n ? p.n[b] : p.max_n;
+        warp_one<V>(p, N, b, matrix_offset(p, N, b), S, lane, pivot64, gate);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Size-class bucketing for batches with per-matrix orders.
 // ws layout: counts[72] | starts[72] | cursor[72] | done | pad to 1024 B | perm[batch]
 // ---------------------------------------------------------------------------
-constexpr int kClasses = 72;
 
 // Orders allowed by a mask (bit c of m[c / 64]).
 CHOL_HD bool order_allowed(const uint64_t m0, const uint64_t m1, int c) {

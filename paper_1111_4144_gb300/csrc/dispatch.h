@@ -45,6 +45,10 @@ cudaError_t launch_redo(int dtype, const BatchParams& p, cudaStream_t s, bool dr
 // MMSE filters (mmse.cu): stage 0 forms A = H^* H + s2 I, stage 1 W = X H^*.
 cudaError_t launch_mmse(int dtype, int stage, const MmseParams& p, double s2, cudaStream_t s, bool dry);
 
+// The whole batch in one persistent launch of the warp body (refine.cu;
+// CHOL_FLAG_SINGLE_LAUNCH); *work must be zero.
+cudaError_t launch_single(int dtype, const BatchParams& p, int* work, cudaStream_t s, bool dry);
+
 // Adjoint dA = -X (G + G^H)/2 X (adjoint.cu).
 cudaError_t launch_backward(int dtype, const BwdParams& p, cudaStream_t s, bool dry);
 

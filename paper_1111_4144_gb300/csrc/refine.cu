@@ -369,6 +369,35 @@ static cudaError_t launch_redo_t(const BatchParams& p, cudaStream_t s, bool dry)
     return cudaGetLastError();
 }
 
+template <typename V>
+static cudaError_t launch_single_t(const BatchParams& p, int* work, cudaStream_t s, bool dry) {
+    static std::once_flag once;
+    static cudaError_t setup = cudaSuccess;
+    std::call_once(once, [&] {
+        setup = cudaFuncSetAttribute(k_warp_all<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
+    if (setup != cudaSuccess || dry) return setup;
+    const int smax = p.max_n;
+    const size_t per = warp_elems(p, smax) * sizeof(V);
+    const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, 98304 / per));
+    int per_sm = 1;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_warp_all<V>, 32 * warps, per * warps);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min((p.batch + warps - 1) / warps, device_info().sms * std::max(per_sm, 1)));
+    k_warp_all<V><<<grid, 32 * warps, per * warps, s>>>(p, smax, warps, work);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_single(int dtype, const BatchParams& p, int* work, cudaStream_t s, bool dry) {
+    switch (dtype) {
+        case CHOL_F32: return launch_single_t<float>(p, work, s, dry);
+        case CHOL_F64: return launch_single_t<double>(p, work, s, dry);
+        case CHOL_C64: return launch_single_t<cpx<float>>(p, work, s, dry);
+        case CHOL_C128: return launch_single_t<cpx<double>>(p, work, s, dry);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_redo(int dtype, const BatchParams& p, cudaStream_t s, bool dry) {
     if (dtype == CHOL_F32) return launch_redo_t<float>(p, s, dry);
     if (dtype == CHOL_C64) return launch_redo_t<cpx<float>>(p, s, dry);

@@ -66,7 +66,7 @@ FAKE = 0x100000  # a non-null pointer value; never dereferenced because validati
     (dict(layout=2), "ARG"),
     (dict(prec=7), "ARG"),
     (dict(refine=3), "ARG"),
-    (dict(flags=0x400), "ARG"),
+    (dict(flags=0x800), "ARG"),
     (dict(flags=0x300), "ARG"),              # two comparison methods at once
     (dict(flags=0x120), "UNSUPPORTED"),      # a comparison method in the LDL form
     (dict(flags=0x40), "ARG"),               # automatic FP64 pivots keep their redo list in info

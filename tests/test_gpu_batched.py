@@ -389,3 +389,23 @@ def test_equation_solving_equals_proposed_bits(tag):
     Xe, ie, _ = run_inv(b, tag, mixed=False, flags=L.CHOL_FLAG_METHOD_ES)
     assert np.all(ip == 0) and np.array_equal(ip, ie)
     assert np.array_equal(Xp, Xe)
+
+
+@pytest.mark.parametrize("tag,kind", [("f32", "uneven"), ("c64", "mimo"), ("f64", "uneven"), ("f32", "uniform")])
+def test_single_launch_matches_oracle(orc, tag, kind):
+    """CHOL_FLAG_SINGLE_LAUNCH: the whole batch in one persistent launch,
+    largest orders first, each matrix at its own order: eager and plan
+    replay against the oracle."""
+    from paper_1111_4144_gb300 import _lib as L
+    if kind == "uneven":
+        b = wl.uneven_loguniform(700, nmin=1, nmax=64, seed=2300, layout=0)
+    elif kind == "mimo":
+        b = wl.mimo_covariance(900, sizes=(4, 8, 16), seed=2301, layout=1)
+    else:
+        b = make_batch(tag, 37, 101, 1, seed=2302)
+    mixed = kind != "uniform"
+    _, Xo, info_o, A_wide = oracle_inv(orc, b, tag)
+    for plan in (False, True):
+        X, info, _ = run_inv(b, tag, mixed=mixed, plan=plan, flags=L.CHOL_FLAG_SINGLE_LAUNCH)
+        assert np.array_equal(info, info_o)
+        check_errors(tag, b, A_wide, upper_errors(b, X, Xo), f"X (single launch, plan={plan})")
