@@ -984,7 +984,8 @@ def run_ours(args, rank, world, local_rank):
         rl = upper_err_ratio(b, Xl.cpu().numpy(), Xo, kap, fp64=False)
         out["ldl_form"] = {"value": b.batch / (msl / 1e3), "unit": METRIC, "ms_per_step": msl,
                            "max_err_over_tol": rl[0], "max_rel_err": rl[1],
-                           "kernel": "one matrix per warp (the LDL form runs only there)"}
+                           "kernel": "the size-class kernels of the Cholesky form, built for the LDL form",
+                           "ratio_over_cholesky_ms": msl / ms}
         planl.close()
         del Xl
 

@@ -121,7 +121,9 @@ typedef enum {
 #define CHOL_FLAG_LDL 0x20         /* the LDL form (Sec. II.A, Eqs. 9-11; Sec. IV.B, Eqs. 25-29): A = R^* D R with R
                                      unit upper and D = diag(d_i), no square roots; X as for Cholesky.  R, when
                                      written, holds d_i on its diagonal (the unit diagonal is implied).  Batched
-                                     path only (orders <= 64; one matrix per warp); not with CHOL_FLAG_PIVOT64 */
+                                     path only (orders <= 64: up to 32 on the same thread-per-matrix and
+                                     group kernels as the Cholesky form, above on the one-matrix-per-warp
+                                     kernel); not with CHOL_FLAG_PIVOT64 */
 #define CHOL_FLAG_PIVOT64_AUTO 0x40 /* F32/C64 batched calls: FP64 pivots only for the matrices that need them.
                                      The FP32 pass watches Eq. 3 at every row i; a matrix whose argument
                                      t_i falls below 2^-10 a_ii (cancellation: about 10 of FP32's 24 bits

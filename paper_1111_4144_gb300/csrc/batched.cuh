@@ -114,7 +114,10 @@ CHOL_D int class_count(const BatchParams& p, int N) {
 // (Loops below run over fixed trip counts with compile-time guards: with
 // bounds that depend on an outer index the front end leaves a register array
 // in local memory.)
-template <typename V, int N, class Acc>
+// LDL: the LDL form of Sec. II.A (Eqs. 9-11) instead: R unit upper, d_i on
+// its diagonal, d_i = a_ii - sum_k d_k |r_ki|^2 and
+// r_ij = (a_ij - sum_k conj(r_ki) d_k r_kj) / d_i; dinv[i] = 1/d_i.
+template <typename V, int N, bool LDL = false, class Acc>
 CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 1], bool pivot64 = false,
                            bool gate = false) {
     using R = typename traits<V>::real;
@@ -122,14 +125,27 @@ CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 
     bool redo = false;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        V col[N > 0 ? N : 1];  // column i of R above the diagonal: r_ki, k < i
+        V col[N > 0 ? N : 1];  // column i of R above the diagonal: r_ki, k < i (LDL: d_k r_ki)
 #pragma unroll
         for (int k = 0; k < N; ++k)
             if (k < i) col[k] = m.at(pidx(N, k, i));
         // Eq. 3
         R t = re_of(m.at(pidx(N, i, i)));
         R rii, inv;
-        if (sizeof(R) == 4 && pivot64) {
+        if constexpr (LDL) {
+            // Eq. 10: d_i; column i scaled by d_k for Eq. 11
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                if (k < i) {
+                    const V w = scale_v(col[k], re_of(m.at(pidx(N, k, k))));
+                    t = fma_re_conjb(-w, col[k], t);
+                    col[k] = w;
+                }
+            }
+            if (info == 0 && !pivot_ok(t)) info = i + 1;
+            rii = t;
+            inv = R(1) / t;
+        } else if (sizeof(R) == 4 && pivot64) {
             double td = (double)t;
 #pragma unroll
             for (int k = 0; k < N; ++k)
@@ -168,8 +184,10 @@ CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 
 // registers, then replaced by row i of X.  Each stored x_km (i < k <= m) is
 // read once and feeds two sums: x_im (term k, r_ik x_km) and, when k < m,
 // x_ik (term m, r_im conj(x_km)).  For every target the terms still arrive
-// with k ascending, the order of the definition.
-template <typename V, int N, class Acc>
+// with k ascending, the order of the definition.  LDL: the form of Sec.
+// IV.B (Eqs. 25-29) over a unit upper R, x_ij = -sum r_ik x~_kj and
+// x_ii = 1/d_i - sum r_ik conj(x_ik).
+template <typename V, int N, bool LDL = false, class Acc>
 CHOL_D void inverse_unrolled(Acc& m, const typename traits<V>::real (&dinv)[N > 0 ? N : 1]) {
     using R = typename traits<V>::real;
 #pragma unroll
@@ -197,12 +215,12 @@ CHOL_D void inverse_unrolled(Acc& m, const typename traits<V>::real (&dinv)[N > 
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             if (j > i) {
-                V x = scale_v(acc[j], -inv);
+                V x = LDL ? -acc[j] : scale_v(acc[j], -inv);
                 m.at(pidx(N, i, j)) = x;
                 sd = fma_re_conjb(row[j], x, sd);
             }
         }
-        m.at(pidx(N, i, i)) = from_real<V>((inv - sd) * inv);
+        m.at(pidx(N, i, i)) = from_real<V>(LDL ? inv - sd : (inv - sd) * inv);
     }
 }
 
@@ -358,7 +376,8 @@ CHOL_D void lane_store(const BatchParams& p, V* out, uint4* buf, const int64_t* 
 // Lane kernel: one matrix per thread.
 // ---------------------------------------------------------------------------
 // GATE: CHOL_FLAG_PIVOT64_AUTO's cancellation test (FP32 value types only).
-template <typename V, int N, bool GATE = false>
+// LDL: the LDL form (CHOL_FLAG_LDL).
+template <typename V, int N, bool GATE = false, bool LDL = false>
 __global__ void __launch_bounds__(LaneCfg<V, N>::THREADS)
 k_lane(BatchParams p) {
     using C = LaneCfg<V, N>;
@@ -431,7 +450,7 @@ k_lane(BatchParams p) {
             int info = 0;
             R dinv[N];
             if (t < m) {
-                info = factor_unrolled<V, N>(r, dinv, p.flags & CHOL_FLAG_PIVOT64, gate);
+                info = factor_unrolled<V, N, LDL>(r, dinv, p.flags & CHOL_FLAG_PIVOT64, gate);
                 if (store_R && (!GATE || info != kInfoRedo)) {
 #pragma unroll
                     for (int e = 0; e < TN; ++e) {
@@ -445,7 +464,7 @@ k_lane(BatchParams p) {
                                 Ro[my_off + (int64_t)s_j[e] * N + s_i[e]] = info ? nan_v<V>() : zero_v<V>();
                     }
                 }
-                if (p.want_inv) inverse_unrolled<V, N>(r, dinv);
+                if (p.want_inv) inverse_unrolled<V, N, LDL>(r, dinv);
 #pragma unroll
                 for (int e = 0; e < TN; ++e) UnitRef<V, N>::at(buf, t, e) = r.a[e];
                 s_info[t] = info;
@@ -473,14 +492,14 @@ k_lane(BatchParams p) {
             int info = 0;
             R dinv[N];
             SmemMat<V, N> sm{buf, t};
-            if (t < m) info = factor_unrolled<V, N>(sm, dinv, p.flags & CHOL_FLAG_PIVOT64, gate);
+            if (t < m) info = factor_unrolled<V, N, LDL>(sm, dinv, p.flags & CHOL_FLAG_PIVOT64, gate);
             if (t < m) s_info[t] = info;
             if (store_R) {
                 __syncthreads();
                 lane_store<V, N, GATE>(p, Ro, buf, s_off, s_info, s_i, s_j, m, vec, true, false);
                 __syncthreads();
             }
-            if (p.want_inv && t < m) inverse_unrolled<V, N>(sm, dinv);
+            if (p.want_inv && t < m) inverse_unrolled<V, N, LDL>(sm, dinv);
             __syncthreads();
             lane_store<V, N, GATE>(p, p.want_inv ? Xo : Ro, buf, s_off, s_info, s_i, s_j, m, vec, !p.want_inv,
                              p.fill_lower != 0);

@@ -293,9 +293,10 @@ constexpr int group_size() {
 //        inverse every thread keeps its columns in full (the lower half
 //        mirrored in once per row), so the dot products run on registers.
 // GATE: CHOL_FLAG_PIVOT64_AUTO's cancellation test (FP32 value types only).
-template <typename V, int N, int G, int ALG, int W = 4, int MINB = 1, bool GATE = false>
+template <typename V, int N, int G, int ALG, int W = 4, int MINB = 1, bool GATE = false, bool LDL = false>
 __global__ void __launch_bounds__(GroupCfg<V, N, G, W>::THREADS, MINB)
 k_group(BatchParams p) {
+    static_assert(!LDL || ALG == 1, "the LDL form is built on the left-looking rows");
     using C = GroupCfg<V, N, G, W>;
     using R = typename traits<V>::real;
     constexpr int NC = C::NC;
@@ -407,6 +408,10 @@ k_group(BatchParams p) {
         int info = 0;
         bool redo = false;
         constexpr bool gate = GATE;
+        // LDL (Sec. II.A, Eqs. 9-11): d_k of the rows done, and R unit upper
+        // with d_i on its diagonal; the mirror's column i is scaled by d_k
+        // before it enters the sums of Eq. 11, whose j = i term is Eq. 10's d_i
+        R dd[LDL ? N : 1];
         // ---------------- factor, Eqs. 3-4, row by row
 #pragma unroll
         for (int i = 0; i < N; ++i) {
@@ -425,7 +430,8 @@ k_group(BatchParams p) {
 #pragma unroll
                 for (int k = 0; k < N; ++k) {
                     if (k < i) {
-                        const V a = M[row_base(N, k) + i];
+                        V a = M[row_base(N, k) + i];
+                        if constexpr (LDL) a = scale_v(a, dd[k]);
                         const float2 nar = make_float2(-a.re, -a.re), aim = make_float2(a.im, a.im);
 #pragma unroll
                         for (int c = 0; c < NC; ++c) {
@@ -443,8 +449,12 @@ k_group(BatchParams p) {
                         sv[c] = i == 0 ? col[c][i] : V{P[c].x - Q[c].y, P[c].y + Q[c].x};
             } else {
 #pragma unroll
-                for (int k = 0; k < N; ++k)
-                    if (k < i) ci[k] = M[row_base(N, k) + i];
+                for (int k = 0; k < N; ++k) {
+                    if (k < i) {
+                        ci[k] = M[row_base(N, k) + i];
+                        if constexpr (LDL) ci[k] = scale_v(ci[k], dd[k]);
+                    }
+                }
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
                     if (i <= c * G + G - 1) {
@@ -460,7 +470,12 @@ k_group(BatchParams p) {
             const R tc = re_of(sv[co]);
             const R tt = __shfl_sync(0xffffffffu, tc, gbase + ho);
             R rii, inv;
-            if (sizeof(R) == 4 && (p.flags & CHOL_FLAG_PIVOT64)) {
+            if constexpr (LDL) {
+                if (info == 0 && !pivot_ok(tt)) info = i + 1;
+                rii = tt;  // d_i
+                inv = R(1) / tt;
+                dd[i] = tt;
+            } else if (sizeof(R) == 4 && (p.flags & CHOL_FLAG_PIVOT64)) {
                 // Eq. 3 in FP64: a_ii (still in the mirror) minus |r_ki|^2 over column i
                 double td = (double)re_of(M[row_base(N, i) + i]);
 #pragma unroll
@@ -554,7 +569,7 @@ k_group(BatchParams p) {
                         if (c * G + G - 1 > i) {
                             const int j = c * G + h;
                             const V acc = i + 1 < N ? V{P[c].x - Q[c].y, P[c].y + Q[c].x} : zero_v<V>();
-                            xs[c] = scale_v(acc, -inv);
+                            xs[c] = LDL ? -acc : scale_v(acc, -inv);
                             if (j > i && j < N) sd = fma_re_conjb(col[c][i], xs[c], sd);
                         }
                     }
@@ -580,7 +595,7 @@ k_group(BatchParams p) {
                                 acc = fma_v(rr[k], xt, acc);
                             }
                         }
-                        xs[c] = scale_v(acc, -inv);
+                        xs[c] = LDL ? -acc : scale_v(acc, -inv);
                         // diagonal partial: r_ij conj(x_ij) over own columns
                         if (act) sd = fma_re_conjb(col[c][i], xs[c], sd);
                     }
@@ -599,7 +614,7 @@ k_group(BatchParams p) {
                 }
 #pragma unroll
                 for (int d = G / 2; d > 0; d >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, d);
-                const V xd = from_real<V>((inv - sd) * inv);
+                const V xd = from_real<V>(LDL ? inv - sd : (inv - sd) * inv);
                 const int co = i / G, ho = i % G;
                 if (h == ho) {
                     col[co][i] = xd;

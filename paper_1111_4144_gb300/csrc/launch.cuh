@@ -33,11 +33,11 @@ CHOL_HD bool gate_on(const BatchParams& p) {
 template <typename V>
 constexpr bool gate_built() { return sizeof(typename traits<V>::real) == 4; }
 
-template <typename V, int N, bool GATE>
+template <typename V, int N, bool GATE, bool LDL = false>
 static cudaError_t launch_lane_t(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
     constexpr int THREADS = LaneCfg<V, N>::THREADS;
     constexpr size_t SMEM = LaneCfg<V, N>::SMEM;
-    auto kern = k_lane<V, N, GATE>;
+    auto kern = k_lane<V, N, GATE, LDL>;
     static std::once_flag once;
     static int per_sm = 1;
     static cudaError_t setup_err = cudaSuccess;
@@ -86,10 +86,10 @@ static cudaError_t launch_warp(const BatchParams& p, int N, int upper_count, cud
 
 // W warps per CTA; MINB resident CTAs per SM requested from the register
 // allocator (MINB = 2 with W = 8 caps a thread at 128 registers).
-template <typename V, int N, int G, int ALG, int W = 4, int MINB = 1, bool GATE = false>
+template <typename V, int N, int G, int ALG, int W = 4, int MINB = 1, bool GATE = false, bool LDL = false>
 static cudaError_t launch_group(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
     using C = GroupCfg<V, N, G, W>;
-    auto kern = k_group<V, N, G, ALG, W, MINB, GATE>;
+    auto kern = k_group<V, N, G, ALG, W, MINB, GATE, LDL>;
     static std::once_flag once;
     static int per_sm = 1;
     static cudaError_t setup_err = cudaSuccess;
@@ -124,7 +124,14 @@ constexpr int num_variants() {
 template <typename V, int N>
 static cudaError_t launch_fixed(const BatchParams& p, int variant, int upper_count, cudaStream_t s, bool dry) {
     constexpr int kind = kernel_kind<V, N>();
-    // with the cancellation test (CHOL_FLAG_PIVOT64_AUTO) the default variant runs
+    // the LDL form (CHOL_FLAG_LDL) and the cancellation test
+    // (CHOL_FLAG_PIVOT64_AUTO) run the default variant, built for them
+    if (p.flags & CHOL_FLAG_LDL) {
+        if constexpr (kind == 0) return launch_lane_t<V, N, false, true>(p, upper_count, s, dry);
+        else if constexpr (kind == 1)
+            return launch_group<V, N, group_size<V, N>(), 1, 4, 1, false, true>(p, upper_count, s, dry);
+        else return launch_warp<V>(p, N, upper_count, s, dry);
+    }
     if constexpr (kind == 0) {
         if constexpr (num_variants<V, N>() > 1)
             if (variant == 1 && !gate_on<V>(p)) return launch_group<V, N, 2, 1>(p, upper_count, s, dry);
@@ -183,8 +190,8 @@ constexpr int kWideMinN = 33;
 // upper_count, in the variant the tuning table holds for it.
 template <typename V, int LO, int HI>
 cudaError_t launch_class_range(const BatchParams& p, int cls, int upper_count, cudaStream_t s, bool dry) {
-    // the LDL form and the comparison methods run on the warp kernel
-    if (p.flags & (CHOL_FLAG_LDL | CHOL_FLAG_METHOD_ES | CHOL_FLAG_METHOD_TMO))
+    // the comparison methods, and the LDL form above order 32, run on the warp kernel
+    if ((p.flags & (CHOL_FLAG_METHOD_ES | CHOL_FLAG_METHOD_TMO)) || ((p.flags & CHOL_FLAG_LDL) && cls > kGroupMaxN))
         return launch_warp<V>(p, cls, upper_count, s, dry);
     const int v = variant_of(dtype_code<V>(), cls);
     if constexpr (HI == kGroupMaxN) {

@@ -14,6 +14,11 @@ TAGS = ["f32", "f64", "c64", "c128"]
 def _batch(tag, kind):
     if kind == "mimo":
         b = wl.mimo_covariance(2000, sizes=(4, 8, 16), seed=2101, layout=1)
+    elif kind == "orders_1_32_packed":
+        # every order of the thread-per-matrix and group kernels, several
+        # chunks of the order-1 lane kernel's CTA
+        b = wl.uneven_loguniform(1500, nmin=1, nmax=32, seed=2103, layout=1)
+        assert set(b.n.tolist()) == set(range(1, 33))
     else:
         b = wl.uneven_loguniform(300, nmin=1, nmax=64, seed=2102, layout=0)
     if tag in ("f32", "f64") and np.iscomplexobj(b.A):
@@ -21,7 +26,7 @@ def _batch(tag, kind):
     return b
 
 
-@pytest.mark.parametrize("kind", ["mimo", "uneven"])
+@pytest.mark.parametrize("kind", ["mimo", "uneven", "orders_1_32_packed"])
 @pytest.mark.parametrize("tag", TAGS)
 def test_ldl_inverse_parity(orc, tag, kind):
     from paper_1111_4144_gb300 import _lib as L
