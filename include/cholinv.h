@@ -173,6 +173,15 @@ typedef struct {
     int32_t fill_lower;    /* dense layout: also write the strictly lower half of X */
     int32_t layout;        /* 0 dense row-major, 1 packed upper */
     int32_t flags;         /* CHOL_FLAG_* */
+    int32_t reserved;      /* must be 0 */
+    uint64_t orders;       /* batches with per-matrix sizes (n != NULL, max_n <= 64): the orders that may
+                              occur, bit c-1 for order c; 0 = any order 1..max_n.  A call launches a
+                              size-class kernel for each order of the set only (an eager call cannot
+                              read n on the host without synchronising, so without a set it launches one
+                              for every order 1..max_n, the absent ones exiting at once).  A matrix of an
+                              order outside the set gets info = -1 and the device error word
+                              CHOL_ERR_ARG, as an order outside 0..max_n.  Ignored for uniform batches
+                              and the blocked path */
 } chol_opts_t;
 
 /* Call identifiers for chol_workspace_bytes(). */

@@ -42,7 +42,7 @@ CHOL_NOALLOC_MAX_BATCH = 1048576
 
 class chol_opts_t(ctypes.Structure):
     _fields_ = [("prec", c_i32), ("refine_steps", c_i32), ("fill_lower", c_i32), ("layout", c_i32),
-                ("flags", c_i32)]
+                ("flags", c_i32), ("reserved", c_i32), ("orders", ctypes.c_uint64)]
 
 
 # name -> (restype, argtypes); mirrors include/cholinv.h
@@ -118,8 +118,21 @@ def check(status: int, what: str) -> None:
         raise CholError(status, what)
 
 
-def opts(prec=CHOL_PREC_NATIVE, refine_steps=0, fill_lower=0, layout=0, flags=0) -> chol_opts_t:
-    return chol_opts_t(int(prec), int(refine_steps), int(fill_lower), int(layout), int(flags))
+def order_set(orders) -> int:
+    """chol_opts_t.orders for an iterable of matrix orders (1..64); 0 for None."""
+    if orders is None:
+        return 0
+    m = 0
+    for c in orders:
+        c = int(c)
+        if not 1 <= c <= 64:
+            raise ValueError(f"order {c} outside 1..64")
+        m |= 1 << (c - 1)
+    return m
+
+
+def opts(prec=CHOL_PREC_NATIVE, refine_steps=0, fill_lower=0, layout=0, flags=0, orders=None) -> chol_opts_t:
+    return chol_opts_t(int(prec), int(refine_steps), int(fill_lower), int(layout), int(flags), 0, order_set(orders))
 
 
 # raw entry points, same names as the C ABI

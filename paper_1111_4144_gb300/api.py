@@ -93,10 +93,12 @@ def workspace(call, dt, batch, max_n, has_sizes, o, device):
 
 
 def inv(A, n=None, off=None, max_n=None, *, layout=LAYOUT_DENSE, prec=L.CHOL_PREC_NATIVE, refine_steps=0,
-        fill_lower=False, want_R=False, flags=0, X=None, R=None, info=None, stream=None):
+        fill_lower=False, want_R=False, flags=0, X=None, R=None, info=None, stream=None, orders=None):
     """Upper half of A^{-1} for every matrix of the batch (Sec. II + Sec. IV.A).
 
     Returns (X, info) or (X, info, R).  X has A's shape and layout.
+    orders: the orders n may hold (an iterable), when known; the call then
+    launches kernels for those orders only (chol_opts_t.orders).
     """
     _need_cuda(A, X, R, info)
     dt = dtype_code(A)
@@ -104,7 +106,7 @@ def inv(A, n=None, off=None, max_n=None, *, layout=LAYOUT_DENSE, prec=L.CHOL_PRE
     _like("X", X, A)
     _like("R", R, A)
     _per_matrix(info, off, batch)
-    o = L.opts(prec, refine_steps, int(fill_lower), layout, flags)
+    o = L.opts(prec, refine_steps, int(fill_lower), layout, flags, orders)
     if X is None:
         X = torch.zeros_like(A)
     if want_R and R is None:
@@ -157,7 +159,7 @@ class HostInv:
 
 
 def mmse(H, n=None, m=None, hoff=None, woff=None, max_n=None, max_m=None, *, sigma2=0.0,
-         prec=L.CHOL_PREC_NATIVE, refine_steps=0, flags=0, W=None, info=None, stream=None):
+         prec=L.CHOL_PREC_NATIVE, refine_steps=0, flags=0, W=None, info=None, stream=None, orders=None):
     """W = (H^* H + sigma2 I)^{-1} H^* for every channel matrix H (with
     sigma2 = 0 and H = D^* square, W^* = D^* (D D^*)^{-1} = D^{-1}, Sec. III.C).
 
@@ -181,7 +183,7 @@ def mmse(H, n=None, m=None, hoff=None, woff=None, max_n=None, max_m=None, *, sig
     _per_matrix(info, hoff, batch)
     if info is None:
         info = torch.empty(batch, dtype=torch.int32, device=H.device)
-    o = L.opts(prec, refine_steps, 0, LAYOUT_PACKED, flags)
+    o = L.opts(prec, refine_steps, 0, LAYOUT_PACKED, flags, orders)
     ws, nbytes = workspace(L.CHOL_CALL_MMSE, dt, batch, max_n, n is not None, o, H.device)
     st = L.chol_mmse_batched(dt, batch, _p(n), _p(m), _p(hoff), _p(woff), int(max_n), int(max_m), _p(H),
                              float(sigma2), _p(W), _p(info), o, _p(ws), nbytes, _s(stream))
@@ -189,14 +191,15 @@ def mmse(H, n=None, m=None, hoff=None, woff=None, max_n=None, max_m=None, *, sig
     return W, info
 
 
-def factor(A, n=None, off=None, max_n=None, *, layout=LAYOUT_DENSE, flags=0, R=None, info=None, stream=None):
+def factor(A, n=None, off=None, max_n=None, *, layout=LAYOUT_DENSE, flags=0, R=None, info=None, stream=None,
+           orders=None):
     """Cholesky factor R (Eqs. 3-4).  Returns (R, info)."""
     _need_cuda(A, R, info)
     dt = dtype_code(A)
     batch, max_n = _geometry(A, n, off, max_n, layout)
     _like("R", R, A)
     _per_matrix(info, off, batch)
-    o = L.opts(L.CHOL_PREC_NATIVE, 0, 0, layout, flags)
+    o = L.opts(L.CHOL_PREC_NATIVE, 0, 0, layout, flags, orders)
     if R is None:
         R = torch.zeros_like(A)
     if info is None:
@@ -289,9 +292,10 @@ class Plan:
 
     def __init__(self, A, X, n=None, off=None, max_n=None, *, R=None, info=None, layout=LAYOUT_DENSE,
                  prec=L.CHOL_PREC_NATIVE, refine_steps=0, fill_lower=False, flags=0, timing=False,
-                 fixed_orders=False):
+                 fixed_orders=False, orders=None):
         """timing: record per-order kernel timing (kernel_ms).  fixed_orders: record
-        kernels only for the orders n holds now (CHOL_FLAG_PLAN_ORDERS)."""
+        kernels only for the orders n holds now (CHOL_FLAG_PLAN_ORDERS).  orders:
+        the orders n may hold in any replay (chol_opts_t.orders)."""
         import ctypes
         if timing:
             flags |= L.CHOL_FLAG_PLAN_TIMING
@@ -303,7 +307,7 @@ class Plan:
         _like("X", X, A)
         _like("R", R, A)
         _per_matrix(info, off, batch)
-        o = L.opts(prec, refine_steps, int(fill_lower), layout, flags)
+        o = L.opts(prec, refine_steps, int(fill_lower), layout, flags, orders)
         self.info = info if info is not None else torch.empty(batch, dtype=torch.int32, device=A.device)
         self.ws, nbytes = workspace(L.CHOL_CALL_INV, dt, batch, max_n, n is not None, o, A.device)
         self._keep = (A, X, n, off, R, self.info, self.ws)

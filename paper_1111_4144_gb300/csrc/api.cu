@@ -76,6 +76,8 @@ chol_opts_t opts_or_default(const chol_opts_t* o) {
     d.fill_lower = 0;
     d.layout = 0;
     d.flags = 0;
+    d.reserved = 0;
+    d.orders = 0;
     return o ? *o : d;
 }
 
@@ -86,6 +88,7 @@ chol_status_t check_common(chol_dtype_t dt, int32_t batch, int32_t max_n, const 
     if (batch < 0) return CHOL_ERR_ARG;
     if (max_n < 1) return CHOL_ERR_ARG;
     if (o.layout != 0 && o.layout != 1) return CHOL_ERR_ARG;
+    if (o.reserved != 0) return CHOL_ERR_ARG;
     if (o.prec < CHOL_PREC_NATIVE || o.prec > CHOL_PREC_BF16_REFINE) return CHOL_ERR_ARG;
     if (o.refine_steps < -1 || o.refine_steps > 2) return CHOL_ERR_ARG;
     if (o.flags & ~(CHOL_FLAG_PIVOT64 | CHOL_FLAG_GRAD_UPPER | CHOL_FLAG_LDL | CHOL_FLAG_PIVOT64_AUTO |
@@ -241,6 +244,13 @@ cudaError_t launch_dtype(chol_dtype_t dt, const BatchParams& p, cudaStream_t s, 
 // Enqueue bucketing (if per-matrix sizes) and every class kernel.
 chol_status_t enqueue_batched(chol_dtype_t dt, BatchParams p, void* ws, cudaStream_t s, bool dry,
                               const uint8_t* present = nullptr) {
+    // a caller-stated order set: kernels for those orders only
+    uint8_t from_mask[kClasses];
+    if (present == nullptr && p.n != nullptr && (~p.order_mask[0] | ~p.order_mask[1]) != 0) {
+        for (int c = 0; c < kClasses; ++c)
+            from_mask[c] = c >= 1 && c <= p.max_n && order_allowed(p.order_mask[0], p.order_mask[1], c);
+        present = from_mask;
+    }
     DevState* ds = nullptr;
     if (dev_state(&ds) != cudaSuccess) return CHOL_ERR_CUDA;
     p.err = ds->err;
@@ -330,7 +340,12 @@ BatchParams make_params(int32_t batch, const int32_t* n, const int64_t* off, int
     p.X = X;
     p.info = info;
     p.flags = o.flags;
+    // the caller's order set (bit c-1 of o.orders for order c) as bit c of the mask
     p.order_mask[0] = p.order_mask[1] = ~0ull;
+    if (n != nullptr && o.orders != 0) {
+        p.order_mask[0] = o.orders << 1;
+        p.order_mask[1] = o.orders >> 63;
+    }
     p.aligned16 = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(R) | reinterpret_cast<uintptr_t>(X)) %
                    16) == 0;
     return p;
@@ -342,6 +357,7 @@ chol_status_t blocked_validate(chol_dtype_t dt, int32_t batch, const int32_t* n,
                                const chol_opts_t& o, size_t need, void* ws, size_t ws_bytes) {
     if (dt < CHOL_F32 || dt > CHOL_C128 || batch < 0) return CHOL_ERR_ARG;
     if (o.layout != 0 && o.layout != 1) return CHOL_ERR_ARG;
+    if (o.reserved != 0) return CHOL_ERR_ARG;
     if (o.prec < CHOL_PREC_NATIVE || o.prec > CHOL_PREC_BF16_REFINE) return CHOL_ERR_ARG;
     if (o.refine_steps < -1 || o.refine_steps > 2) return CHOL_ERR_ARG;
     if (o.flags & CHOL_FLAG_LDL) return CHOL_ERR_UNSUPPORTED;
@@ -836,9 +852,10 @@ chol_status_t chol_plan_inv_create(chol_plan_t** plan, chol_dtype_t dt, int32_t 
         std::vector<int32_t> nh((size_t)batch);
         if (cudaMemcpy(nh.data(), n, (size_t)batch * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
             return CHOL_ERR_CUDA;
+        const uint64_t stated[2] = {p.order_mask[0], p.order_mask[1]};
         p.order_mask[0] = p.order_mask[1] = 0;
         for (int32_t v : nh)
-            if (v > 0 && v <= max_n) {
+            if (v > 0 && v <= max_n && order_allowed(stated[0], stated[1], v)) {
                 present[v] = 1;
                 p.order_mask[v / 64] |= 1ull << (v % 64);
             }

@@ -87,6 +87,22 @@ def test_invalid_arguments_rejected_on_host(L, case, expect):
     assert st == getattr(L, "CHOL_ERR_" + expect)
 
 
+def test_opts_layout_and_order_set(L):
+    # chol_opts_t: five int32 fields, the reserved word, then the 64-bit order set
+    assert ctypes.sizeof(L.chol_opts_t) == 32
+    assert L.chol_opts_t.orders.offset == 24 and L.chol_opts_t.reserved.offset == 20
+    assert L.order_set(None) == 0
+    assert L.order_set((4, 8, 16)) == (1 << 3) | (1 << 7) | (1 << 15)
+    assert L.order_set([1, 64]) == 1 | (1 << 63)
+    for bad in ([0], [65], [-3]):
+        with pytest.raises(ValueError):
+            L.order_set(bad)
+    o = L.opts()
+    o.reserved = 1
+    st = L.chol_inv_batched(L.CHOL_F32, 10, None, None, 8, FAKE, None, FAKE, None, o, None, 0, None)
+    assert st == L.CHOL_ERR_ARG
+
+
 def test_factor_and_plan_argument_checks(L):
     o = L.opts()
     assert L.chol_factor_batched(L.CHOL_F64, 3, None, None, 4, FAKE, None, None, o, None, 0, None) == L.CHOL_ERR_ARG

@@ -409,3 +409,66 @@ def test_single_launch_matches_oracle(orc, tag, kind):
         X, info, _ = run_inv(b, tag, mixed=mixed, plan=plan, flags=L.CHOL_FLAG_SINGLE_LAUNCH)
         assert np.array_equal(info, info_o)
         check_errors(tag, b, A_wide, upper_errors(b, X, Xo), f"X (single launch, plan={plan})")
+
+
+def _class_kernel_launches(fn):
+    """Names of the size-class kernels (k_lane / k_group / k_wide / k_warp)
+    that fn() launched, from the CUDA activity of torch's profiler; None if
+    the profiler records no CUDA activity here."""
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+    torch.cuda.synchronize()
+    try:
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            fn()
+            torch.cuda.synchronize()
+        names = [e.name for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA]
+    except RuntimeError:
+        return None
+    if not names:
+        return None
+    return [s for s in names if any(k in s for k in ("k_lane", "k_group", "k_wide", "k_warp"))]
+
+
+def test_order_set_launches_only_stated_orders(orc):
+    """chol_opts_t.orders: an eager call on a batch of orders {4, 8, 16}
+    launches those three size-class kernels only, with results bit-identical
+    to the call without the set; a matrix of an order outside the set gets
+    info = -1 and the device error word CHOL_ERR_ARG."""
+    import torch
+    from paper_1111_4144_gb300 import _lib as L, api
+    b = wl.mimo_covariance(3000, sizes=(4, 8, 16), seed=2401, layout=1)
+    dev = torch.device("cuda", 0)
+    A = torch.from_numpy(b.A.astype(np.complex64)).to(dev)
+    n = torch.from_numpy(b.n).to(dev)
+    off = torch.from_numpy(b.off).to(dev)
+    api.last_device_error()  # clear
+    X0, i0 = api.inv(A, n, off, 16, layout=1)
+    X1, i1 = api.inv(A, n, off, 16, layout=1, orders=(4, 8, 16))
+    torch.cuda.synchronize()
+    assert torch.equal(i0, i1) and int(i1.abs().sum()) == 0
+    assert torch.equal(X0.view(torch.float32), X1.view(torch.float32))
+    assert api.last_device_error() == L.CHOL_OK
+    # the same through a plan (the set restricts every replay)
+    Xp = torch.zeros_like(A)
+    p = api.Plan(A, Xp, n, off, 16, layout=1, orders=(4, 8, 16))
+    p.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(X0.view(torch.float32), Xp.view(torch.float32))
+    p.close()
+    # launches: three class kernels with the set, one per order 1..16 without
+    stated = _class_kernel_launches(lambda: api.inv(A, n, off, 16, layout=1, orders=(4, 8, 16)))
+    every = _class_kernel_launches(lambda: api.inv(A, n, off, 16, layout=1))
+    if stated is not None:
+        assert len(stated) == 3, stated
+        assert len(every) == 16, every
+    # order 16 left out of the set: its matrices are rejected, the rest unchanged
+    X2, i2 = api.inv(A, n, off, 16, layout=1, orders=(4, 8))
+    torch.cuda.synchronize()
+    i2 = i2.cpu().numpy()
+    assert np.all(i2[b.n == 16] == -1) and np.all(i2[b.n != 16] == 0)
+    assert api.last_device_error() == L.CHOL_ERR_ARG
+    Xa, Xb = X0.cpu().numpy(), X2.cpu().numpy()
+    for k in np.flatnonzero(b.n != 16)[:200]:
+        o, T = int(b.off[k]), int(b.n[k]) * (int(b.n[k]) + 1) // 2
+        assert np.array_equal(Xa[o:o + T], Xb[o:o + T])
