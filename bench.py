@@ -762,13 +762,27 @@ def mmse_workload(dev, stream, steps):
 
 
 def run_profile_case(args, local_rank):
-    """One order's default kernel on a uniform packed batch (profiling case)."""
+    """One order's default kernel on a uniform packed batch (profiling case).
+
+    DTYPE:N:BATCH[:OPT...], OPT one of rK (FP32 + K refinement steps), ldl
+    (the LDL form), bwd (the timed region runs the adjoint of the inverse,
+    dA for G = I, instead)."""
     import torch
-    from paper_1111_4144_gb300 import api, workloads as wl
+    from paper_1111_4144_gb300 import _lib as L, api, workloads as wl
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    tag, N, batch = args.profile_case.split(":")
+    tag, N, batch, *opts = args.profile_case.split(":")
     N, batch = int(N), int(batch)
+    kw, bwd = {}, False
+    for o in opts:
+        if o.startswith("r") and o[1:].isdigit():
+            kw.update(prec=L.CHOL_PREC_FP32_REFINE, refine_steps=int(o[1:]))
+        elif o == "ldl":
+            kw["flags"] = kw.get("flags", 0) | L.CHOL_FLAG_LDL
+        elif o == "bwd":
+            bwd = True
+        else:
+            raise SystemExit(f"--profile-case: unknown option {o!r}")
     npd = {"f32": np.float32, "f64": np.float64, "c64": np.complex64, "c128": np.complex128}[tag]
     base = 1024
     if tag.startswith("c"):
@@ -779,7 +793,13 @@ def run_profile_case(args, local_rank):
     A = torch.from_numpy(np.tile(b.A.astype(npd), (batch + base - 1) // base)[:batch * (N * (N + 1) // 2)]).to(dev)
     X = torch.zeros_like(A)
     info = torch.empty(batch, dtype=torch.int32, device=dev)
-    call = lambda: api.inv(A, max_n=N, layout=wl.LAYOUT_PACKED, X=X, info=info)
+    call = lambda: api.inv(A, max_n=N, layout=wl.LAYOUT_PACKED, X=X, info=info, **kw)
+    if bwd:
+        call()
+        G = torch.zeros((batch, N, N), dtype=A.dtype, device=dev)
+        G[:, torch.arange(N), torch.arange(N)] = 1
+        dA = torch.empty_like(G)
+        call = lambda: api.backward(X, G, max_n=N, layout=wl.LAYOUT_PACKED, dA=dA)
     for _ in range(max(args.warmup, 1)):
         call()
     torch.cuda.synchronize()
