@@ -43,11 +43,18 @@
  *   Large orders.  max_n <= 64 runs the batched kernels (one matrix per
  *     thread, thread group or warp).  max_n > 64 runs the blocked path
  *     (factor and inverse by b x b blocks, products as tiled GEMMs): uniform
- *     batches only (n == NULL, off == NULL), dense layout, CHOL_F32 or
- *     CHOL_F64, one matrix after another.  There X is the working storage:
- *     its lower half is always written (the full Hermitian inverse), X may
- *     not alias A or R, and refine_steps = -1 means one step.  Other
- *     combinations return CHOL_ERR_UNSUPPORTED.
+ *     batches only (n == NULL, off == NULL), dense layout, one matrix after
+ *     another.  There X is the working storage: its lower half is always
+ *     written (the full Hermitian inverse), X may not alias A or R, and
+ *     refine_steps = -1 means one step.  Complex matrices (CHOL_C64,
+ *     CHOL_C128) run as their real symmetric embedding [[B, -C], [C, B]] of
+ *     order 2 max_n (A = B + iC; A^{-1} = P + iQ is read back from the
+ *     embedding's inverse [[P, -Q], [Q, P]]), in the precision of their real
+ *     part (CHOL_C64 as CHOL_F32, with the same precision modes): the inverse
+ *     only (R must be NULL; chol_factor_batched returns
+ *     CHOL_ERR_UNSUPPORTED), info being the embedding's failing row (in
+ *     1..2 max_n), and about twice the arithmetic of complex products.
+ *     Other combinations return CHOL_ERR_UNSUPPORTED.
  *   Layout (opts->layout).  0: dense row-major n*n; only the upper triangle
  *     (i <= j) of A is read (Sec. II: the lower part is never needed).
  *     1: upper triangle packed row by row (row i holds columns i..n-1),

@@ -365,11 +365,12 @@ chol_status_t blocked_validate(chol_dtype_t dt, int32_t batch, const int32_t* n,
                     CHOL_FLAG_RESIDUAL_FP64))
         return CHOL_ERR_ARG;
     if (n != nullptr || off != nullptr || o.layout != 0) return CHOL_ERR_UNSUPPORTED;
-    if (dt != CHOL_F32 && dt != CHOL_F64) return CHOL_ERR_UNSUPPORTED;
     if (o.prec == CHOL_PREC_BF16_REFINE) return CHOL_ERR_UNSUPPORTED;
-    if ((o.prec == CHOL_PREC_FP32_REFINE || o.prec == CHOL_PREC_TF32_REFINE) && dt != CHOL_F32)
+    if ((o.prec == CHOL_PREC_FP32_REFINE || o.prec == CHOL_PREC_TF32_REFINE) && !is_fp32(dt))
         return CHOL_ERR_UNSUPPORTED;
-    if (max_n > 1 << 16) return CHOL_ERR_UNSUPPORTED;
+    // complex matrices run as their real embedding of order 2 max_n
+    const bool cplx = dt == CHOL_C64 || dt == CHOL_C128;
+    if ((cplx ? 2 * (int64_t)max_n : (int64_t)max_n) > 1 << 16) return CHOL_ERR_UNSUPPORTED;
     if (batch > 0 && (ws == nullptr || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256 != 0))
         return CHOL_ERR_WORKSPACE;
     return CHOL_OK;
@@ -498,6 +499,7 @@ chol_status_t chol_factor_batched(chol_dtype_t dt, int32_t batch, const int32_t*
                                             blocked_workspace_bytes(dt, max_n, 0), ws, ws_bytes);
         if (sb != CHOL_OK || batch == 0) return sb;
         if (A == nullptr || R == nullptr) return CHOL_ERR_ARG;
+        if (dt == CHOL_C64 || dt == CHOL_C128) return CHOL_ERR_UNSUPPORTED;  // no complex R above order 64
         // the factor is formed in R itself (R is the working storage)
         return blocked_run(dt, batch, max_n, A, nullptr, R, info, blocked_pivot64(o), 0, 0, 0, blocked_tc(o),
                            device_error_word(), ws, static_cast<cudaStream_t>(stream));
@@ -524,6 +526,7 @@ chol_status_t chol_inv_batched(chol_dtype_t dt, int32_t batch, const int32_t* n,
         if (sb != CHOL_OK || batch == 0) return sb;
         if (A == nullptr || X == nullptr) return CHOL_ERR_ARG;
         if (X == A || (R != nullptr && (R == A || R == X))) return CHOL_ERR_ARG;
+        if ((dt == CHOL_C64 || dt == CHOL_C128) && R != nullptr) return CHOL_ERR_UNSUPPORTED;
         return blocked_run(dt, batch, max_n, A, R, X, info, blocked_pivot64(o), rs,
                            (o.flags & CHOL_FLAG_RESIDUAL_FP64) ? 1 : 0, 1, blocked_tc(o),
                            device_error_word(), ws, static_cast<cudaStream_t>(stream));

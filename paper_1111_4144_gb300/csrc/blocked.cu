@@ -719,6 +719,52 @@ __global__ void k_copy_upper(T* R, const T* X, int n, const int* failed) {
     }
 }
 
+// Complex Hermitian A = B + iC (B symmetric, C = Im A antisymmetric) as the
+// real symmetric matrix M = [[B, -C], [C, B]] of order 2n (M [x; y] is A z
+// for z = x + iy): M is positive definite exactly when A is, and
+// M^{-1} = [[P, -Q], [Q, P]] for A^{-1} = P + iQ.  Only A's upper triangle is
+// read (its diagonal taken as real); M is written in full.  32 x 32 tiles,
+// those below the diagonal read transposed through shared memory.
+constexpr int kEmT = 32;
+template <typename R>
+__global__ void __launch_bounds__(kEmT * 8) k_embed_hermitian(const cpx<R>* __restrict__ A, R* __restrict__ M,
+                                                               int n) {
+    __shared__ cpx<R> tile[kEmT][kEmT + 1];
+    const int ti = blockIdx.y, tj = blockIdx.x;
+    const bool up = ti <= tj;  // the source tile: (ti, tj) on or above the diagonal, else (tj, ti)
+    const int si = up ? ti : tj, sj = up ? tj : ti;
+    const int c = threadIdx.x;
+    for (int r = threadIdx.y; r < kEmT; r += blockDim.y) {
+        const int i = si * kEmT + r, j = sj * kEmT + c;
+        tile[r][c] = (i < n && j < n) ? A[(int64_t)i * n + j] : cpx<R>{R(0), R(0)};
+    }
+    __syncthreads();
+    const int64_t L = 2 * (int64_t)n;
+    for (int r = threadIdx.y; r < kEmT; r += blockDim.y) {
+        const int i = ti * kEmT + r, j = tj * kEmT + c;
+        if (i >= n || j >= n) continue;
+        // a_ij from the upper triangle: a_ij itself, or conj(a_ji) below the diagonal
+        const cpx<R> a = (i <= j) ? tile[r][c] : conj_v(tile[c][r]);
+        const R im = (i == j) ? R(0) : a.im;
+        M[i * L + j] = a.re;
+        M[(n + i) * L + n + j] = a.re;
+        M[i * L + n + j] = -im;
+        M[(n + i) * L + j] = im;
+    }
+}
+
+// X = P + iQ from the inverse of the embedding (full, n x n, dense): P its
+// top-left block, Q its bottom-left one; the diagonal real.
+template <typename R>
+__global__ void k_extract_hermitian(const R* __restrict__ XM, cpx<R>* __restrict__ X, int n) {
+    const int64_t L = 2 * (int64_t)n;
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < (int64_t)n * n;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = f / n, j = f - i * n;
+        X[f] = {XM[i * L + j], (i == j) ? R(0) : XM[(n + i) * L + j]};
+    }
+}
+
 // Convert the FP64 residual to the working precision.
 __global__ void k_narrow(float* dst, const double* src, int64_t count) {
     for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < count; f += (int64_t)gridDim.x * blockDim.x)
@@ -992,6 +1038,12 @@ cudaError_t blocked_timing_read(int kind, float* ms, double* flops, int* launche
 
 size_t blocked_workspace_bytes(int dtype, int n, int refine) {
     if (n <= 0) return 0;
+    if (dtype == CHOL_C64 || dtype == CHOL_C128) {
+        // the real embedding of order 2n and its inverse, then the real path's own
+        const int real = dtype == CHOL_C64 ? CHOL_F32 : CHOL_F64;
+        const size_t es = dtype == CHOL_C64 ? 4 : 8;
+        return 2 * align256((size_t)4 * n * n * es) + blocked_workspace_bytes(real, 2 * n, refine);
+    }
     const size_t es = (dtype == CHOL_F64) ? 8 : 4;
     const int kBlk = kblk(dtype);
     const int nb = (n + kBlk - 1) / kBlk;
@@ -1223,9 +1275,35 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
     return CHOL_OK;
 }
 
+// One complex Hermitian matrix through its real embedding (k_embed_hermitian):
+// the real path of order 2n on M in the workspace, then X = P + iQ.  info is
+// the embedding's (a row in 1..2n).
+template <typename Rl>
+static chol_status_t blocked_complex(const cpx<Rl>* A, cpx<Rl>* X, int n, int32_t* info, int pivot64,
+                                     int refine_steps, int resid64, int tc, int* err_word, char* ws, cudaStream_t s) {
+    const int n2 = 2 * n;
+    const size_t mbytes = align256((size_t)n2 * n2 * sizeof(Rl));
+    Rl* M = reinterpret_cast<Rl*>(ws);
+    Rl* XM = reinterpret_cast<Rl*>(ws + mbytes);
+    const int tiles = (n + kEmT - 1) / kEmT;
+    k_embed_hermitian<Rl><<<dim3(tiles, tiles), dim3(kEmT, 8), 0, s>>>(A, M, n);
+    if (cudaGetLastError() != cudaSuccess) return CHOL_ERR_CUDA;
+    chol_status_t st;
+    if constexpr (sizeof(Rl) == 4)
+        st = blocked_one<float>(M, nullptr, XM, n2, info, pivot64, refine_steps, resid64, 1, tc, err_word,
+                                ws + 2 * mbytes, s);
+    else
+        st = blocked_one<double>(M, nullptr, XM, n2, info, 0, 0, 0, 1, 0, err_word, ws + 2 * mbytes, s);
+    if (st != CHOL_OK) return st;
+    const int grid = std::max(1, std::min((int)(((int64_t)n * n + 255) / 256), device_info().sms * 8));
+    k_extract_hermitian<Rl><<<grid, 256, 0, s>>>(XM, X, n);
+    return cudaGetLastError() == cudaSuccess ? CHOL_OK : CHOL_ERR_CUDA;
+}
+
 chol_status_t blocked_run(int dtype, int32_t batch, int32_t n, const void* A, void* R, void* X, int32_t* info,
                           int pivot64, int refine_steps, int resid64, int want_inv, int tc, int* err_word, void* ws,
                           cudaStream_t s) {
+    if ((dtype == CHOL_C64 || dtype == CHOL_C128) && (R != nullptr || !want_inv)) return CHOL_ERR_UNSUPPORTED;
     for (int32_t bi = 0; bi < batch; ++bi) {
         const int64_t o = (int64_t)bi * n * n;
         chol_status_t st = CHOL_OK;
@@ -1240,6 +1318,14 @@ chol_status_t blocked_run(int dtype, int32_t batch, int32_t n, const void* A, vo
             st = blocked_one<double>(static_cast<const double*>(A) + o, R ? static_cast<double*>(R) + o : nullptr,
                                      static_cast<double*>(X) + o, n, info ? info + bi : nullptr, 0, 0, 0, want_inv,
                                      0, err_word, static_cast<char*>(ws), s);
+        else if (dtype == CHOL_C64)
+            st = blocked_complex<float>(static_cast<const cpx<float>*>(A) + o, static_cast<cpx<float>*>(X) + o, n,
+                                        info ? info + bi : nullptr, pivot64, refine_steps, resid64, tc, err_word,
+                                        static_cast<char*>(ws), s);
+        else if (dtype == CHOL_C128)
+            st = blocked_complex<double>(static_cast<const cpx<double>*>(A) + o, static_cast<cpx<double>*>(X) + o,
+                                         n, info ? info + bi : nullptr, 0, 0, 0, 0, err_word, static_cast<char*>(ws),
+                                         s);
         else
             return CHOL_ERR_UNSUPPORTED;
         if (st != CHOL_OK) return st;

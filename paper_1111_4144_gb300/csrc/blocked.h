@@ -14,7 +14,8 @@ size_t blocked_workspace_bytes(int dtype, int n, int refine);
 
 // Factor (and, if want_inv, invert) `batch` dense n x n matrices stored back
 // to back.  X is the working storage and receives the full Hermitian
-// inverse; R (optional) receives the factor.  Real types only.
+// inverse; R (optional) receives the factor.  Complex matrices go through
+// their real symmetric embedding of order 2n (the inverse only, R NULL).
 // tc: 0 CUDA-core products; 1 tensor-core TF32; 2 tensor-core TF32 with the
 // three-product split (FP32-level accuracy).  refine_steps (FP32): steps of
 // X <- X + X (I - A X), the residual in compensated FP32 pairs, or in FP64

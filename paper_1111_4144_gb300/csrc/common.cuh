@@ -172,6 +172,19 @@ CHOL_D void f2_fma2(f2acc2& r, float2 a, float2 b) {
 // Index helpers.  Packed upper, row by row: row i holds columns i..n-1.
 // ---------------------------------------------------------------------------
 CHOL_CX int pidx(int n, int i, int j) { return i * n - (i * (i - 1)) / 2 + (j - i); }
+
+// Row and column (i <= j) of element e of an order-n packed upper triangle:
+// i from the closed form of pidx's inverse, corrected by one step either way
+// against rounding.
+CHOL_D void tri_rc(int n, int e, int& i, int& j) {
+    const float b = 2.0f * n + 1.0f;
+    int r = (int)((b - sqrtf(b * b - 8.0f * (float)e)) * 0.5f);
+    r = max(0, min(r, n - 1));
+    if (pidx(n, r, r) > e) --r;
+    else if (r + 1 < n && pidx(n, r + 1, r + 1) <= e) ++r;
+    i = r;
+    j = e - pidx(n, r, r) + r;
+}
 CHOL_CX int tri(int n) { return n * (n + 1) / 2; }
 CHOL_CX int64_t tri64(int64_t n) { return n * (n + 1) / 2; }
 

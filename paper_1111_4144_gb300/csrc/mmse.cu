@@ -24,19 +24,6 @@ CHOL_HD size_t mmse_warp_elems(int max_n, int max_m) {
     return (size_t)(max_m + 1) * max_n + (size_t)max_n * (max_n + 1);
 }
 
-// Row and column (i <= j) of element e of an order-n packed upper triangle:
-// i from the closed form of pidx's inverse, corrected by one step either way
-// against rounding.
-CHOL_D void tri_rc(int n, int e, int& i, int& j) {
-    const float b = 2.0f * n + 1.0f;
-    int r = (int)((b - sqrtf(b * b - 8.0f * (float)e)) * 0.5f);
-    r = max(0, min(r, n - 1));
-    if (pidx(n, r, r) > e) --r;
-    else if (r + 1 < n && pidx(n, r + 1, r + 1) <= e) ++r;
-    i = r;
-    j = e - pidx(n, r, r) + r;
-}
-
 // Order and rows of matrix b, and its offsets in H, W and the packed A / X.
 CHOL_D void mmse_geom(const MmseParams& p, int64_t b, int& n, int& m, int64_t& oh, int64_t& ow, int64_t& oa) {
     n = p.n ? p.n[b] : p.max_n;

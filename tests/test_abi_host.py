@@ -59,7 +59,9 @@ FAKE = 0x100000  # a non-null pointer value; never dereferenced because validati
     (dict(max_n=0), "ARG"),
     (dict(max_n=65), "WORKSPACE"),          # blocked path: needs its workspace
     (dict(max_n=65, n=FAKE), "UNSUPPORTED"),  # blocked path: uniform batches only
-    (dict(max_n=65, dt=2), "UNSUPPORTED"),    # blocked path: real types only
+    (dict(max_n=65, dt=2), "WORKSPACE"),      # blocked path, complex: the real embedding's workspace
+    (dict(max_n=65, dt=2, R=2 * FAKE, X=3 * FAKE, ws=FAKE, ws_bytes=1 << 40), "UNSUPPORTED"),  # no complex R
+    (dict(max_n=65, dt=3, prec=1, X=3 * FAKE, ws=FAKE, ws_bytes=1 << 40), "UNSUPPORTED"),  # C128: no FP32 modes
     (dict(max_n=65, layout=1), "UNSUPPORTED"),
     (dict(A=None), "ARG"),
     (dict(X=None), "ARG"),
@@ -105,6 +107,9 @@ def test_opts_layout_and_order_set(L):
 
 def test_factor_and_plan_argument_checks(L):
     o = L.opts()
+    # the blocked path forms no complex factor
+    assert L.chol_factor_batched(L.CHOL_C64, 1, None, None, 65, FAKE, 2 * FAKE, None, o, FAKE, 1 << 40, None) \
+        == L.CHOL_ERR_UNSUPPORTED
     assert L.chol_factor_batched(L.CHOL_F64, 3, None, None, 4, FAKE, None, None, o, None, 0, None) == L.CHOL_ERR_ARG
     assert L.chol_factor_batched(L.CHOL_F64, 0, None, None, 4, None, None, None, o, None, 0, None) == L.CHOL_OK
     assert L.chol_plan_inv_create(None, L.CHOL_F32, 1, None, None, 4, FAKE, None, FAKE, None, o, None, 0) \

@@ -92,6 +92,70 @@ def test_blocked_non_pd_info(orc):
     assert np.all(np.isnan(X[0]))
 
 
+def _hermitian_pd(N, seed, decades=3.0):
+    """A = U diag(lambda) U^H, U unitary (QR of a complex Gaussian), lambda
+    log-spaced over [1, 10^decades]: complex Hermitian, kappa = 10^decades."""
+    rng = np.random.default_rng(seed)
+    Z = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    U, Rq = np.linalg.qr(Z)
+    U = U * (np.diagonal(Rq) / np.abs(np.diagonal(Rq)))
+    lam = 10.0 ** np.linspace(0.0, decades, N)
+    A = (U * lam) @ np.conj(U).T
+    return 0.5 * (A + np.conj(A).T)
+
+
+@pytest.mark.parametrize("N", [65, 100, 256])
+def test_blocked_complex128_parity(orc, N):
+    """Complex Hermitian matrices above order 64 (the real embedding of order
+    2N): X against the oracle's complex Cholesky and Sec. IV.A recurrence,
+    within 1e-11; X Hermitian with a real diagonal."""
+    A = _hermitian_pd(N, 900 + N)
+    X, info = _run(A.reshape(1, N, N))
+    _, Xo, info_o = _oracle(orc, A)
+    assert info[0] == 0 and info_o == 0
+    assert _rel(np.triu(X[0]), np.triu(Xo)) <= TOL64
+    assert np.array_equal(np.tril(X[0], -1), np.conj(np.triu(X[0], 1)).T)
+    assert np.all(np.imag(np.diagonal(X[0])) == 0)
+
+
+@pytest.mark.parametrize("N,mode", [(96, "native"), (300, "native"), (512, "tf32_refine2"), (1000, "fp32_refine1")])
+def test_blocked_complex64_parity(orc, N, mode):
+    """Complex64 above order 64 in the FP32 precision modes, against the
+    oracle on the same complex64-rounded matrix: within the FP32 tolerance,
+    and at FP32 accuracy (64 u32) after refinement."""
+    from paper_1111_4144_gb300 import _lib as L
+    A = _hermitian_pd(N, 950 + N).astype(np.complex64)
+    kw = {"native": {},
+          "tf32_refine2": dict(prec=L.CHOL_PREC_TF32_REFINE, refine_steps=2, flags=L.CHOL_FLAG_PIVOT64),
+          "fp32_refine1": dict(prec=L.CHOL_PREC_FP32_REFINE, refine_steps=1)}[mode]
+    X, info = _run(A.reshape(1, N, N), **kw)
+    _, Xo, info_o = _oracle(orc, A.astype(np.complex128))
+    assert info[0] == 0 and info_o == 0
+    err = _rel(np.triu(X[0]).astype(np.complex128), np.triu(Xo))
+    assert err <= tol32(1e3), (mode, err)
+    if mode != "native":
+        assert err <= 64 * U32, (mode, err)
+
+
+def test_blocked_complex_non_pd_and_rejections(orc):
+    """A non-positive-definite complex matrix: info > 0 (a row of the
+    embedding) and X all NaN; a complex factor, or R, above order 64 is
+    refused."""
+    import torch
+    from paper_1111_4144_gb300 import _lib as L, api
+    N = 130
+    A = _hermitian_pd(N, 7)
+    A[40, 40] = -3.0
+    X, info = _run(A.reshape(1, N, N))
+    assert 0 < info[0] <= 2 * N
+    assert np.all(np.isnan(np.real(X[0])))
+    At = torch.from_numpy(_hermitian_pd(N, 8).reshape(1, N, N)).cuda()
+    with pytest.raises(L.CholError):
+        api.inv(At, want_R=True)
+    with pytest.raises(L.CholError):
+        api.factor(At)
+
+
 def test_blocked_factor_only(orc):
     import torch
     from paper_1111_4144_gb300 import api
