@@ -766,7 +766,8 @@ def run_profile_case(args, local_rank):
 
     DTYPE:N:BATCH[:OPT...], OPT one of rK (FP32 + K refinement steps), ldl
     (the LDL form), bwd (the timed region runs the adjoint of the inverse,
-    dA for G = I, instead)."""
+    dA for G = I, instead), vK (kernel variant K of the order, pinned in the
+    tuning table), p64 (FP64 pivots)."""
     import torch
     from paper_1111_4144_gb300 import _lib as L, api, workloads as wl
     torch.cuda.set_device(local_rank)
@@ -781,6 +782,11 @@ def run_profile_case(args, local_rank):
             kw["flags"] = kw.get("flags", 0) | L.CHOL_FLAG_LDL
         elif o == "bwd":
             bwd = True
+        elif o.startswith("v") and o[1:].isdigit():
+            dtc = {"f32": L.CHOL_F32, "f64": L.CHOL_F64, "c64": L.CHOL_C64, "c128": L.CHOL_C128}[tag]
+            L.check(L.chol_tune_set(dtc, N, int(o[1:])), "chol_tune_set")
+        elif o == "p64":
+            kw["flags"] = kw.get("flags", 0) | L.CHOL_FLAG_PIVOT64
         else:
             raise SystemExit(f"--profile-case: unknown option {o!r}")
     npd = {"f32": np.float32, "f64": np.float64, "c64": np.complex64, "c128": np.complex128}[tag]

@@ -117,9 +117,10 @@ CHOL_D int class_count(const BatchParams& p, int N) {
 // LDL: the LDL form of Sec. II.A (Eqs. 9-11) instead: R unit upper, d_i on
 // its diagonal, d_i = a_ii - sum_k d_k |r_ki|^2 and
 // r_ij = (a_ij - sum_k conj(r_ki) d_k r_kj) / d_i; dinv[i] = 1/d_i.
-template <typename V, int N, bool LDL = false, class Acc>
-CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 1], bool pivot64 = false,
-                           bool gate = false) {
+// P64: Eq. 3 accumulated in FP64 (CHOL_FLAG_PIVOT64; FP32 value types), a
+// compile-time choice so that the default kernels carry no branch for it.
+template <typename V, int N, bool LDL = false, bool P64 = false, class Acc>
+CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 1], bool gate = false) {
     using R = typename traits<V>::real;
     int info = 0;
     bool redo = false;
@@ -145,7 +146,7 @@ CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 
             if (info == 0 && !pivot_ok(t)) info = i + 1;
             rii = t;
             inv = R(1) / t;
-        } else if (sizeof(R) == 4 && pivot64) {
+        } else if constexpr (sizeof(R) == 4 && P64) {
             double td = (double)t;
 #pragma unroll
             for (int k = 0; k < N; ++k)
@@ -376,8 +377,8 @@ CHOL_D void lane_store(const BatchParams& p, V* out, uint4* buf, const int64_t* 
 // Lane kernel: one matrix per thread.
 // ---------------------------------------------------------------------------
 // GATE: CHOL_FLAG_PIVOT64_AUTO's cancellation test (FP32 value types only).
-// LDL: the LDL form (CHOL_FLAG_LDL).
-template <typename V, int N, bool GATE = false, bool LDL = false>
+// LDL: the LDL form (CHOL_FLAG_LDL).  P64: FP64 pivots (CHOL_FLAG_PIVOT64).
+template <typename V, int N, bool GATE = false, bool LDL = false, bool P64 = false>
 __global__ void __launch_bounds__(LaneCfg<V, N>::THREADS)
 k_lane(BatchParams p) {
     using C = LaneCfg<V, N>;
@@ -450,7 +451,7 @@ k_lane(BatchParams p) {
             int info = 0;
             R dinv[N];
             if (t < m) {
-                info = factor_unrolled<V, N, LDL>(r, dinv, p.flags & CHOL_FLAG_PIVOT64, gate);
+                info = factor_unrolled<V, N, LDL, P64>(r, dinv, gate);
                 if (store_R && (!GATE || info != kInfoRedo)) {
 #pragma unroll
                     for (int e = 0; e < TN; ++e) {
@@ -492,7 +493,7 @@ k_lane(BatchParams p) {
             int info = 0;
             R dinv[N];
             SmemMat<V, N> sm{buf, t};
-            if (t < m) info = factor_unrolled<V, N, LDL>(sm, dinv, p.flags & CHOL_FLAG_PIVOT64, gate);
+            if (t < m) info = factor_unrolled<V, N, LDL, P64>(sm, dinv, gate);
             if (t < m) s_info[t] = info;
             if (store_R) {
                 __syncthreads();

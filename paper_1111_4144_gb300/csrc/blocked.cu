@@ -753,15 +753,19 @@ __global__ void __launch_bounds__(kEmT * 8) k_embed_hermitian(const cpx<R>* __re
     }
 }
 
-// X = P + iQ from the inverse of the embedding (full, n x n, dense): P its
-// top-left block, Q its bottom-left one; the diagonal real.
+// X = P + iQ from the inverse of the embedding (full, dense): P its top-left
+// block, Q the mean of its bottom-left block and the negated top-right one
+// (equal but for rounding), each entry below the diagonal the conjugate of
+// its mirror, so that X is exactly Hermitian with a real diagonal.
 template <typename R>
 __global__ void k_extract_hermitian(const R* __restrict__ XM, cpx<R>* __restrict__ X, int n) {
     const int64_t L = 2 * (int64_t)n;
     for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < (int64_t)n * n;
          f += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = f / n, j = f - i * n;
-        X[f] = {XM[i * L + j], (i == j) ? R(0) : XM[(n + i) * L + j]};
+        const int64_t r = f / n, c = f - r * n;
+        const int64_t i = r < c ? r : c, j = r < c ? c : r;  // the upper-triangle entry (i <= j)
+        const R q = (i == j) ? R(0) : R(0.5) * (XM[(n + i) * L + j] - XM[i * L + n + j]);
+        X[f] = {XM[i * L + j], r <= c ? q : -q};
     }
 }
 

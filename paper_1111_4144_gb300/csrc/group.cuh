@@ -293,7 +293,8 @@ constexpr int group_size() {
 //        inverse every thread keeps its columns in full (the lower half
 //        mirrored in once per row), so the dot products run on registers.
 // GATE: CHOL_FLAG_PIVOT64_AUTO's cancellation test (FP32 value types only).
-template <typename V, int N, int G, int ALG, int W = 4, int MINB = 1, bool GATE = false, bool LDL = false>
+template <typename V, int N, int G, int ALG, int W = 4, int MINB = 1, bool GATE = false, bool LDL = false,
+          bool P64 = false>
 __global__ void __launch_bounds__(GroupCfg<V, N, G, W>::THREADS, MINB)
 k_group(BatchParams p) {
     static_assert(!LDL || ALG == 1, "the LDL form is built on the left-looking rows");
@@ -475,7 +476,7 @@ k_group(BatchParams p) {
                 rii = tt;  // d_i
                 inv = R(1) / tt;
                 dd[i] = tt;
-            } else if (sizeof(R) == 4 && (p.flags & CHOL_FLAG_PIVOT64)) {
+            } else if constexpr (sizeof(R) == 4 && P64) {
                 // Eq. 3 in FP64: a_ii (still in the mirror) minus |r_ki|^2 over column i
                 double td = (double)re_of(M[row_base(N, i) + i]);
 #pragma unroll

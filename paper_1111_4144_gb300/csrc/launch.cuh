@@ -33,11 +33,11 @@ CHOL_HD bool gate_on(const BatchParams& p) {
 template <typename V>
 constexpr bool gate_built() { return sizeof(typename traits<V>::real) == 4; }
 
-template <typename V, int N, bool GATE, bool LDL = false>
+template <typename V, int N, bool GATE, bool LDL = false, bool P64 = false>
 static cudaError_t launch_lane_t(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
     constexpr int THREADS = LaneCfg<V, N>::THREADS;
     constexpr size_t SMEM = LaneCfg<V, N>::SMEM;
-    auto kern = k_lane<V, N, GATE, LDL>;
+    auto kern = k_lane<V, N, GATE, LDL, P64>;
     static std::once_flag once;
     static int per_sm = 1;
     static cudaError_t setup_err = cudaSuccess;
@@ -86,10 +86,11 @@ static cudaError_t launch_warp(const BatchParams& p, int N, int upper_count, cud
 
 // W warps per CTA; MINB resident CTAs per SM requested from the register
 // allocator (MINB = 2 with W = 8 caps a thread at 128 registers).
-template <typename V, int N, int G, int ALG, int W = 4, int MINB = 1, bool GATE = false, bool LDL = false>
+template <typename V, int N, int G, int ALG, int W = 4, int MINB = 1, bool GATE = false, bool LDL = false,
+          bool P64 = false>
 static cudaError_t launch_group(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
     using C = GroupCfg<V, N, G, W>;
-    auto kern = k_group<V, N, G, ALG, W, MINB, GATE, LDL>;
+    auto kern = k_group<V, N, G, ALG, W, MINB, GATE, LDL, P64>;
     static std::once_flag once;
     static int per_sm = 1;
     static cudaError_t setup_err = cudaSuccess;
@@ -124,13 +125,22 @@ constexpr int num_variants() {
 template <typename V, int N>
 static cudaError_t launch_fixed(const BatchParams& p, int variant, int upper_count, cudaStream_t s, bool dry) {
     constexpr int kind = kernel_kind<V, N>();
-    // the LDL form (CHOL_FLAG_LDL) and the cancellation test
-    // (CHOL_FLAG_PIVOT64_AUTO) run the default variant, built for them
+    // the LDL form (CHOL_FLAG_LDL), FP64 pivots (CHOL_FLAG_PIVOT64) and the
+    // cancellation test (CHOL_FLAG_PIVOT64_AUTO) run the default variant,
+    // built for each
     if (p.flags & CHOL_FLAG_LDL) {
         if constexpr (kind == 0) return launch_lane_t<V, N, false, true>(p, upper_count, s, dry);
         else if constexpr (kind == 1)
             return launch_group<V, N, group_size<V, N>(), 1, 4, 1, false, true>(p, upper_count, s, dry);
         else return launch_warp<V>(p, N, upper_count, s, dry);
+    }
+    if constexpr (gate_built<V>()) {
+        if (p.flags & CHOL_FLAG_PIVOT64) {
+            if constexpr (kind == 0) return launch_lane_t<V, N, false, false, true>(p, upper_count, s, dry);
+            else if constexpr (kind == 1)
+                return launch_group<V, N, group_size<V, N>(), 1, 4, 1, false, false, true>(p, upper_count, s, dry);
+            else return launch_warp<V>(p, N, upper_count, s, dry);
+        }
     }
     if constexpr (kind == 0) {
         if constexpr (num_variants<V, N>() > 1)
