@@ -41,17 +41,18 @@ __global__ void k_backward(BwdParams p) {
         if (n <= 0 || n > N) continue;
         const int64_t og = p.off ? p.off[b] : (int64_t)b * N * N;
         const int64_t ox = p.xoff ? p.xoff[b] : (int64_t)b * (p.layout ? tri64(N) : (int64_t)N * N);
+        __syncwarp();  // the previous matrix's squares are no longer read
+        stage_hermitian(X + ox, n, p.layout, Xf, LD, lane);
+        // G into Tf (free until T = S X), then S = (G + G^H)/2 into Sf
+        warp_gather(G + og, n * n, lane, [&](int e, V v) {
+            const int i = e / n, j = e - i * n;
+            Tf[i * LD + j] = v;
+        });
+        __syncwarp();
         for (int i = 0; i < n; ++i)
             for (int j = i + lane; j < n; j += 32) {
-                const int64_t gx = p.layout ? (int64_t)pidx(n, i, j) : (int64_t)i * n + j;
-                V x = X[ox + gx];
-                if (i == j) x = from_real<V>(re_of(x));
-                Xf[i * LD + j] = x;
-                Xf[j * LD + i] = conj_v(x);
-                // S = (G + G^H)/2
-                const V gij = G[og + (int64_t)i * n + j], gji = G[og + (int64_t)j * n + i];
                 using R = typename traits<V>::real;
-                const V sij = scale_v(gij + conj_v(gji), R(0.5));
+                const V sij = scale_v(Tf[i * LD + j] + conj_v(Tf[j * LD + i]), R(0.5));
                 Sf[i * LD + j] = (i == j) ? from_real<V>(re_of(sij)) : sij;
                 Sf[j * LD + i] = conj_v(sij);
             }
@@ -196,37 +197,21 @@ __global__ void __launch_bounds__(128) k_backward_tiled(BwdParams p) {
         if (n <= 0 || n > N) continue;
         const int64_t og = p.off ? p.off[b] : (int64_t)b * N * N;
         const int64_t ox = p.xoff ? p.xoff[b] : (int64_t)b * (p.layout ? tri64(N) : (int64_t)N * N);
-        // zero padding beyond n; G staged in Ts
-        for (int e = lane; e < kTB * kTLD; e += 32) {
-            Xs[e] = zero_v<V>();
-            St[e] = zero_v<V>();
+        __syncwarp();  // the previous matrix's squares are no longer read
+        if (n < kTB) {
+            // the zero padding rows and columns n..kTB-1 (the products run over kTB)
+            for (int e = lane; e < kTB * kTB; e += 32) {
+                const int i = e / kTB, j = e % kTB;
+                if (i >= n || j >= n) Xs[i * kTLD + j] = St[i * kTLD + j] = zero_v<V>();
+            }
         }
-        for (int e = lane; e < n * n; e += 32) {
+        // G staged in Ts; X in full from its upper half
+        warp_gather(G + og, n * n, lane, [&](int e, V v) {
             const int k = e / n, r = e - k * n;
-            Ts[k * kTLD + r] = G[og + e];
-        }
+            Ts[k * kTLD + r] = v;
+        });
+        stage_hermitian(X + ox, n, p.layout, Xs, kTLD, lane);
         __syncwarp();
-        // X in full from its upper half
-        if (p.layout) {
-            for (int e = lane; e < tri(n); e += 32) {
-                int i = 0;
-                while (pidx(n, i + 1, i + 1) <= e && i + 1 < n) ++i;
-                const int j = e - pidx(n, i, i) + i;
-                V x = X[ox + e];
-                if (i == j) x = from_real<V>(re_of(x));
-                Xs[i * kTLD + j] = x;
-                Xs[j * kTLD + i] = conj_v(x);
-            }
-        } else {
-            for (int e = lane; e < n * n; e += 32) {
-                const int i = e / n, j = e - i * n;
-                if (j < i) continue;
-                V x = X[ox + e];
-                if (i == j) x = from_real<V>(re_of(x));
-                Xs[i * kTLD + j] = x;
-                Xs[j * kTLD + i] = conj_v(x);
-            }
-        }
         // St[k][r] = s_rk = (g_rk + conj(g_kr)) / 2
         for (int e = lane; e < n * n; e += 32) {
             const int k = e / n, r = e - k * n;

@@ -519,6 +519,58 @@ CHOL_HD size_t warp_elems(const BatchParams& p, int N) {
 }
 
 // ---------------------------------------------------------------------------
+// Warp-wide staging of one matrix from global into shared memory.
+// ---------------------------------------------------------------------------
+// f(e, src[e]) for e = 0..count-1 over the 32 lanes of a warp, each lane
+// issuing eight loads before it hands any on: a matrix costs a few memory
+// round trips instead of one per element a lane takes.
+template <typename V, class F>
+CHOL_D void warp_gather(const V* __restrict__ src, int count, int lane, F&& f) {
+    constexpr int U = 8;
+#pragma unroll 1
+    for (int e0 = 0; e0 < count; e0 += 32 * U) {
+        V v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * 32 + lane;
+            if (e < count) v[u] = src[e];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * 32 + lane;
+            if (e < count) f(e, v[u]);
+        }
+    }
+}
+
+// Row and column of element e of an order-n matrix stored dense (row-major)
+// or packed (upper triangle by rows); dense elements below the diagonal
+// come back with i > j.
+CHOL_D void elem_rc(int layout, int n, int e, int& i, int& j) {
+    if (layout) {
+        tri_rc(n, e, i, j);
+    } else {
+        i = e / n;
+        j = e - i * n;
+    }
+}
+
+// The upper triangle of the order-n matrix at src (dense or packed) into the
+// square S (row stride ld) in full: mirrored (conjugated), diagonal real.
+template <typename V>
+CHOL_D void stage_hermitian(const V* __restrict__ src, int n, int layout, V* S, int ld, int lane) {
+    warp_gather(src, layout ? n * (n + 1) / 2 : n * n, lane, [&](int e, V v) {
+        int i, j;
+        elem_rc(layout, n, e, i, j);
+        if (i <= j) {
+            const V x = (i == j) ? from_real<V>(re_of(v)) : v;
+            S[i * ld + j] = x;
+            S[j * ld + i] = conj_v(x);
+        }
+    });
+}
+
+// ---------------------------------------------------------------------------
 // Warp kernel: one matrix per warp, runtime order N (<= 64), lanes own the
 // columns j = lane and j = lane + 32.  The matrix is a padded dense square
 // in shared memory (row stride N+1).
@@ -533,19 +585,12 @@ CHOL_D void warp_one(const BatchParams& p, int N, int64_t b, int64_t o, V* S, in
     const V* A = static_cast<const V*>(p.A);
     V* Xo = static_cast<V*>(p.X);
     V* Ro = static_cast<V*>(p.R);
-    const int TN = tri(N);
     // load the upper triangle
-    if (p.layout) {
-        for (int e = lane; e < TN; e += 32) {
-            int i = 0;
-            while (pidx(N, i + 1, i + 1) <= e && i + 1 < N) ++i;
-            const int j = e - pidx(N, i, i) + i;
-            S[i * LD + j] = A[o + e];
-        }
-    } else {
-        for (int i = 0; i < N; ++i)
-            for (int j = i + lane; j < N; j += 32) S[i * LD + j] = A[o + (int64_t)i * N + j];
-    }
+    warp_gather(A + o, p.layout ? tri(N) : N * N, lane, [&](int e, V v) {
+        int i, j;
+        elem_rc(p.layout, N, e, i, j);
+        if (i <= j) S[i * LD + j] = v;
+    });
     __syncwarp();
     // ---- factor, Eqs. 3-4, row by row; with CHOL_FLAG_LDL the LDL form of
     // Sec. II.A (Eqs. 9-11): d_i = a_ii - sum |r_ki|^2 d_k and

@@ -46,7 +46,8 @@ __global__ void k_gram(MmseParams p, typename traits<V>::real s2) {
         int64_t oh, ow, oa;
         mmse_geom(p, b, n, m, oh, ow, oa);
         if (n < 1 || n > p.max_n || m < 0 || m > p.max_m) continue;  // invalid orders are flagged by the inverse
-        for (int e = lane; e < m * n; e += 32) Hs[e] = H[oh + e];
+        __syncwarp();  // the previous matrix's H is no longer read
+        warp_gather(H + oh, m * n, lane, [&](int e, V v) { Hs[e] = v; });
         __syncwarp();
         const int T = tri(n);
         for (int e = lane; e < T; e += 32) {
@@ -77,20 +78,19 @@ __global__ void k_apply(MmseParams p) {
         mmse_geom(p, b, n, m, oh, ow, oa);
         if (n < 1 || n > p.max_n || m < 0 || m > p.max_m) continue;
         const bool bad = p.info && p.info[b] != 0;
+        __syncwarp();  // the previous matrix's H and X are no longer read
         // H transposed (row stride m + 1), so that lanes over k read consecutive words below
-        for (int e = lane; e < m * n; e += 32) {
+        warp_gather(H + oh, m * n, lane, [&](int e, V v) {
             const int r = e / n, c = e - r * n;
-            Ht[c * (m + 1) + r] = H[oh + e];
-        }
+            Ht[c * (m + 1) + r] = v;
+        });
         const int LD = n + 1;
-        const int T = tri(n);
-        for (int e = lane; e < T; e += 32) {
+        warp_gather(X + oa, tri(n), lane, [&](int e, V x) {
             int i, j;
             tri_rc(n, e, i, j);
-            const V x = X[oa + e];
             Xs[i * LD + j] = x;
             Xs[j * LD + i] = conj_v(x);
-        }
+        });
         __syncwarp();
         // w_ik = sum_j x_ij conj(h_kj), W row-major n x m
         for (int e = lane; e < n * m; e += 32) {

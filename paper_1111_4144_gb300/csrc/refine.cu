@@ -72,43 +72,6 @@ CHOL_D V resid_entry(const V* Arow, const V* Xcol, int LD, int n, bool diag) {
     }
 }
 
-// The upper triangle of an order-n matrix at element offset o of src (dense
-// or packed) into the square S (row stride ld) in full, mirrored, with a
-// real diagonal.  Each lane issues its loads eight at a time before it
-// stores any of them, so a matrix costs a few memory round trips, not n.
-template <typename V>
-CHOL_D void stage_hermitian(const V* __restrict__ src, int64_t o, int n, int layout, V* S, int ld, int lane) {
-    constexpr int U = 8;
-    const int count = layout ? n * (n + 1) / 2 : n * n;
-#pragma unroll 1
-    for (int e0 = 0; e0 < count; e0 += 32 * U) {
-        V v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = e0 + u * 32 + lane;
-            if (e < count) v[u] = src[o + e];
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = e0 + u * 32 + lane;
-            if (e < count) {
-                int i, j;
-                if (layout) {
-                    tri_rc(n, e, i, j);
-                } else {
-                    i = e / n;
-                    j = e - i * n;
-                }
-                if (i <= j) {
-                    const V x = (i == j) ? from_real<V>(re_of(v[u])) : v[u];
-                    S[i * ld + j] = x;
-                    S[j * ld + i] = conj_v(x);
-                }
-            }
-        }
-    }
-}
-
 template <typename V, bool R64>
 __global__ void k_refine(BatchParams p, int steps, int automatic) {
     using W = typename wide<V>::type;
@@ -130,12 +93,12 @@ __global__ void k_refine(BatchParams p, int steps, int automatic) {
         const int64_t o = p.off ? p.off[b] : (int64_t)b * (p.layout ? tri64(N) : (int64_t)N * N);
         auto gidx = [&](int i, int j) { return p.layout ? (int64_t)pidx(n, i, j) : (int64_t)i * n + j; };
         __syncwarp();  // the previous matrix's squares are no longer read
-        stage_hermitian(A, o, n, p.layout, Af, LD, lane);
+        stage_hermitian(A + o, n, p.layout, Af, LD, lane);
         int todo = steps;
         for (int s = 0; s <= todo; ++s) {
             // (re)load the current X (the columns below update it in memory)
             __syncwarp();
-            stage_hermitian(static_cast<const V*>(X), o, n, p.layout, Xf, LD, lane);
+            stage_hermitian(static_cast<const V*>(X) + o, n, p.layout, Xf, LD, lane);
             __syncwarp();
             if (s == 0 && automatic) {
                 double g = 0.0;
@@ -262,8 +225,8 @@ __global__ void __launch_bounds__(128) k_refine_tiled(BatchParams p, int steps, 
                 if (i >= n || j >= n) As[i * kRLD + j] = Xs[i * kRLD + j] = zero_v<V>();
             }
         }
-        stage_hermitian(A, o, n, p.layout, As, kRLD, lane);
-        stage_hermitian(static_cast<const V*>(X), o, n, p.layout, Xs, kRLD, lane);
+        stage_hermitian(A + o, n, p.layout, As, kRLD, lane);
+        stage_hermitian(static_cast<const V*>(X) + o, n, p.layout, Xs, kRLD, lane);
         int todo = steps;
 #pragma unroll 1
         for (int s = 0; s <= todo; ++s) {
