@@ -360,7 +360,9 @@ chol_status_t chol_pivot64_redo_count(void* stream, int64_t* count);
  * compiled kernel variant (one matrix per thread vs. G threads per matrix,
  * or G vs. 2G threads); which is fastest depends on the GPU.
  * chol_autotune times every variant of every order 1..max_n for dtype dt and
- * layout on a synthetic batch of `batch` matrices on `stream` and keeps the
+ * layout on a synthetic batch of `batch` matrices on `stream` (each timed
+ * launch after L2 is overwritten, as for batches streamed from HBM; it
+ * allocates twice L2 for that) and keeps the
  * fastest in a per-process table that all later calls use (plans capture
  * the variant current at creation).  It allocates and frees device memory
  * and synchronises the stream, so it is a set-up call, not for the hot path

@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "batched.cuh"
+#include "tile32.cuh"
 #include "dispatch.h"
 
 namespace cholinv {
@@ -97,87 +98,13 @@ __global__ void k_backward(BwdParams p) {
 //   Ts: T = S X; then -X T is staged in St and its upper half written,
 //       mirrored, so that dA is exactly Hermitian.
 // ---------------------------------------------------------------------------
-constexpr int kTB = 32;          // padded order
-constexpr int kTLD = kTB + 4;    // row stride
 
 template <typename V>
 CHOL_HD size_t bwd_tiled_warp_bytes() {
-    return (size_t)3 * kTB * kTLD * sizeof(V);
+    // Xs, St, Ts; then the next matrix's G and X as stored (asynchronous copies)
+    return (size_t)3 * kTB * kTLD * sizeof(V) + (size_t)2 * kTB * kTB * sizeof(V);
 }
 
-// acc[r][c] += sum_k op(Lt[k][r0 + r]) Rm[k][c0 + c], k = 0..31; op is the
-// conjugate when CONJ.  FP32 and complex64 run on paired FP32 instructions
-// (two entries of a row, or the two parts of a complex entry, per
-// instruction); FP64 types on plain fused multiply-adds.
-template <typename V, bool CONJ>
-CHOL_D void tile_product(const V* Lt, const V* Rm, int r0, int c0, V (&acc)[4][8]) {
-    if constexpr (std::is_same<V, float>::value) {
-        float2 a2[4][4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int cp = 0; cp < 4; ++cp) a2[r][cp] = make_float2(acc[r][2 * cp], acc[r][2 * cp + 1]);
-#pragma unroll 4
-        for (int k = 0; k < kTB; ++k) {
-            float2 b[4];
-#pragma unroll
-            for (int cp = 0; cp < 4; ++cp) b[cp] = *reinterpret_cast<const float2*>(&Rm[k * kTLD + c0 + 2 * cp]);
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const float a = Lt[k * kTLD + r0 + r];
-                const float2 aa = make_float2(a, a);
-#pragma unroll
-                for (int cp = 0; cp < 4; ++cp) a2[r][cp] = __ffma2_rn(aa, b[cp], a2[r][cp]);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int cp = 0; cp < 4; ++cp) {
-                acc[r][2 * cp] = a2[r][cp].x;
-                acc[r][2 * cp + 1] = a2[r][cp].y;
-            }
-        return;
-    } else if constexpr (std::is_same<V, cpx<float>>::value) {
-        // {re, im} += a.re {b.re, b.im} + a.im {-b.im, b.re}  (a conjugated when CONJ)
-#pragma unroll 2
-        for (int k = 0; k < kTB; ++k) {
-            float2 b[8], bs[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const cpx<float> v = Rm[k * kTLD + c0 + c];
-                b[c] = make_float2(v.re, v.im);
-                bs[c] = make_float2(-v.im, v.re);
-            }
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const cpx<float> a = Lt[k * kTLD + r0 + r];
-                const float ai = CONJ ? -a.im : a.im;
-                const float2 ar = make_float2(a.re, a.re), aim = make_float2(ai, ai);
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    float2 q = make_float2(acc[r][c].re, acc[r][c].im);
-                    q = __ffma2_rn(ar, b[c], q);
-                    q = __ffma2_rn(aim, bs[c], q);
-                    acc[r][c] = {q.x, q.y};
-                }
-            }
-        }
-        return;
-    }
-#pragma unroll 4
-    for (int k = 0; k < kTB; ++k) {
-        V a[4], b[8];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) a[r] = CONJ ? conj_v(Lt[k * kTLD + r0 + r]) : Lt[k * kTLD + r0 + r];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) b[c] = Rm[k * kTLD + c0 + c];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int c = 0; c < 8; ++c) acc[r][c] = fma_v(a[r], b[c], acc[r][c]);
-    }
-}
 
 template <typename V>
 __global__ void __launch_bounds__(128) k_backward_tiled(BwdParams p) {
@@ -187,39 +114,62 @@ __global__ void __launch_bounds__(128) k_backward_tiled(BwdParams p) {
     V* Xs = reinterpret_cast<V*>(smem_raw + (size_t)w * bwd_tiled_warp_bytes<V>());
     V* St = Xs + kTB * kTLD;
     V* Ts = St + kTB * kTLD;
+    V* RawG = Ts + kTB * kTLD;
+    V* RawX = RawG + kTB * kTB;
     const V* X = static_cast<const V*>(p.X);
     const V* G = static_cast<const V*>(p.G);
     V* dA = static_cast<V*>(p.dA);
     const int r0 = (lane / 4) * 4, c0 = (lane % 4) * 8;
     const int N = p.max_n;
-    for (int b = blockIdx.x * wpc + w; b < p.batch; b += gridDim.x * wpc) {
-        const int n = p.n ? p.n[b] : N;
-        if (n <= 0 || n > N) continue;
-        const int64_t og = p.off ? p.off[b] : (int64_t)b * N * N;
-        const int64_t ox = p.xoff ? p.xoff[b] : (int64_t)b * (p.layout ? tri64(N) : (int64_t)N * N);
-        __syncwarp();  // the previous matrix's squares are no longer read
-        if (n < kTB) {
-            // the zero padding rows and columns n..kTB-1 (the products run over kTB)
-            for (int e = lane; e < kTB * kTB; e += 32) {
-                const int i = e / kTB, j = e % kTB;
-                if (i >= n || j >= n) Xs[i * kTLD + j] = St[i * kTLD + j] = zero_v<V>();
+    // matrix b's order (0: nothing to do) and the offsets of G / dA and of X
+    auto geom = [&](int b, int& n, int64_t& og, int64_t& ox) {
+        n = p.n ? p.n[b] : N;
+        if (n <= 0 || n > N) n = 0;
+        og = p.off ? p.off[b] : (int64_t)b * N * N;
+        ox = p.xoff ? p.xoff[b] : (int64_t)b * (p.layout ? tri64(N) : (int64_t)N * N);
+    };
+    // matrix b's G and X as stored, into RawG / RawX (asynchronous)
+    auto prefetch = [&](int b) {
+        if (b < p.batch) {
+            int n;
+            int64_t og, ox;
+            geom(b, n, og, ox);
+            if (n > 0) {
+                warp_copy_async(RawG, G + og, n * n, lane);
+                warp_copy_async(RawX, X + ox, p.layout ? n * (n + 1) / 2 : n * n, lane);
             }
         }
-        // G staged in Ts; X in full from its upper half
-        warp_gather(G + og, n * n, lane, [&](int e, V v) {
-            const int k = e / n, r = e - k * n;
-            Ts[k * kTLD + r] = v;
-        });
-        stage_hermitian(X + ox, n, p.layout, Xs, kTLD, lane);
-        __syncwarp();
-        // St[k][r] = s_rk = (g_rk + conj(g_kr)) / 2
-        for (int e = lane; e < n * n; e += 32) {
-            const int k = e / n, r = e - k * n;
-            V sv = scale_v(Ts[r * kTLD + k] + conj_v(Ts[k * kTLD + r]), R(0.5));
-            if (k == r) sv = from_real<V>(re_of(sv));
-            St[k * kTLD + r] = sv;
+        cp_async_commit();
+    };
+    const int stride = gridDim.x * wpc;
+    int b = blockIdx.x * wpc + w;
+    prefetch(b);
+    for (; b < p.batch; b += stride) {
+        int n;
+        int64_t og, ox;
+        geom(b, n, og, ox);
+        cp_async_wait<0>();
+        __syncwarp();  // every lane's copies are visible; the previous matrix's squares are no longer read
+        if (n > 0) {
+            if (n < kTB) {
+                // the zero padding rows and columns n..kTB-1 (the products run over kTB)
+                for (int e = lane; e < kTB * kTB; e += 32) {
+                    const int i = e / kTB, j = e % kTB;
+                    if (i >= n || j >= n) Xs[i * kTLD + j] = St[i * kTLD + j] = zero_v<V>();
+                }
+            }
+            // X in full from its upper half; St[k][r] = s_rk = (g_rk + conj(g_kr)) / 2
+            unpack_hermitian(RawX, n, p.layout, Xs, kTLD, lane);
+            for (int e = lane; e < n * n; e += 32) {
+                const int k = e / n, r = e - k * n;
+                V sv = scale_v(RawG[r * n + k] + conj_v(RawG[k * n + r]), R(0.5));
+                if (k == r) sv = from_real<V>(re_of(sv));
+                St[k * kTLD + r] = sv;
+            }
         }
-        __syncwarp();
+        __syncwarp();  // the stored copies are read: the next matrix's may land there
+        prefetch(b + stride);
+        if (n == 0) continue;
         V acc[4][8];
         // T = S X
 #pragma unroll
@@ -259,7 +209,7 @@ template <typename V>
 static cudaError_t launch_bwd_tiled(const BwdParams& p, cudaStream_t s, bool dry) {
     static std::once_flag once;
     static cudaError_t setup = cudaSuccess;
-    constexpr int warps = 4;
+    constexpr int warps = sizeof(V) == 4 ? 4 : 2;
     const size_t smem = bwd_tiled_warp_bytes<V>() * warps;
     std::call_once(once, [&] {
         setup = cudaFuncSetAttribute(k_backward_tiled<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

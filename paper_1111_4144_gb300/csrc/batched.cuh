@@ -570,6 +570,39 @@ CHOL_D void stage_hermitian(const V* __restrict__ src, int n, int layout, V* S, 
     });
 }
 
+// One warp's asynchronous copy (cp.async; complete after cp_async_wait) of
+// `count` elements from global src to shared dst: 16-byte units when both
+// ends are 16-byte aligned and the size is a multiple of 16, else 4-byte
+// units (every element type here is a whole number of aligned words).
+template <typename V>
+CHOL_D void warp_copy_async(V* dst, const V* src, int count, int lane) {
+    const int bytes = count * (int)sizeof(V);
+    char* d = reinterpret_cast<char*>(dst);
+    const char* s = reinterpret_cast<const char*>(src);
+    if (((reinterpret_cast<uintptr_t>(d) | reinterpret_cast<uintptr_t>(s)) % 16) == 0 && bytes % 16 == 0) {
+        for (int k = lane; k < bytes / 16; k += 32) cp_async<16>(d + 16 * k, s + 16 * k);
+    } else {
+        for (int k = lane; k < bytes / 4; k += 32) cp_async<4>(d + 4 * k, s + 4 * k);
+    }
+}
+
+// The upper triangle of an order-n matrix held as stored (dense or packed)
+// in shared memory into the square S (row stride ld) in full: mirrored
+// (conjugated), diagonal real.
+template <typename V>
+CHOL_D void unpack_hermitian(const V* raw, int n, int layout, V* S, int ld, int lane) {
+    const int count = layout ? n * (n + 1) / 2 : n * n;
+    for (int e = lane; e < count; e += 32) {
+        int i, j;
+        elem_rc(layout, n, e, i, j);
+        if (i <= j) {
+            const V x = (i == j) ? from_real<V>(re_of(raw[e])) : raw[e];
+            S[i * ld + j] = x;
+            S[j * ld + i] = conj_v(x);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Warp kernel: one matrix per warp, runtime order N (<= 64), lanes own the
 // columns j = lane and j = lane + 32.  The matrix is a padded dense square

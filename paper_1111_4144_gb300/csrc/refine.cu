@@ -18,6 +18,7 @@
 
 #include "batched.cuh"
 #include "dispatch.h"
+#include "tile32.cuh"
 
 namespace cholinv {
 
@@ -135,10 +136,13 @@ __global__ void k_refine(BatchParams p, int steps, int automatic) {
 // ---------------------------------------------------------------------------
 constexpr int kRB = 32;
 constexpr int kRLD = kRB + 4;
+static_assert(kRB == kTB && kRLD == kTLD, "the correction runs on the adjoint's tile product");
 
+// A, X and E as padded squares, then the next matrix's A and X as stored
+// (dense or packed), filled by asynchronous copies during this one's steps.
 template <typename V>
 CHOL_HD size_t refine_tiled_warp_bytes() {
-    return (size_t)3 * kRB * kRLD * sizeof(V);
+    return (size_t)3 * kRB * kRLD * sizeof(V) + (size_t)2 * kRB * kRB * sizeof(V);
 }
 
 // acc += a b with a, b real (paired lanes: two entries of a row) or complex
@@ -207,26 +211,55 @@ __global__ void __launch_bounds__(128) k_refine_tiled(BatchParams p, int steps, 
     V* As = reinterpret_cast<V*>(smem_raw + (size_t)w * refine_tiled_warp_bytes<V>());
     V* Xs = As + kRB * kRLD;
     V* Es = Xs + kRB * kRLD;
+    V* RawA = Es + kRB * kRLD;
+    V* RawX = RawA + kRB * kRB;
     const V* A = static_cast<const V*>(p.A);
     V* X = static_cast<V*>(p.X);
     const int r0 = (lane / 4) * 4, c0 = (lane % 4) * 8;
-
-    for (int b = blockIdx.x * wpc + w; b < p.batch; b += gridDim.x * wpc) {
-        const int n = p.n ? p.n[b] : N;
-        if (n <= 0 || n > N) continue;
-        if (p.info && p.info[b] != 0) continue;
-        const int64_t o = p.off ? p.off[b] : (int64_t)b * (p.layout ? tri64(N) : (int64_t)N * N);
-        auto gidx = [&](int i, int j) { return p.layout ? (int64_t)pidx(n, i, j) : (int64_t)i * n + j; };
-        __syncwarp();  // the previous matrix's squares are no longer read
-        if (n < kRB) {
-            // the zero padding rows and columns n..kRB-1 (the products run over kRB)
-            for (int e = lane; e < kRB * kRB; e += 32) {
-                const int i = e / kRB, j = e % kRB;
-                if (i >= n || j >= n) As[i * kRLD + j] = Xs[i * kRLD + j] = zero_v<V>();
+    // matrix b's order (0: nothing to refine) and element offset
+    auto geom = [&](int b, int& n, int64_t& o) {
+        n = p.n ? p.n[b] : N;
+        if (n <= 0 || n > N || (p.info && p.info[b] != 0)) n = 0;
+        o = p.off ? p.off[b] : (int64_t)b * (p.layout ? tri64(N) : (int64_t)N * N);
+    };
+    // matrix b's A and X as stored, into RawA / RawX (asynchronous)
+    auto prefetch = [&](int b) {
+        if (b < p.batch) {
+            int n;
+            int64_t o;
+            geom(b, n, o);
+            if (n > 0) {
+                const int count = p.layout ? n * (n + 1) / 2 : n * n;
+                warp_copy_async(RawA, A + o, count, lane);
+                warp_copy_async(RawX, static_cast<const V*>(X) + o, count, lane);
             }
         }
-        stage_hermitian(A + o, n, p.layout, As, kRLD, lane);
-        stage_hermitian(static_cast<const V*>(X) + o, n, p.layout, Xs, kRLD, lane);
+        cp_async_commit();
+    };
+    const int stride = gridDim.x * wpc;
+    int b = blockIdx.x * wpc + w;
+    prefetch(b);
+    for (; b < p.batch; b += stride) {
+        int n;
+        int64_t o;
+        geom(b, n, o);
+        cp_async_wait<0>();
+        __syncwarp();  // every lane's copies are visible; the previous matrix's squares are no longer read
+        if (n > 0) {
+            if (n < kRB) {
+                // the zero padding rows and columns n..kRB-1 (the products run over kRB)
+                for (int e = lane; e < kRB * kRB; e += 32) {
+                    const int i = e / kRB, j = e % kRB;
+                    if (i >= n || j >= n) As[i * kRLD + j] = Xs[i * kRLD + j] = zero_v<V>();
+                }
+            }
+            unpack_hermitian(RawA, n, p.layout, As, kRLD, lane);
+            unpack_hermitian(RawX, n, p.layout, Xs, kRLD, lane);
+        }
+        __syncwarp();  // the stored copies are read: the next matrix's may land there
+        prefetch(b + stride);
+        if (n == 0) continue;
+        auto gidx = [&](int i, int j) { return p.layout ? (int64_t)pidx(n, i, j) : (int64_t)i * n + j; };
         int todo = steps;
 #pragma unroll 1
         for (int s = 0; s <= todo; ++s) {
@@ -257,23 +290,13 @@ __global__ void __launch_bounds__(128) k_refine_tiled(BatchParams p, int steps, 
                 for (int c = 0; c < 8; ++c) Es[(r0 + r) * kRLD + c0 + c] = et.value(r, c);
             __syncwarp();
             // X + X E, upper half written back
+            // (X's rows from its conjugate columns: X Hermitian)
             V acc[4][8];
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
                 for (int c = 0; c < 8; ++c) acc[r][c] = Xs[(r0 + r) * kRLD + c0 + c];
-#pragma unroll 4
-            for (int k = 0; k < kRB; ++k) {
-                V a[4], bb[8];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) a[r] = conj_v(Xs[k * kRLD + r0 + r]);
-#pragma unroll
-                for (int c = 0; c < 8; ++c) bb[c] = Es[k * kRLD + c0 + c];
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) acc[r][c] = fma_v(a[r], bb[c], acc[r][c]);
-            }
+            tile_product<V, true>(Xs, Es, r0, c0, acc);
             __syncwarp();  // every lane has read X: its square now takes the new X (mirrored upper half)
 #pragma unroll
             for (int r = 0; r < 4; ++r)
@@ -288,7 +311,6 @@ __global__ void __launch_bounds__(128) k_refine_tiled(BatchParams p, int steps, 
                     }
                 }
         }
-        __syncwarp();
     }
 }
 
@@ -296,7 +318,7 @@ template <typename V>
 static cudaError_t launch_refine_tiled(const BatchParams& p, int steps, int automatic, cudaStream_t s, bool dry) {
     static std::once_flag once;
     static cudaError_t setup = cudaSuccess;
-    constexpr int warps = 4;
+    constexpr int warps = sizeof(V) == 4 ? 4 : 2;
     const size_t smem = refine_tiled_warp_bytes<V>() * warps;
     std::call_once(once, [&] {
         setup = cudaFuncSetAttribute(k_refine_tiled<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

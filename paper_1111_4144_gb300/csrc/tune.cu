@@ -128,6 +128,18 @@ chol_status_t chol_autotune(chol_dtype_t dt, int32_t max_n, int32_t layout, int3
     void *A = nullptr, *X = nullptr;
     if (cudaMalloc(&A, (size_t)batch * per * es) != cudaSuccess) return CHOL_ERR_CUDA;
     if (cudaMalloc(&X, (size_t)batch * per * es) != cudaSuccess) { cudaFree(A); return CHOL_ERR_CUDA; }
+    // each timed launch starts with L2 overwritten (a memset of twice its
+    // size), so that variants are ranked on HBM-resident batches, as they run
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    const size_t flush_bytes = std::max<size_t>(2 * (size_t)std::max(l2, 0), 1 << 20);
+    void* flush = nullptr;
+    if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+        cudaFree(A);
+        cudaFree(X);
+        return CHOL_ERR_CUDA;
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -154,14 +166,18 @@ chol_status_t chol_autotune(chol_dtype_t dt, int32_t max_n, int32_t layout, int3
             g_variant[dt][n].store(v);
             for (int w = 0; w < 2; ++w)
                 if (launch_one(dt, p, n, s) != cudaSuccess) st = CHOL_ERR_CUDA;
-            cudaEventRecord(e0, s);
             const int reps = 5;
-            for (int r = 0; r < reps; ++r)
-                if (launch_one(dt, p, n, s) != cudaSuccess) st = CHOL_ERR_CUDA;
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) st = CHOL_ERR_CUDA;
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            for (int r = 0; r < reps; ++r) {
+                if (cudaMemsetAsync(flush, r & 0xff, flush_bytes, s) != cudaSuccess) st = CHOL_ERR_CUDA;
+                cudaEventRecord(e0, s);
+                if (launch_one(dt, p, n, s) != cudaSuccess) st = CHOL_ERR_CUDA;
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) st = CHOL_ERR_CUDA;
+                float one = 0.f;
+                cudaEventElapsedTime(&one, e0, e1);
+                ms += one;
+            }
             ms /= reps;
             times += " " + std::to_string(ms * 1000.f);
             if (ms < best_ms) { best_ms = ms; best = v; }
@@ -171,6 +187,7 @@ chol_status_t chol_autotune(chol_dtype_t dt, int32_t max_n, int32_t layout, int3
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaFree(flush);
     cudaFree(A);
     cudaFree(X);
     if (st == CHOL_OK && cache_path && cache_path[0]) {
