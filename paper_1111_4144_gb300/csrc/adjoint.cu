@@ -101,8 +101,7 @@ __global__ void k_backward(BwdParams p) {
 
 template <typename V>
 CHOL_HD size_t bwd_tiled_warp_bytes() {
-    // Xs, St, Ts; then the next matrix's G and X as stored (asynchronous copies)
-    return (size_t)3 * kTB * kTLD * sizeof(V) + (size_t)2 * kTB * kTB * sizeof(V);
+    return (size_t)3 * kTB * kTLD * sizeof(V);
 }
 
 
@@ -114,62 +113,39 @@ __global__ void __launch_bounds__(128) k_backward_tiled(BwdParams p) {
     V* Xs = reinterpret_cast<V*>(smem_raw + (size_t)w * bwd_tiled_warp_bytes<V>());
     V* St = Xs + kTB * kTLD;
     V* Ts = St + kTB * kTLD;
-    V* RawG = Ts + kTB * kTLD;
-    V* RawX = RawG + kTB * kTB;
     const V* X = static_cast<const V*>(p.X);
     const V* G = static_cast<const V*>(p.G);
     V* dA = static_cast<V*>(p.dA);
     const int r0 = (lane / 4) * 4, c0 = (lane % 4) * 8;
     const int N = p.max_n;
-    // matrix b's order (0: nothing to do) and the offsets of G / dA and of X
-    auto geom = [&](int b, int& n, int64_t& og, int64_t& ox) {
-        n = p.n ? p.n[b] : N;
-        if (n <= 0 || n > N) n = 0;
-        og = p.off ? p.off[b] : (int64_t)b * N * N;
-        ox = p.xoff ? p.xoff[b] : (int64_t)b * (p.layout ? tri64(N) : (int64_t)N * N);
-    };
-    // matrix b's G and X as stored, into RawG / RawX (asynchronous)
-    auto prefetch = [&](int b) {
-        if (b < p.batch) {
-            int n;
-            int64_t og, ox;
-            geom(b, n, og, ox);
-            if (n > 0) {
-                warp_copy_async(RawG, G + og, n * n, lane);
-                warp_copy_async(RawX, X + ox, p.layout ? n * (n + 1) / 2 : n * n, lane);
+    for (int b = blockIdx.x * wpc + w; b < p.batch; b += gridDim.x * wpc) {
+        const int n = p.n ? p.n[b] : N;
+        if (n <= 0 || n > N) continue;
+        const int64_t og = p.off ? p.off[b] : (int64_t)b * N * N;
+        const int64_t ox = p.xoff ? p.xoff[b] : (int64_t)b * (p.layout ? tri64(N) : (int64_t)N * N);
+        __syncwarp();  // the previous matrix's squares are no longer read
+        if (n < kTB) {
+            // the zero padding rows and columns n..kTB-1 (the products run over kTB)
+            for (int e = lane; e < kTB * kTB; e += 32) {
+                const int i = e / kTB, j = e % kTB;
+                if (i >= n || j >= n) Xs[i * kTLD + j] = St[i * kTLD + j] = zero_v<V>();
             }
         }
-        cp_async_commit();
-    };
-    const int stride = gridDim.x * wpc;
-    int b = blockIdx.x * wpc + w;
-    prefetch(b);
-    for (; b < p.batch; b += stride) {
-        int n;
-        int64_t og, ox;
-        geom(b, n, og, ox);
-        cp_async_wait<0>();
-        __syncwarp();  // every lane's copies are visible; the previous matrix's squares are no longer read
-        if (n > 0) {
-            if (n < kTB) {
-                // the zero padding rows and columns n..kTB-1 (the products run over kTB)
-                for (int e = lane; e < kTB * kTB; e += 32) {
-                    const int i = e / kTB, j = e % kTB;
-                    if (i >= n || j >= n) Xs[i * kTLD + j] = St[i * kTLD + j] = zero_v<V>();
-                }
-            }
-            // X in full from its upper half; St[k][r] = s_rk = (g_rk + conj(g_kr)) / 2
-            unpack_hermitian(RawX, n, p.layout, Xs, kTLD, lane);
-            for (int e = lane; e < n * n; e += 32) {
-                const int k = e / n, r = e - k * n;
-                V sv = scale_v(RawG[r * n + k] + conj_v(RawG[k * n + r]), R(0.5));
-                if (k == r) sv = from_real<V>(re_of(sv));
-                St[k * kTLD + r] = sv;
-            }
+        // G staged in Ts; X in full from its upper half
+        warp_gather(G + og, n * n, lane, [&](int e, V v) {
+            const int k = e / n, r = e - k * n;
+            Ts[k * kTLD + r] = v;
+        });
+        stage_hermitian(X + ox, n, p.layout, Xs, kTLD, lane);
+        __syncwarp();
+        // St[k][r] = s_rk = (g_rk + conj(g_kr)) / 2
+        for (int e = lane; e < n * n; e += 32) {
+            const int k = e / n, r = e - k * n;
+            V sv = scale_v(Ts[r * kTLD + k] + conj_v(Ts[k * kTLD + r]), R(0.5));
+            if (k == r) sv = from_real<V>(re_of(sv));
+            St[k * kTLD + r] = sv;
         }
-        __syncwarp();  // the stored copies are read: the next matrix's may land there
-        prefetch(b + stride);
-        if (n == 0) continue;
+        __syncwarp();
         V acc[4][8];
         // T = S X
 #pragma unroll
@@ -209,7 +185,7 @@ template <typename V>
 static cudaError_t launch_bwd_tiled(const BwdParams& p, cudaStream_t s, bool dry) {
     static std::once_flag once;
     static cudaError_t setup = cudaSuccess;
-    constexpr int warps = sizeof(V) == 4 ? 4 : 2;
+    constexpr int warps = 4;
     const size_t smem = bwd_tiled_warp_bytes<V>() * warps;
     std::call_once(once, [&] {
         setup = cudaFuncSetAttribute(k_backward_tiled<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
