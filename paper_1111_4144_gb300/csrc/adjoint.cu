@@ -13,7 +13,7 @@
 #include <type_traits>
 
 #include "batched.cuh"
-#include "tile32.cuh"
+#include "tile.cuh"
 #include "dispatch.h"
 
 namespace cholinv {

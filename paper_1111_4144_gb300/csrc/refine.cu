@@ -18,7 +18,7 @@
 
 #include "batched.cuh"
 #include "dispatch.h"
-#include "tile32.cuh"
+#include "tile.cuh"
 
 namespace cholinv {
 
@@ -126,48 +126,46 @@ __global__ void k_refine(BatchParams p, int steps, int automatic) {
 }
 
 // ---------------------------------------------------------------------------
-// Register-tiled form for orders up to 32 (zero-padded to 32), compensated
-// FP32 residual: one warp per matrix; lane l holds the 4 x 8 block at rows
-// 4 (l / 4).., columns 8 (l % 4).. of E = I - A X (compensated pairs, two
-// entries or the two parts of a complex entry per paired FP32 instruction)
-// and then of the correction X E (plain FP32).  A, X and E are full 32 x 32
-// squares in shared memory (row stride 36); the left operands' 4-row slices
-// come from their conjugate-transposed rows (both are Hermitian).
+// Register-tiled form for orders up to 32, compensated FP32 residual: one
+// warp per matrix, the matrix zero-padded to a square of order TB (16 for
+// orders up to 16, else 32); lane l holds the TR x TC block (4 x 8 or
+// 2 x 4) at rows TR (l / 4).., columns TC (l % 4).. of E = I - A X
+// (compensated pairs, two entries or the two parts of a complex entry per
+// paired FP32 instruction) and then of the correction X E (plain FP32).
+// A, X and E are full squares in shared memory (row stride TB + 4); the
+// left operands' row slices come from their conjugate-transposed rows (both
+// are Hermitian).
 // ---------------------------------------------------------------------------
-constexpr int kRB = 32;
-constexpr int kRLD = kRB + 4;
-static_assert(kRB == kTB && kRLD == kTLD, "the correction runs on the adjoint's tile product");
-
 // A, X and E as padded squares, then the next matrix's A and X as stored
 // (dense or packed), filled by asynchronous copies during this one's steps.
-template <typename V>
+template <typename V, int TB>
 CHOL_HD size_t refine_tiled_warp_bytes() {
-    return (size_t)3 * kRB * kRLD * sizeof(V) + (size_t)2 * kRB * kRB * sizeof(V);
+    return (size_t)3 * TB * Tile<TB>::LD * sizeof(V) + (size_t)2 * TB * TB * sizeof(V);
 }
 
 // acc += a b with a, b real (paired lanes: two entries of a row) or complex
-// (paired lanes: the real and imaginary parts of one entry)
-template <typename V>
+// (paired lanes: the real and imaginary parts of one entry), over a TR x TC block
+template <typename V, int TR, int TC>
 struct ResidTile;
-template <>
-struct ResidTile<float> {
-    f2acc2 acc[4][4];  // [row][column pair]
+template <int TR, int TC>
+struct ResidTile<float, TR, TC> {
+    f2acc2 acc[TR][TC / 2];  // [row][column pair]
     CHOL_D void init(int r0, int c0) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < TR; ++r)
 #pragma unroll
-            for (int cp = 0; cp < 4; ++cp) {
+            for (int cp = 0; cp < TC / 2; ++cp) {
                 const int i = r0 + r, j = c0 + 2 * cp;
                 acc[r][cp].s = make_float2(i == j ? 1.f : 0.f, i == j + 1 ? 1.f : 0.f);
                 acc[r][cp].c = make_float2(0.f, 0.f);
             }
     }
     // acc[r][c] -= a_r b_c over one k
-    CHOL_D void step(const float (&a)[4], const float (&b)[8]) {
+    CHOL_D void step(const float (&a)[TR], const float (&b)[TC]) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < TR; ++r)
 #pragma unroll
-            for (int cp = 0; cp < 4; ++cp)
+            for (int cp = 0; cp < TC / 2; ++cp)
                 f2_fma2(acc[r][cp], make_float2(-a[r], -a[r]), make_float2(b[2 * cp], b[2 * cp + 1]));
     }
     CHOL_D float value(int r, int c) const {
@@ -175,24 +173,24 @@ struct ResidTile<float> {
         return (c & 1) ? __fadd_rn(q.s.y, q.c.y) : __fadd_rn(q.s.x, q.c.x);
     }
 };
-template <>
-struct ResidTile<cpx<float>> {
-    f2acc2 acc[4][8];  // lanes x, y: real and imaginary parts
+template <int TR, int TC>
+struct ResidTile<cpx<float>, TR, TC> {
+    f2acc2 acc[TR][TC];  // lanes x, y: real and imaginary parts
     CHOL_D void init(int r0, int c0) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < TR; ++r)
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
+            for (int c = 0; c < TC; ++c) {
                 acc[r][c].s = make_float2(r0 + r == c0 + c ? 1.f : 0.f, 0.f);
                 acc[r][c].c = make_float2(0.f, 0.f);
             }
     }
     // (a b).re = a.re b.re - a.im b.im, (a b).im = a.re b.im + a.im b.re; subtracted
-    CHOL_D void step(const cpx<float> (&a)[4], const cpx<float> (&b)[8]) {
+    CHOL_D void step(const cpx<float> (&a)[TR], const cpx<float> (&b)[TC]) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < TR; ++r)
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
+            for (int c = 0; c < TC; ++c) {
                 f2_fma2(acc[r][c], make_float2(-a[r].re, -a[r].re), make_float2(b[c].re, b[c].im));
                 f2_fma2(acc[r][c], make_float2(a[r].im, -a[r].im), make_float2(b[c].im, b[c].re));
             }
@@ -203,19 +201,20 @@ struct ResidTile<cpx<float>> {
     }
 };
 
-template <typename V>
+template <typename V, int TB>
 __global__ void __launch_bounds__(128) k_refine_tiled(BatchParams p, int steps, int automatic) {
+    constexpr int LD = Tile<TB>::LD, TR = Tile<TB>::TR, TC = Tile<TB>::TC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = p.max_n;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-    V* As = reinterpret_cast<V*>(smem_raw + (size_t)w * refine_tiled_warp_bytes<V>());
-    V* Xs = As + kRB * kRLD;
-    V* Es = Xs + kRB * kRLD;
-    V* RawA = Es + kRB * kRLD;
-    V* RawX = RawA + kRB * kRB;
+    V* As = reinterpret_cast<V*>(smem_raw + (size_t)w * refine_tiled_warp_bytes<V, TB>());
+    V* Xs = As + TB * LD;
+    V* Es = Xs + TB * LD;
+    V* RawA = Es + TB * LD;
+    V* RawX = RawA + TB * TB;
     const V* A = static_cast<const V*>(p.A);
     V* X = static_cast<V*>(p.X);
-    const int r0 = (lane / 4) * 4, c0 = (lane % 4) * 8;
+    const int r0 = (lane / 4) * TR, c0 = (lane % 4) * TC;
     // matrix b's order (0: nothing to refine) and element offset
     auto geom = [&](int b, int& n, int64_t& o) {
         n = p.n ? p.n[b] : N;
@@ -246,15 +245,15 @@ __global__ void __launch_bounds__(128) k_refine_tiled(BatchParams p, int steps, 
         cp_async_wait<0>();
         __syncwarp();  // every lane's copies are visible; the previous matrix's squares are no longer read
         if (n > 0) {
-            if (n < kRB) {
-                // the zero padding rows and columns n..kRB-1 (the products run over kRB)
-                for (int e = lane; e < kRB * kRB; e += 32) {
-                    const int i = e / kRB, j = e % kRB;
-                    if (i >= n || j >= n) As[i * kRLD + j] = Xs[i * kRLD + j] = zero_v<V>();
+            if (n < TB) {
+                // the zero padding rows and columns n..TB-1 (the products run over TB)
+                for (int e = lane; e < TB * TB; e += 32) {
+                    const int i = e / TB, j = e % TB;
+                    if (i >= n || j >= n) As[i * LD + j] = Xs[i * LD + j] = zero_v<V>();
                 }
             }
-            unpack_hermitian(RawA, n, p.layout, As, kRLD, lane);
-            unpack_hermitian(RawX, n, p.layout, Xs, kRLD, lane);
+            unpack_hermitian(RawA, n, p.layout, As, LD, lane);
+            unpack_hermitian(RawX, n, p.layout, Xs, LD, lane);
         }
         __syncwarp();  // the stored copies are read: the next matrix's may land there
         prefetch(b + stride);
@@ -267,68 +266,69 @@ __global__ void __launch_bounds__(128) k_refine_tiled(BatchParams p, int steps, 
             if (s == 0 && automatic) {
                 double g = 0.0;
                 for (int i = lane; i < n; i += 32)
-                    g = fmax(g, (double)re_of(As[i * kRLD + i]) * (double)re_of(Xs[i * kRLD + i]));
+                    g = fmax(g, (double)re_of(As[i * LD + i]) * (double)re_of(Xs[i * LD + i]));
                 for (int d = 16; d > 0; d >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, d));
                 todo = g > kAutoRefineGamma ? 1 : 0;
             }
             if (s == todo) break;
             // E = I - A X (rows of A from its conjugate: A Hermitian)
-            ResidTile<V> et;
+            ResidTile<V, TR, TC> et;
             et.init(r0, c0);
 #pragma unroll 2
-            for (int k = 0; k < kRB; ++k) {
-                V a[4], bb[8];
+            for (int k = 0; k < TB; ++k) {
+                V a[TR], bb[TC];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) a[r] = conj_v(As[k * kRLD + r0 + r]);
+                for (int r = 0; r < TR; ++r) a[r] = conj_v(As[k * LD + r0 + r]);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) bb[c] = Xs[k * kRLD + c0 + c];
+                for (int c = 0; c < TC; ++c) bb[c] = Xs[k * LD + c0 + c];
                 et.step(a, bb);
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < TR; ++r)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) Es[(r0 + r) * kRLD + c0 + c] = et.value(r, c);
+                for (int c = 0; c < TC; ++c) Es[(r0 + r) * LD + c0 + c] = et.value(r, c);
             __syncwarp();
             // X + X E, upper half written back
             // (X's rows from its conjugate columns: X Hermitian)
-            V acc[4][8];
+            V acc[TR][TC];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < TR; ++r)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) acc[r][c] = Xs[(r0 + r) * kRLD + c0 + c];
-            tile_product<V, true>(Xs, Es, r0, c0, acc);
+                for (int c = 0; c < TC; ++c) acc[r][c] = Xs[(r0 + r) * LD + c0 + c];
+            tile_product<V, true, TB>(Xs, Es, r0, c0, acc);
             __syncwarp();  // every lane has read X: its square now takes the new X (mirrored upper half)
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < TR; ++r)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
+                for (int c = 0; c < TC; ++c) {
                     const int i = r0 + r, j = c0 + c;
                     if (i <= j && j < n) {
                         const V x = (i == j) ? from_real<V>(re_of(acc[r][c])) : acc[r][c];
                         X[o + gidx(i, j)] = x;
-                        Xs[i * kRLD + j] = x;
-                        Xs[j * kRLD + i] = conj_v(x);
+                        Xs[i * LD + j] = x;
+                        Xs[j * LD + i] = conj_v(x);
                     }
                 }
         }
     }
 }
 
-template <typename V>
+template <typename V, int TB>
 static cudaError_t launch_refine_tiled(const BatchParams& p, int steps, int automatic, cudaStream_t s, bool dry) {
     static std::once_flag once;
     static cudaError_t setup = cudaSuccess;
-    constexpr int warps = sizeof(V) == 4 ? 4 : 2;
-    const size_t smem = refine_tiled_warp_bytes<V>() * warps;
+    constexpr int warps = (sizeof(V) == 4 || TB == 16) ? 4 : 2;
+    const size_t smem = refine_tiled_warp_bytes<V, TB>() * warps;
+    auto kern = k_refine_tiled<V, TB>;
     std::call_once(once, [&] {
-        setup = cudaFuncSetAttribute(k_refine_tiled<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        setup = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     });
     if (setup != cudaSuccess || dry) return setup;
     int per_sm = 1;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine_tiled<V>, 32 * warps, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, smem);
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, std::min((p.batch + warps - 1) / warps, device_info().sms * std::max(per_sm, 1)));
-    k_refine_tiled<V><<<grid, 32 * warps, smem, s>>>(p, steps, automatic);
+    kern<<<grid, 32 * warps, smem, s>>>(p, steps, automatic);
     return cudaGetLastError();
 }
 
@@ -354,7 +354,8 @@ static cudaError_t launch_refine_r(const BatchParams& p, int steps, int automati
 template <typename V>
 static cudaError_t launch_refine_t(const BatchParams& p, int steps, int automatic, cudaStream_t s, bool dry) {
     if (p.flags & CHOL_FLAG_RESIDUAL_FP64) return launch_refine_r<V, true>(p, steps, automatic, s, dry);
-    if (p.max_n <= kRB) return launch_refine_tiled<V>(p, steps, automatic, s, dry);
+    if (p.max_n <= 16) return launch_refine_tiled<V, 16>(p, steps, automatic, s, dry);
+    if (p.max_n <= 32) return launch_refine_tiled<V, 32>(p, steps, automatic, s, dry);
     return launch_refine_r<V, false>(p, steps, automatic, s, dry);
 }
 

@@ -24,7 +24,7 @@ def _full(Xu):
 
 
 @pytest.mark.parametrize("resid64", [False, True])
-@pytest.mark.parametrize("N", [8, 16, 40])
+@pytest.mark.parametrize("N", [8, 16, 17, 32, 40])
 def test_refinement_steps_reduce_error(orc, N, resid64):
     """Refinement with the residual in compensated FP32 pairs (default) or
     in FP64 (CHOL_FLAG_RESIDUAL_FP64): each step cuts the error tenfold or
@@ -175,7 +175,7 @@ def test_autograd_fp32_against_fp64_central_differences(orc):
             assert abs(fd - an) <= (2 * tol32(1e2) + 32 * U32) * max(abs(fd), 1.0), (fd, an)
 
 
-@pytest.mark.parametrize("N", [6, 16, 33])
+@pytest.mark.parametrize("N", [6, 16, 24, 33])
 def test_refinement_complex_both_residuals(orc, N):
     """Complex64 refinement, both residual forms, against the oracle."""
     from paper_1111_4144_gb300 import _lib as L
@@ -188,3 +188,21 @@ def test_refinement_complex_both_residuals(orc, N):
         assert np.all(info == 0)
         e = upper_errors(b, X, Xo)
         assert np.all(e <= np.maximum(e0 / 10, 64 * U32)), (flags, e.max(), e0.max())
+
+
+@pytest.mark.parametrize("tag,nmax", [("f32", 16), ("f32", 32), ("c64", 16), ("c64", 32)])
+def test_refinement_mixed_orders(orc, tag, nmax):
+    """Refinement of a batch of mixed orders 1..nmax (the order-16 and
+    order-32 tiles, zero padding of every smaller order, packed layout): two
+    steps reach FP32 accuracy or cut the error tenfold, matrix by matrix."""
+    from paper_1111_4144_gb300 import _lib as L
+    b = wl.uneven_loguniform(300, nmin=1, nmax=nmax, decades=3.0, seed=90 + nmax, layout=1)
+    if tag == "c64":
+        b = wl.Batch(b.A.astype(np.complex128), b.n, b.off, b.layout)
+    _, Xo, _, A_wide = oracle_inv(orc, b, tag)
+    X0, _, _ = run_inv(b, tag, mixed=True)
+    X, info, _ = run_inv(b, tag, mixed=True, prec=L.CHOL_PREC_FP32_REFINE, refine_steps=2)
+    assert np.all(info == 0)
+    e0 = upper_errors(b, X0, Xo)
+    e = upper_errors(b, X, Xo)
+    assert np.all(e <= np.maximum(e0 / 10, 64 * U32)), (e.max(), e0.max())
