@@ -45,10 +45,7 @@ __global__ void k_backward(BwdParams p) {
         __syncwarp();  // the previous matrix's squares are no longer read
         stage_hermitian(X + ox, n, p.layout, Xf, LD, lane);
         // G into Tf (free until T = S X), then S = (G + G^H)/2 into Sf
-        warp_gather(G + og, n * n, lane, [&](int e, V v) {
-            const int i = e / n, j = e - i * n;
-            Tf[i * LD + j] = v;
-        });
+        warp_rows<false>(G + og, n, n, 0, lane, [&](int i, int j, V v) { Tf[i * LD + j] = v; });
         __syncwarp();
         for (int i = 0; i < n; ++i)
             for (int j = i + lane; j < n; j += 32) {
@@ -126,24 +123,25 @@ __global__ void __launch_bounds__(128) k_backward_tiled(BwdParams p) {
         __syncwarp();  // the previous matrix's squares are no longer read
         if (n < kTB) {
             // the zero padding rows and columns n..kTB-1 (the products run over kTB)
-            for (int e = lane; e < kTB * kTB; e += 32) {
-                const int i = e / kTB, j = e % kTB;
-                if (i >= n || j >= n) Xs[i * kTLD + j] = St[i * kTLD + j] = zero_v<V>();
-            }
+            for (int i = 0; i < kTB; ++i)
+                if (i >= n || lane >= n) Xs[i * kTLD + lane] = St[i * kTLD + lane] = zero_v<V>();
         }
-        // G staged in Ts; X in full from its upper half
-        warp_gather(G + og, n * n, lane, [&](int e, V v) {
-            const int k = e / n, r = e - k * n;
-            Ts[k * kTLD + r] = v;
+        // G staged in Ts; X in full from its upper half (lanes over columns)
+        warp_rows<false>(G + og, n, n, 0, lane, [&](int i, int j, V v) { Ts[i * kTLD + j] = v; });
+        warp_rows<true>(X + ox, n, n, p.layout, lane, [&](int i, int j, V v) {
+            const V x = (i == j) ? from_real<V>(re_of(v)) : v;
+            Xs[i * kTLD + j] = x;
+            Xs[j * kTLD + i] = conj_v(x);
         });
-        stage_hermitian(X + ox, n, p.layout, Xs, kTLD, lane);
         __syncwarp();
-        // St[k][r] = s_rk = (g_rk + conj(g_kr)) / 2
-        for (int e = lane; e < n * n; e += 32) {
-            const int k = e / n, r = e - k * n;
-            V sv = scale_v(Ts[r * kTLD + k] + conj_v(Ts[k * kTLD + r]), R(0.5));
-            if (k == r) sv = from_real<V>(re_of(sv));
-            St[k * kTLD + r] = sv;
+        // St[k][r] = s_rk = (g_rk + conj(g_kr)) / 2, lanes over k
+        if (lane < n) {
+            for (int r = 0; r < n; ++r) {
+                const int k = lane;
+                V sv = scale_v(Ts[r * kTLD + k] + conj_v(Ts[k * kTLD + r]), R(0.5));
+                if (k == r) sv = from_real<V>(re_of(sv));
+                St[k * kTLD + r] = sv;
+            }
         }
         __syncwarp();
         V acc[4][8];
@@ -170,12 +168,15 @@ __global__ void __launch_bounds__(128) k_backward_tiled(BwdParams p) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) St[(r0 + r) * kTLD + c0 + c] = zero_v<V>() - acc[r][c];
         __syncwarp();
-        for (int e = lane; e < n * n; e += 32) {
-            const int i = e / n, j = e - i * n;
-            V d = (i <= j) ? St[i * kTLD + j] : conj_v(St[j * kTLD + i]);
-            if (i == j) d = from_real<V>(re_of(d));
-            if (p.flags & CHOL_FLAG_GRAD_UPPER) d = (i < j) ? scale_v(d, R(2)) : (i == j) ? d : zero_v<V>();
-            dA[og + e] = d;
+        const bool upper_param = (p.flags & CHOL_FLAG_GRAD_UPPER) != 0;
+        if (lane < n) {
+            for (int i = 0; i < n; ++i) {
+                const int j = lane;
+                V d = (i <= j) ? St[i * kTLD + j] : conj_v(St[j * kTLD + i]);
+                if (i == j) d = from_real<V>(re_of(d));
+                if (upper_param) d = (i < j) ? scale_v(d, R(2)) : (i == j) ? d : zero_v<V>();
+                dA[og + i * n + j] = d;
+            }
         }
         __syncwarp();
     }
