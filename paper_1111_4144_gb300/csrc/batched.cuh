@@ -559,7 +559,9 @@ CHOL_D void elem_rc(int layout, int n, int e, int& i, int& j) {
 // one warp, lanes over the columns j = lane and lane + 32, eight loads in
 // flight per lane before any is handed on.  UPPER: an order-rows matrix's
 // upper triangle only (j >= i), stored dense or packed (`layout`); else a
-// dense row-major matrix in full.  No index needs a division.
+// dense row-major matrix in full.  No index needs a division, but lanes
+// beyond `cols` idle: for matrices of order near 32 or 64 (warp_gather
+// keeps every lane busy for smaller ones).
 template <bool UPPER, typename V, class F>
 CHOL_D void warp_rows(const V* __restrict__ src, int rows, int cols, int layout, int lane, F&& f) {
     constexpr int U = 4;
@@ -588,10 +590,14 @@ CHOL_D void warp_rows(const V* __restrict__ src, int rows, int cols, int layout,
 // square S (row stride ld) in full: mirrored (conjugated), diagonal real.
 template <typename V>
 CHOL_D void stage_hermitian(const V* __restrict__ src, int n, int layout, V* S, int ld, int lane) {
-    warp_rows<true>(src, n, n, layout, lane, [&](int i, int j, V v) {
-        const V x = (i == j) ? from_real<V>(re_of(v)) : v;
-        S[i * ld + j] = x;
-        S[j * ld + i] = conj_v(x);
+    warp_gather(src, layout ? n * (n + 1) / 2 : n * n, lane, [&](int e, V v) {
+        int i, j;
+        elem_rc(layout, n, e, i, j);
+        if (i <= j) {
+            const V x = (i == j) ? from_real<V>(re_of(v)) : v;
+            S[i * ld + j] = x;
+            S[j * ld + i] = conj_v(x);
+        }
     });
 }
 
@@ -616,15 +622,16 @@ CHOL_D void warp_copy_async(V* dst, const V* src, int count, int lane) {
 // (conjugated), diagonal real.
 template <typename V>
 CHOL_D void unpack_hermitian(const V* raw, int n, int layout, V* S, int ld, int lane) {
-    for (int i = 0; i < n; ++i)
-        for (int j = lane; j < n; j += 32) {
-            if (j >= i) {
-                const V v = raw[layout ? pidx(n, i, j) : i * n + j];
-                const V x = (i == j) ? from_real<V>(re_of(v)) : v;
-                S[i * ld + j] = x;
-                S[j * ld + i] = conj_v(x);
-            }
+    const int count = layout ? n * (n + 1) / 2 : n * n;
+    for (int e = lane; e < count; e += 32) {
+        int i, j;
+        elem_rc(layout, n, e, i, j);
+        if (i <= j) {
+            const V x = (i == j) ? from_real<V>(re_of(raw[e])) : raw[e];
+            S[i * ld + j] = x;
+            S[j * ld + i] = conj_v(x);
         }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -643,7 +650,11 @@ CHOL_D void warp_one(const BatchParams& p, int N, int64_t b, int64_t o, V* S, in
     V* Xo = static_cast<V*>(p.X);
     V* Ro = static_cast<V*>(p.R);
     // load the upper triangle
-    warp_rows<true>(A + o, N, N, p.layout, lane, [&](int i, int j, V v) { S[i * LD + j] = v; });
+    warp_gather(A + o, p.layout ? tri(N) : N * N, lane, [&](int e, V v) {
+        int i, j;
+        elem_rc(p.layout, N, e, i, j);
+        if (i <= j) S[i * LD + j] = v;
+    });
     __syncwarp();
     // ---- factor, Eqs. 3-4, row by row; with CHOL_FLAG_LDL the LDL form of
     // Sec. II.A (Eqs. 9-11): d_i = a_ii - sum |r_ki|^2 d_k and

@@ -80,9 +80,14 @@ __global__ void k_apply(MmseParams p) {
         const bool bad = p.info && p.info[b] != 0;
         __syncwarp();  // the previous matrix's H and X are no longer read
         // H transposed (row stride m + 1), so that lanes over k read consecutive words below
-        warp_rows<false>(H + oh, m, n, 0, lane, [&](int r, int c, V v) { Ht[c * (m + 1) + r] = v; });
+        warp_gather(H + oh, m * n, lane, [&](int e, V v) {
+            const int r = e / n, c = e - r * n;
+            Ht[c * (m + 1) + r] = v;
+        });
         const int LD = n + 1;
-        warp_rows<true>(X + oa, n, n, 1, lane, [&](int i, int j, V x) {
+        warp_gather(X + oa, tri(n), lane, [&](int e, V x) {
+            int i, j;
+            tri_rc(n, e, i, j);
             Xs[i * LD + j] = x;
             Xs[j * LD + i] = conj_v(x);
         });
