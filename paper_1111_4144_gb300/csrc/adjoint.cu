@@ -127,8 +127,9 @@ __global__ void __launch_bounds__(128) k_backward_tiled(BwdParams p) {
                 if (i >= n || lane >= n) Xs[i * kTLD + lane] = St[i * kTLD + lane] = zero_v<V>();
         }
         // G staged in Ts; X in full from its upper half (lanes over columns)
-        warp_rows<false>(G + og, n, n, 0, lane, [&](int i, int j, V v) { Ts[i * kTLD + j] = v; });
-        warp_rows<true>(X + ox, n, n, p.layout, lane, [&](int i, int j, V v) {
+        constexpr int U = sizeof(V) == 4 ? 16 : 8;  // rows a round: the loads in flight per lane
+        warp_rows<false, 1, U>(G + og, n, n, 0, lane, [&](int i, int j, V v) { Ts[i * kTLD + j] = v; });
+        warp_rows<true, 1, U>(X + ox, n, n, p.layout, lane, [&](int i, int j, V v) {
             const V x = (i == j) ? from_real<V>(re_of(v)) : v;
             Xs[i * kTLD + j] = x;
             Xs[j * kTLD + i] = conj_v(x);

@@ -555,23 +555,22 @@ CHOL_D void elem_rc(int layout, int n, int e, int& i, int& j) {
     }
 }
 
-// f(i, j, element (i, j)) over a rows x cols matrix at src (cols <= 64) by
-// one warp, lanes over the columns j = lane and lane + 32, eight loads in
-// flight per lane before any is handed on.  UPPER: an order-rows matrix's
-// upper triangle only (j >= i), stored dense or packed (`layout`); else a
-// dense row-major matrix in full.  No index needs a division, but lanes
-// beyond `cols` idle: for matrices of order near 32 or 64 (warp_gather
-// keeps every lane busy for smaller ones).
-template <bool UPPER, typename V, class F>
+// f(i, j, element (i, j)) over a rows x cols matrix at src by one warp,
+// lanes over the columns j = lane + 32 h (h < NS, so cols <= 32 NS), U rows
+// a round with every load of the round in flight before any is handed on.
+// UPPER: an order-rows matrix's upper triangle only (j >= i), stored dense
+// or packed (`layout`); else a dense row-major matrix in full.  No index
+// needs a division, but lanes beyond `cols` idle: for matrices of order
+// near 32 or 64 (warp_gather keeps every lane busy for smaller ones).
+template <bool UPPER, int NS = 2, int U = 4, typename V, class F>
 CHOL_D void warp_rows(const V* __restrict__ src, int rows, int cols, int layout, int lane, F&& f) {
-    constexpr int U = 4;
 #pragma unroll 1
     for (int i0 = 0; i0 < rows; i0 += U) {
-        V v[U][2];
+        V v[U][NS];
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < NS; ++h) {
                 const int i = i0 + u, j = lane + 32 * h;
                 if (i < rows && j < cols && (!UPPER || j >= i))
                     v[u][h] = src[(UPPER && layout) ? pidx(cols, i, j) : i * cols + j];
@@ -579,7 +578,7 @@ CHOL_D void warp_rows(const V* __restrict__ src, int rows, int cols, int layout,
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < NS; ++h) {
                 const int i = i0 + u, j = lane + 32 * h;
                 if (i < rows && j < cols && (!UPPER || j >= i)) f(i, j, v[u][h]);
             }
