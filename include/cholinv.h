@@ -272,6 +272,7 @@ chol_status_t chol_inv_backward(chol_dtype_t dt, int32_t batch, const int32_t* n
  * and the host buffers must stay valid and unmodified until then.
  * ws: device workspace of chol_workspace_bytes(CHOL_CALL_INV_HOST, dt,
  * batch, max_n, n_host != NULL, opts) bytes, 256-byte aligned (it holds the
+ * whole batch's orders, offsets and info, each copied in one piece, and the
  * four slots).  Concurrent calls on one device serialise their enqueueing.
  */
 chol_status_t chol_inv_batched_host(chol_dtype_t dt, int32_t batch, const int32_t* n_host, const int64_t* off_host,

@@ -397,20 +397,29 @@ int64_t host_chunk_matrices(int32_t batch) {
 size_t elem_size(chol_dtype_t dt) { return dt == CHOL_F32 ? 4 : dt == CHOL_C128 ? 16 : 8; }
 int64_t matrix_elems(int layout, int64_t n) { return layout ? n * (n + 1) / 2 : n * n; }
 
+// The workspace of the host path: the whole batch's orders, offsets and
+// info (each copied in one piece: per-chunk copies of a few hundred KB cost
+// more in copy-engine and event latency than in bytes), then kHostSlots
+// slots of A, X and the bucketing workspace for one chunk.
 struct HostSlotLayout {
-    size_t a, x, n, off, info, ws, total;  // byte offsets within one slot
+    size_t n, off, info;     // byte offsets of the whole-batch arrays
+    size_t slots;            // byte offset of the first slot
+    size_t a, x, ws, total;  // byte offsets within one slot, and its size
+    size_t bytes;            // the whole workspace
 };
 HostSlotLayout host_slot_layout(chol_dtype_t dt, int32_t batch, int32_t max_n, int layout, bool has_sizes) {
     const int64_t mc = host_chunk_matrices(batch);
     const size_t data = align_up((size_t)mc * matrix_elems(layout, max_n) * elem_size(dt) + 16, 256);
     HostSlotLayout l;
+    l.n = 0;
+    l.off = l.n + (has_sizes ? align_up((size_t)batch * sizeof(int32_t), 256) : 0);
+    l.info = l.off + (has_sizes ? align_up((size_t)batch * sizeof(int64_t), 256) : 0);
+    l.slots = l.info + align_up((size_t)batch * sizeof(int32_t), 256);
     l.a = 0;
     l.x = l.a + data;
-    l.n = l.x + data;
-    l.off = l.n + align_up((size_t)mc * sizeof(int32_t), 256);
-    l.info = l.off + align_up((size_t)mc * sizeof(int64_t), 256);
-    l.ws = l.info + align_up((size_t)mc * sizeof(int32_t), 256);
+    l.ws = l.x + data;
     l.total = l.ws + ws_need_batched((int32_t)mc, has_sizes);
+    l.bytes = l.slots + l.total * kHostSlots;
     return l;
 }
 
@@ -574,7 +583,7 @@ chol_status_t chol_inv_batched_host(chol_dtype_t dt, int32_t batch, const int32_
     if (A_host == nullptr || X_host == nullptr || A_host == X_host) return CHOL_ERR_ARG;
     const bool sized = n_host != nullptr;
     const HostSlotLayout L = host_slot_layout(dt, batch, max_n, o.layout, sized);
-    if (ws == nullptr || ws_bytes < L.total * kHostSlots || reinterpret_cast<uintptr_t>(ws) % 256 != 0)
+    if (ws == nullptr || ws_bytes < L.bytes || reinterpret_cast<uintptr_t>(ws) % 256 != 0)
         return CHOL_ERR_WORKSPACE;
     if (o.layout == 0) o.fill_lower = 1;  // every element of a dense matrix goes back to the host
     const size_t es = elem_size(dt);
@@ -608,9 +617,19 @@ chol_status_t chol_inv_batched_host(chol_dtype_t dt, int32_t batch, const int32_
         if (cudaStreamWaitEvent(st2, hs->fork, 0) != cudaSuccess) return CHOL_ERR_CUDA;
     const char* Ah = static_cast<const char*>(A_host);
     char* Xh = static_cast<char*>(X_host);
+    char* wsb = static_cast<char*>(ws);
+    int32_t* n_dev = reinterpret_cast<int32_t*>(wsb + L.n);
+    int64_t* off_dev = reinterpret_cast<int64_t*>(wsb + L.off);
+    int32_t* info_dev = reinterpret_cast<int32_t*>(wsb + L.info);
+    // the orders and offsets of the whole batch, ahead of the first chunk
+    if (sized && (cudaMemcpyAsync(n_dev, n_host, (size_t)batch * sizeof(int32_t), cudaMemcpyHostToDevice, hs->in) !=
+                      cudaSuccess ||
+                  cudaMemcpyAsync(off_dev, off_host, (size_t)batch * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                  hs->in) != cudaSuccess))
+        return CHOL_ERR_CUDA;
     for (int64_t k = 0; k < nchunks; ++k) {
         const int slot = (int)(k % kHostSlots);
-        char* base = static_cast<char*>(ws) + (size_t)slot * L.total;
+        char* base = wsb + L.slots + (size_t)slot * L.total;
         const int64_t b0 = k * mc;
         const int32_t cnt = (int32_t)(std::min<int64_t>(b0 + mc, batch) - b0);
         int64_t e0, e1;
@@ -625,22 +644,14 @@ chol_status_t chol_inv_batched_host(chol_dtype_t dt, int32_t batch, const int32_
         if (cudaMemcpyAsync(base + L.a, Ah + e0 * (int64_t)es - pad, bytes + pad, cudaMemcpyHostToDevice, hs->in) !=
             cudaSuccess)
             return CHOL_ERR_CUDA;
-        if (sized) {
-            if (cudaMemcpyAsync(base + L.n, n_host + b0, (size_t)cnt * sizeof(int32_t), cudaMemcpyHostToDevice,
-                                hs->in) != cudaSuccess ||
-                cudaMemcpyAsync(base + L.off, off_host + b0, (size_t)cnt * sizeof(int64_t), cudaMemcpyHostToDevice,
-                                hs->in) != cudaSuccess)
-                return CHOL_ERR_CUDA;
-        }
         if (cudaEventRecord(hs->loaded[k], hs->in) != cudaSuccess) return CHOL_ERR_CUDA;
         // kernels
         if (cudaStreamWaitEvent(hs->run, hs->loaded[k], 0) != cudaSuccess) return CHOL_ERR_CUDA;
         const intptr_t shift = sized ? (intptr_t)(e0 * (int64_t)es) - (intptr_t)pad : 0;
         const void* Ad = reinterpret_cast<const void*>(reinterpret_cast<intptr_t>(base + L.a) - shift);
         void* Xd = reinterpret_cast<void*>(reinterpret_cast<intptr_t>(base + L.x) - shift);
-        BatchParams p = make_params(cnt, sized ? reinterpret_cast<const int32_t*>(base + L.n) : nullptr,
-                                    sized ? reinterpret_cast<const int64_t*>(base + L.off) : nullptr, max_n, Ad,
-                                    nullptr, Xd, reinterpret_cast<int32_t*>(base + L.info), o, 1);
+        BatchParams p = make_params(cnt, sized ? n_dev + b0 : nullptr, sized ? off_dev + b0 : nullptr, max_n, Ad,
+                                    nullptr, Xd, info_dev + b0, o, 1);
         // the orders are in host memory here: launch only the classes that occur
         // (an order outside [0, max_n] is left to the device check, which flags it)
         uint8_t present[kClasses] = {};
@@ -657,11 +668,13 @@ chol_status_t chol_inv_batched_host(chol_dtype_t dt, int32_t batch, const int32_
         if (cudaMemcpyAsync(Xh + e0 * (int64_t)es, base + L.x + pad, bytes, cudaMemcpyDeviceToHost, hs->out) !=
             cudaSuccess)
             return CHOL_ERR_CUDA;
-        if (info_host && cudaMemcpyAsync(info_host + b0, base + L.info, (size_t)cnt * sizeof(int32_t),
-                                         cudaMemcpyDeviceToHost, hs->out) != cudaSuccess)
-            return CHOL_ERR_CUDA;
         if (cudaEventRecord(hs->freed[slot], hs->out) != cudaSuccess) return CHOL_ERR_CUDA;
     }
+    // info of the whole batch, after the last chunk's kernels (the copy-out
+    // stream has waited for them)
+    if (info_host && cudaMemcpyAsync(info_host, info_dev, (size_t)batch * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                     hs->out) != cudaSuccess)
+        return CHOL_ERR_CUDA;
     for (int k = 0; k < 3; ++k)
         if (cudaEventRecord(hs->join[k], stage[k]) != cudaSuccess || cudaStreamWaitEvent(cs, hs->join[k], 0) != cudaSuccess)
             return CHOL_ERR_CUDA;
@@ -680,7 +693,7 @@ size_t chol_workspace_bytes(int32_t call, chol_dtype_t dt, int32_t batch, int32_
     if (call == CHOL_CALL_FACTOR || call == CHOL_CALL_INV) return ws_need_batched(batch, has_sizes);
     if (call == CHOL_CALL_INV_HOST) {
         if (batch <= 0 || max_n < 1 || max_n > kBatchedMaxN || dt < CHOL_F32 || dt > CHOL_C128) return 0;
-        return host_slot_layout(dt, batch, max_n, o.layout, has_sizes != 0).total * kHostSlots;
+        return host_slot_layout(dt, batch, max_n, o.layout, has_sizes != 0).bytes;
     }
     return 0;
 }

@@ -61,6 +61,25 @@ def test_odd_byte_offsets_and_refinement(orc):
     check_errors("f32", b, A_wide, upper_errors(b, X, Xo), "X")
 
 
+def test_info_of_every_chunk(orc):
+    """Non-PD matrices in the first, a middle and the last chunk: info (copied
+    back for the whole batch in one piece) flags exactly those, with the
+    failing row, and their X is NaN; the others match the oracle."""
+    b = wl.mimo_covariance(20011, sizes=(4, 8, 16), seed=1104, layout=1)
+    A = b.A.copy()
+    bad = [3, 10000, 20010]
+    for k in bad:
+        A[b.off[k]] = -1.0  # a_11 < 0
+    b = wl.Batch(A, b.n, b.off, b.layout)
+    X, info = _run_host(b, "c64", mixed=True)
+    _, Xo, info_o, A_wide = oracle_inv(orc, b, "c64")
+    assert np.array_equal(info, info_o)
+    assert sorted(np.flatnonzero(info).tolist()) == bad and np.all(info[bad] == 1)
+    for k in bad:
+        T = int(b.n[k]) * (int(b.n[k]) + 1) // 2
+        assert np.all(np.isnan(np.real(X[b.off[k]:b.off[k] + T])))
+
+
 def test_rejects_matrices_not_back_to_back():
     import torch
     from paper_1111_4144_gb300 import _lib as L, api
