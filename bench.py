@@ -60,6 +60,8 @@ def parse():
                     help="time the blocked path instead: one FP32 matrix of this order, lambda log-spaced over "
                          "[1, 1e4], tensor-core products (prints one JSON line)")
     ap.add_argument("--blocked-prec", default="tf32", choices=["tf32", "fp32", "fp64"])
+    ap.add_argument("--blocked-pivots", default="fp64", choices=["fp64", "fp32"],
+                    help="pivots of the FP32 / TF32 blocked run: FP64 (the large workload's setting) or FP32")
     ap.add_argument("--blocked-refine", type=int, default=2,
                     help="refinement steps of the FP32 / TF32 blocked run (the large workload takes 2, with FP64 "
                          "pivots)")
@@ -842,10 +844,11 @@ def run_blocked(args, local_rank):
         A = wl.rotated_log_spaced_torch(N, decades=4.0, seed=1004, device=dev).to(dt).reshape(1, N, N)
     A = A.contiguous()
     kw = {}
+    piv = L.CHOL_FLAG_PIVOT64 if args.blocked_pivots == "fp64" else 0
     if args.blocked_prec == "tf32":
-        kw = dict(prec=L.CHOL_PREC_TF32_REFINE, refine_steps=args.blocked_refine, flags=L.CHOL_FLAG_PIVOT64)
+        kw = dict(prec=L.CHOL_PREC_TF32_REFINE, refine_steps=args.blocked_refine, flags=piv)
     elif args.blocked_prec == "fp32":
-        kw = dict(prec=L.CHOL_PREC_FP32_REFINE, refine_steps=args.blocked_refine, flags=L.CHOL_FLAG_PIVOT64)
+        kw = dict(prec=L.CHOL_PREC_FP32_REFINE, refine_steps=args.blocked_refine, flags=piv)
     X, info = api.inv(A, **kw)
     torch.cuda.synchronize()
     for _ in range(max(args.warmup - 1, 0)):
@@ -861,6 +864,7 @@ def run_blocked(args, local_rank):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     print(json.dumps({"blocked_order": N, "prec": args.blocked_prec, "refine_steps": kw.get("refine_steps", 0),
+                      "pivots": args.blocked_pivots if args.blocked_prec != "fp64" else "fp64",
                       "ms_per_inverse": ms,
                       "alg_tflops": N ** 3 / (ms / 1e3) / 1e12, "info": int(info.item()),
                       "device_error": L.chol_last_device_error(None)}), flush=True)
