@@ -266,8 +266,9 @@ chol_status_t chol_inv_backward(chol_dtype_t dt, int32_t batch, const int32_t* n
  *   chol_inv_batched.
  * The batch is cut into chunks of whole matrices (up to 16 per call, each at
  * least 8192 matrices or the whole batch) that pass through four device
- * slots and three internal streams (copy in, kernels, copy out), so the
- * copies of one chunk overlap the kernels and copies of the others.  The
+ * slots and four internal streams (copy in, two for the kernels of
+ * alternate chunks, copy out), so the copies of one chunk overlap the
+ * kernels and copies of the others.  The
  * call returns once everything is enqueued: `stream` waits for all of it,
  * and the host buffers must stay valid and unmodified until then.
  * ws: device workspace of chol_workspace_bytes(CHOL_CALL_INV_HOST, dt,

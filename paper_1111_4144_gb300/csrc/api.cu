@@ -428,8 +428,8 @@ HostSlotLayout host_slot_layout(chol_dtype_t dt, int32_t batch, int32_t max_n, i
 // free its slot again, and those that fork the stages from and join them to
 // the caller's stream.  Enqueueing holds the mutex.
 struct HostStreams {
-    cudaStream_t in = nullptr, run = nullptr, out = nullptr;
-    cudaEvent_t fork = nullptr, join[3] = {};
+    cudaStream_t in = nullptr, run[2] = {}, out = nullptr;  // chunks alternate between the two kernel streams
+    cudaEvent_t fork = nullptr, join[4] = {};
     cudaEvent_t loaded[kHostChunks] = {}, computed[kHostChunks] = {}, freed[kHostSlots] = {};
     std::mutex mu;
 };
@@ -443,9 +443,10 @@ HostStreams* host_streams() {
         HostStreams* h = new HostStreams();
         auto ev = [](cudaEvent_t* e) { return cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess; };
         bool ok = cudaStreamCreateWithFlags(&h->in, cudaStreamNonBlocking) == cudaSuccess &&
-                  cudaStreamCreateWithFlags(&h->run, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h->run[0], cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h->run[1], cudaStreamNonBlocking) == cudaSuccess &&
                   cudaStreamCreateWithFlags(&h->out, cudaStreamNonBlocking) == cudaSuccess && ev(&h->fork);
-        for (int k = 0; k < 3 && ok; ++k) ok = ev(&h->join[k]);
+        for (int k = 0; k < 4 && ok; ++k) ok = ev(&h->join[k]);
         for (int k = 0; k < kHostChunks && ok; ++k) ok = ev(&h->loaded[k]) && ev(&h->computed[k]);
         for (int k = 0; k < kHostSlots && ok; ++k) ok = ev(&h->freed[k]);
         if (!ok) {
@@ -611,7 +612,7 @@ chol_status_t chol_inv_batched_host(chol_dtype_t dt, int32_t batch, const int32_
     if (hs == nullptr) return CHOL_ERR_CUDA;
     std::lock_guard<std::mutex> lk(hs->mu);
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
-    cudaStream_t stage[3] = {hs->in, hs->run, hs->out};
+    cudaStream_t stage[4] = {hs->in, hs->run[0], hs->run[1], hs->out};
     if (cudaEventRecord(hs->fork, cs) != cudaSuccess) return CHOL_ERR_CUDA;
     for (cudaStream_t st2 : stage)
         if (cudaStreamWaitEvent(st2, hs->fork, 0) != cudaSuccess) return CHOL_ERR_CUDA;
@@ -646,7 +647,9 @@ chol_status_t chol_inv_batched_host(chol_dtype_t dt, int32_t batch, const int32_
             return CHOL_ERR_CUDA;
         if (cudaEventRecord(hs->loaded[k], hs->in) != cudaSuccess) return CHOL_ERR_CUDA;
         // kernels
-        if (cudaStreamWaitEvent(hs->run, hs->loaded[k], 0) != cudaSuccess) return CHOL_ERR_CUDA;
+        // a chunk's kernels fill only part of the GPU: consecutive chunks run side by side
+        cudaStream_t run = hs->run[k % 2];
+        if (cudaStreamWaitEvent(run, hs->loaded[k], 0) != cudaSuccess) return CHOL_ERR_CUDA;
         const intptr_t shift = sized ? (intptr_t)(e0 * (int64_t)es) - (intptr_t)pad : 0;
         const void* Ad = reinterpret_cast<const void*>(reinterpret_cast<intptr_t>(base + L.a) - shift);
         void* Xd = reinterpret_cast<void*>(reinterpret_cast<intptr_t>(base + L.x) - shift);
@@ -660,9 +663,9 @@ chol_status_t chol_inv_batched_host(chol_dtype_t dt, int32_t batch, const int32_
                 const uint32_t nb = (uint32_t)n_host[b0 + b];
                 if (nb < (uint32_t)kClasses) present[nb] = 1;
             }
-        st = enqueue_inv(dt, p, base + L.ws, hs->run, false, o, sized ? present : nullptr);
+        st = enqueue_inv(dt, p, base + L.ws, run, false, o, sized ? present : nullptr);
         if (st != CHOL_OK) return st;
-        if (cudaEventRecord(hs->computed[k], hs->run) != cudaSuccess) return CHOL_ERR_CUDA;
+        if (cudaEventRecord(hs->computed[k], run) != cudaSuccess) return CHOL_ERR_CUDA;
         // copy out, then free the slot
         if (cudaStreamWaitEvent(hs->out, hs->computed[k], 0) != cudaSuccess) return CHOL_ERR_CUDA;
         if (cudaMemcpyAsync(Xh + e0 * (int64_t)es, base + L.x + pad, bytes, cudaMemcpyDeviceToHost, hs->out) !=
@@ -675,7 +678,7 @@ chol_status_t chol_inv_batched_host(chol_dtype_t dt, int32_t batch, const int32_
     if (info_host && cudaMemcpyAsync(info_host, info_dev, (size_t)batch * sizeof(int32_t), cudaMemcpyDeviceToHost,
                                      hs->out) != cudaSuccess)
         return CHOL_ERR_CUDA;
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 4; ++k)
         if (cudaEventRecord(hs->join[k], stage[k]) != cudaSuccess || cudaStreamWaitEvent(cs, hs->join[k], 0) != cudaSuccess)
             return CHOL_ERR_CUDA;
     return CHOL_OK;

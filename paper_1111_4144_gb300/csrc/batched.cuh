@@ -152,8 +152,7 @@ CHOL_D int factor_unrolled(Acc& m, typename traits<V>::real (&dinv)[N > 0 ? N : 
             for (int k = 0; k < N; ++k)
                 if (k < i) td -= pivot64_term(col[k]);
             t = (R)td;
-            rii = (R)sqrt(td);
-            inv = (R)(1.0 / sqrt(td));
+            pivot_root64(td, rii, inv);
             if (info == 0 && !pivot_ok(td)) info = i + 1;
         } else {
             const R aii = t;
@@ -692,8 +691,7 @@ CHOL_D void warp_one(const BatchParams& p, int N, int64_t b, int64_t o, V* S, in
             double td = (double)aii;
             for (int k = 0; k < i; ++k) td -= pivot64_term(S[k * LD + i]);
             if (info == 0 && !pivot_ok(td)) info = i + 1;
-            rii = (R)sqrt(td);
-            inv = (R)(1.0 / sqrt(td));
+            pivot_root64(td, rii, inv);
         } else {
             if (gate && pivot_cancels(tt, aii)) redo = true;
             if (info == 0 && !pivot_ok(tt)) info = i + 1;

@@ -447,8 +447,7 @@ k_blk_potrf_blk(T* X, int64_t ldx, int k0, int b, T* Rinv, int* failed, int32_t*
                         if (k < i) td -= (double)a[k] * (double)a[k];
                     td = __shfl_sync(0xffffffffu, td, i);
                     if (!bad && !(td > 0.0 && isfinite(td))) bad = o + i + 1;
-                    rii = (T)sqrt(td);
-                    inv = (T)(1.0 / sqrt(td));
+                    pivot_root64(td, rii, inv);
                 } else {
                     if (!bad && !(tt > T(0) && isfinite(tt))) bad = o + i + 1;
                     pivot_root(tt, rii, inv);

@@ -125,6 +125,31 @@ CHOL_D void pivot_root(double t, double& rii, double& inv) {
     inv = 1.0 / rii;
 }
 
+// Eq. 3's root from an argument t accumulated in FP64 (FP64 pivots), for a
+// factor held in R: r_ii = sqrt(t) and 1/r_ii.  For FP32 factors the
+// hardware FP32 reciprocal square root of t is refined by one
+// Newton-Raphson step taken in FP64 arithmetic, y <- y + (y/2)(1 - t y^2),
+// good to about 44 bits before the rounding to FP32 (the FP64 square root
+// and division are long instruction sequences on the FP64 pipe); outside the
+// normal FP32 range of t, and for FP64 factors, the FP64 square root and
+// division.
+template <typename R>
+CHOL_D void pivot_root64(double t, R& rii, R& inv) {
+    if constexpr (sizeof(R) == 4) {
+        if (t >= 1.2e-38 && t <= 3.0e38) {
+            const double y = (double)rsqrtf((float)t);
+            const double e = fma(-(t * y), y, 1.0);
+            const double yi = fma(0.5 * y, e, y);
+            inv = (R)yi;
+            rii = (R)(t * yi);
+            return;
+        }
+    }
+    const double r = sqrt(t);
+    rii = (R)r;
+    inv = (R)(1.0 / r);
+}
+
 // ---------------------------------------------------------------------------
 // Compensated FP32 accumulation (Ogita, Rump & Oishi, "Accurate sum and dot
 // product", 2005, Algorithm Dot2): a dot product carried as an unevaluated

@@ -487,8 +487,7 @@ k_group(BatchParams p) {
                     }
                 }
                 if (info == 0 && !pivot_ok(td)) info = i + 1;
-                rii = (R)sqrt(td);
-                inv = (R)(1.0 / sqrt(td));
+                pivot_root64(td, rii, inv);
             } else {
                 if (gate && pivot_cancels(tt, aii)) redo = true;
                 if (info == 0 && !pivot_ok(tt)) info = i + 1;

@@ -35,9 +35,12 @@ def _run_flat(tag, H, n, m, hoff, woff, sigma2, **kw):
     return W.cpu().numpy(), info.cpu().numpy()
 
 
+@pytest.mark.parametrize("sizes", [(3, 4, 8, 16, 23), (1, 3, 4, 8, 16)], ids=["to23", "to16_tiled"])
 @pytest.mark.parametrize("tag", ["c64", "c128", "f32", "f64"])
-def test_mmse_filter_matches_oracle(orc, tag):
-    H, n, m, hoff, woff = wl.mimo_channels(900, sizes=(3, 4, 8, 16, 23), seed=3100)
+def test_mmse_filter_matches_oracle(orc, tag, sizes):
+    """Orders up to 23 (the warp-per-matrix products) and up to 16 with up
+    to 32 rows (the register-tiled products), mixed in one flat batch."""
+    H, n, m, hoff, woff = wl.mimo_channels(900, sizes=sizes, seed=3100)
     if tag in ("f32", "f64"):
         H = H.real.copy()
     sigma2 = 0.1
