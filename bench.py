@@ -769,14 +769,15 @@ def run_profile_case(args, local_rank):
     DTYPE:N:BATCH[:OPT...], OPT one of rK (FP32 + K refinement steps), ldl
     (the LDL form), bwd (the timed region runs the adjoint of the inverse,
     dA for G = I, instead), vK (kernel variant K of the order, pinned in the
-    tuning table), p64 (FP64 pivots)."""
+    tuning table), p64 (FP64 pivots), mmse (the timed region runs the MMSE
+    filters of BATCH channel matrices of 2N x N instead)."""
     import torch
     from paper_1111_4144_gb300 import _lib as L, api, workloads as wl
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     tag, N, batch, *opts = args.profile_case.split(":")
     N, batch = int(N), int(batch)
-    kw, bwd = {}, False
+    kw, bwd, mmse_case = {}, False, False
     for o in opts:
         if o.startswith("r") and o[1:].isdigit():
             kw.update(prec=L.CHOL_PREC_FP32_REFINE, refine_steps=int(o[1:]))
@@ -789,6 +790,8 @@ def run_profile_case(args, local_rank):
             L.check(L.chol_tune_set(dtc, N, int(o[1:])), "chol_tune_set")
         elif o == "p64":
             kw["flags"] = kw.get("flags", 0) | L.CHOL_FLAG_PIVOT64
+        elif o == "mmse":
+            mmse_case = True
         else:
             raise SystemExit(f"--profile-case: unknown option {o!r}")
     npd = {"f32": np.float32, "f64": np.float64, "c64": np.complex64, "c128": np.complex128}[tag]
@@ -802,6 +805,12 @@ def run_profile_case(args, local_rank):
     X = torch.zeros_like(A)
     info = torch.empty(batch, dtype=torch.int32, device=dev)
     call = lambda: api.inv(A, max_n=N, layout=wl.LAYOUT_PACKED, X=X, info=info, **kw)
+    if mmse_case:
+        rng = np.random.default_rng(1010)
+        Hn = (rng.standard_normal((1024, 2 * N, N)) + 1j * rng.standard_normal((1024, 2 * N, N))) * np.sqrt(0.5)
+        H = torch.from_numpy(np.tile(Hn.astype(npd), ((batch + 1023) // 1024, 1, 1))[:batch]).to(dev)
+        Wm = torch.empty((batch, N, 2 * N), dtype=H.dtype, device=dev)
+        call = lambda: api.mmse(H, sigma2=0.1, W=Wm, info=info, **kw)
     if bwd:
         call()
         G = torch.zeros((batch, N, N), dtype=A.dtype, device=dev)

@@ -435,17 +435,15 @@ k_blk_potrf_blk(T* X, int64_t ldx, int k0, int b, T* Rinv, int* failed, int32_t*
 #pragma unroll
             for (int k = 0; k < kSB; ++k) a[k] = S[(o + k) * LD + o + lane];
             int bad = 0;
+            // pivot64: lane j's Eq. 3 argument in FP64, a_jj less r_kj^2 over
+            // the rows k finished so far (one term per row, k ascending)
+            double dl = pivot64 ? ds[o + lane] : 0.0;
 #pragma unroll
             for (int i = 0; i < kSB; ++i) {
                 const T tt = __shfl_sync(0xffffffffu, a[i], i);  // Eq. 3 argument (row i, column i)
                 T rii, inv;
                 if (pivot64) {
-                    // lane i: a[k], k < i, hold r_{o+k, o+i}
-                    double td = ds[o + lane];
-#pragma unroll
-                    for (int k = 0; k < kSB; ++k)
-                        if (k < i) td -= (double)a[k] * (double)a[k];
-                    td = __shfl_sync(0xffffffffu, td, i);
+                    const double td = __shfl_sync(0xffffffffu, dl, i);
                     if (!bad && !(td > 0.0 && isfinite(td))) bad = o + i + 1;
                     pivot_root64(td, rii, inv);
                 } else {
@@ -454,6 +452,7 @@ k_blk_potrf_blk(T* X, int64_t ldx, int k0, int b, T* Rinv, int* failed, int32_t*
                 }
                 if (lane == i) a[i] = rii;
                 else if (lane > i) a[i] = a[i] * inv;  // r_ij, Eq. 4
+                if (pivot64 && lane > i) dl -= (double)a[i] * (double)a[i];
                 if (lane == 0) dv[o + i] = inv;
 #pragma unroll
                 for (int k = 0; k < kSB; ++k) {  // fixed trip count: every index stays a constant
