@@ -115,7 +115,9 @@ __global__ void k_apply(MmseParams p) {
 constexpr int kMN = 16;        // orders
 constexpr int kMM = 32;        // rows of H
 constexpr int kGLD = kMN + 4;  // row stride of H in k_gram16 and of X in k_apply16
-constexpr int kALD = kMM + 4;  // row stride of H^* (transposed) in k_apply16
+// row stride of H^* (transposed) in k_apply16: odd, so that the transposing
+// stores of a warp's consecutive elements land on distinct banks
+constexpr int kALD = kMM + 1;
 
 // acc += a b (complex64 on paired FP32 instructions: the two parts of an entry)
 template <typename V>
