@@ -181,41 +181,12 @@ ClassFork* class_fork(bool may_create) {
     return &f;
 }
 
-// Padded launches (FP32 orders 33-64 of a bucketed batch): the classes
-// 8g+33..8g+40 share one launch of the order-(8g+40) register kernel, each
-// matrix embedded as diag(A, I), when that order is within max_n and its
-// tuned variant is that kernel.  Not with options that take other kernels
-// (FP64 pivots, the cancellation test, the LDL form, the comparison methods)
-// nor in plans timing each order's kernel.  Returns the group's top order,
-// or 0 for an exact-order launch.
-int pad_group_top(chol_dtype_t dt, const BatchParams& p, int c) {
-    if (dt != CHOL_F32 || p.cls_count == nullptr || c < 33 || c > 64 || t_timing != nullptr) return 0;
-    if (p.flags & (CHOL_FLAG_PIVOT64 | CHOL_FLAG_PIVOT64_AUTO | CHOL_FLAG_LDL | CHOL_FLAG_METHOD_ES |
-                   CHOL_FLAG_METHOD_TMO))
-        return 0;
-    const int top = 40 + ((c - 33) / 8) * 8;
-    if (top > p.max_n || variant_of(CHOL_F32, top) != 0) return 0;
-    return top;
-}
-
-// One kernel launch of launch_dtype: the class, and the first class of a padded group (0: none).
-struct ClassLaunch {
-    int cls, pad_lo;
-};
-
-cudaError_t launch_item(chol_dtype_t dt, const BatchParams& p, const ClassLaunch& it, cudaStream_t st, bool dry) {
-    BatchParams q = p;
-    q.pad_lo = it.pad_lo;
-    return dry ? launch_dtype_class(dt, q, it.cls, p.batch, st, true) : launch_class_timed(dt, q, it.cls, st);
-}
-
 // Every size class of a batch, largest orders first: one class for uniform
 // batches, otherwise every class 1..max_n (a class kernel with no members
 // exits at once).  `present` (optional, host memory): present[c] != 0 for
 // the orders that occur in the batch, when the caller knows them; other
-// classes are skipped.  FP32 orders 33-64 may go as padded groups of eight
-// (pad_group_top).
-// With kForkMinClasses or more launches the kernels are dealt round-robin to
+// classes are skipped.
+// With kForkMinClasses or more classes the kernels are dealt round-robin to
 // side streams forked from `s` and joined back (inside a capture: parallel
 // branches of the graph).  Fewer, larger classes each fill the GPU and run on
 // `s` in order (three classes of 349,525 matrices measured no faster side by
@@ -227,33 +198,15 @@ cudaError_t launch_dtype(chol_dtype_t dt, const BatchParams& p, cudaStream_t s, 
         if (dry) return launch_dtype_class(dt, p, p.max_n, p.batch, s, true);
         return launch_class_timed(dt, p, p.max_n, s);
     }
-    ClassLaunch items[kClasses];
-    int nitems = 0;
-    for (int c = p.max_n; c >= 1; --c) {
-        const int top = pad_group_top(dt, p, c);
-        if (top != 0) {
-            if (c != top) continue;  // taken by the group's launch
-            bool any = present == nullptr;
-            for (int k = top - 7; k <= top && !any; ++k) any = present[k] != 0;
-            if (any) items[nitems++] = {top, top - 7};
-            continue;
-        }
-        if (present && !present[c]) continue;
-        items[nitems++] = {c, 0};
-    }
-    const bool want_fork = nitems >= kForkMinClasses && t_timing == nullptr;
+    int nclasses = 0;
+    for (int c = p.max_n; c >= 1; --c) nclasses += (!present || present[c]) ? 1 : 0;
+    const bool want_fork = nclasses >= kForkMinClasses && t_timing == nullptr;
     if (dry || !want_fork) {
-        // the dry pass (before a plan's capture) makes the side streams and
-        // sets up every class's exact-order kernel too (a plan timing each
-        // order's kernel launches those)
+        // the dry pass (before a plan's capture) makes the side streams
         if (dry && want_fork) class_fork(true);
-        for (int c = p.max_n; dry && c >= 1; --c) {
+        for (int c = p.max_n; c >= 1; --c) {
             if (present && !present[c]) continue;
-            cudaError_t e = launch_dtype_class(dt, p, c, p.batch, s, true);
-            if (e != cudaSuccess) return e;
-        }
-        for (int k = 0; k < nitems; ++k) {
-            cudaError_t e = launch_item(dt, p, items[k], s, dry);
+            cudaError_t e = dry ? launch_dtype_class(dt, p, c, p.batch, s, true) : launch_class_timed(dt, p, c, s);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -262,16 +215,22 @@ cudaError_t launch_dtype(chol_dtype_t dt, const BatchParams& p, cudaStream_t s, 
     if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return cudaGetLastError();
     ClassFork* f = class_fork(cap == cudaStreamCaptureStatusNone);
     if (f == nullptr) {
-        for (int k = 0; k < nitems; ++k) {
-            cudaError_t e = launch_item(dt, p, items[k], s, false);
+        for (int c = p.max_n; c >= 1; --c) {
+            if (present && !present[c]) continue;
+            cudaError_t e = launch_class_timed(dt, p, c, s);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
     }
-    const int used = std::min(nitems, kForkStreams);
+    const int used = std::min(nclasses, kForkStreams);
     cudaError_t e = cudaEventRecord(f->fork, s);
     for (int k = 0; e == cudaSuccess && k < used; ++k) e = cudaStreamWaitEvent(f->side[k], f->fork, 0);
-    for (int k = 0; e == cudaSuccess && k < nitems; ++k) e = launch_item(dt, p, items[k], f->side[k % used], false);
+    int next = 0;
+    for (int c = p.max_n; e == cudaSuccess && c >= 1; --c) {
+        if (present && !present[c]) continue;
+        e = launch_class_timed(dt, p, c, f->side[next]);
+        next = (next + 1) % used;
+    }
     // join every side stream that waited on the fork, also after an error,
     // so that a capture in progress is left with no unjoined work
     for (int k = 0; k < used; ++k) {

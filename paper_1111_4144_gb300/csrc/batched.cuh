@@ -37,7 +37,6 @@ struct BatchParams {
     uint64_t order_mask[2];    // bit c: order c may occur (bucketing rejects the others)
     unsigned long long* redo_count;  // matrices redone with FP64 pivots (CHOL_FLAG_PIVOT64_AUTO)
     int32_t aligned16;         // A, R and X all start on 16-byte boundaries (16-byte copies allowed)
-    int32_t pad_lo;            // 0, or a padded launch of the order-max kernel over classes pad_lo.. (wide.cuh)
 };
 
 // CHOL_FLAG_PIVOT64_AUTO: a matrix whose FP32 pass saw cancellation in Eq. 3

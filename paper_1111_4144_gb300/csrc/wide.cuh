@@ -74,62 +74,9 @@ using WideCfg = GroupCfg<float, N, 32, 4>;
 template <int N>
 constexpr int wide_minb() { return N <= 48 ? 3 : 2; }
 
-// Padded launches (PAD): one order-N kernel takes the members of classes
-// p.pad_lo..N of a bucketed batch, each matrix of order n <= N embedded as
-// diag(A, I) (identity rows and columns n..N-1, so that R = diag(R_A, I) and
-// X = diag(A^{-1}, I)); staging and storing map element (i, j) between the
-// order-n matrix as stored and the order-N mirror, one warp per matrix.
-// One launch over eight orders replaces eight launches of a few thousand
-// matrices each, at the price of the padded rows' arithmetic.
-template <int N>
-CHOL_D void wide_stage_padded(const BatchParams& p, const float* A, float* M, int64_t o, int n, const uint8_t* s_i,
-                              const uint8_t* s_j, int lane) {
-    constexpr int TN = tri(N);
-    constexpr int U = 8;
-#pragma unroll 1
-    for (int e0 = 0; e0 < TN; e0 += 32 * U) {
-        float v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = e0 + 32 * u + lane;
-            if (e < TN) {
-                const int i = s_i[e], j = s_j[e];
-                v[u] = (j < n) ? A[o + (p.layout ? (int64_t)pidx(n, i, j) : (int64_t)i * n + j)] : (i == j ? 1.f : 0.f);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int e = e0 + 32 * u + lane;
-            if (e < TN) M[e] = v[u];
-        }
-    }
-}
-template <int N>
-CHOL_D void wide_store_padded(const BatchParams& p, float* out, const float* M, int64_t o, int n, int info,
-                              const uint8_t* s_i, const uint8_t* s_j, bool is_factor, bool fill_lower, int lane) {
-    constexpr int TN = tri(N);
-    const float qn = nan_v<float>();
-    for (int e = lane; e < TN; e += 32) {
-        const int i = s_i[e], j = s_j[e];
-        if (j >= n) continue;  // the padding
-        const float v = info ? qn : M[e];
-        if (p.layout) {
-            out[o + pidx(n, i, j)] = v;
-        } else {
-            out[o + (int64_t)i * n + j] = v;
-            if (i != j) {
-                if (is_factor) out[o + (int64_t)j * n + i] = info ? qn : 0.f;
-                else if (fill_lower) out[o + (int64_t)j * n + i] = v;
-            }
-        }
-    }
-}
-
-// GATE: CHOL_FLAG_PIVOT64_AUTO's cancellation test.  PAD: a padded launch
-// (above; GATE off).
-template <int N, int MINB = wide_minb<N>(), bool GATE = false, bool PAD = false>
+// GATE: CHOL_FLAG_PIVOT64_AUTO's cancellation test.
+template <int N, int MINB = wide_minb<N>(), bool GATE = false>
 __global__ void __launch_bounds__(128, MINB) k_wide(BatchParams p) {
-    static_assert(!(GATE && PAD), "padded launches run without the cancellation test");
     static_assert(N >= kWideLo && N <= kWideHi, "the wide kernel covers orders 33..64");
     using C = WideCfg<N>;
     constexpr int TN = C::TN;
@@ -161,19 +108,7 @@ __global__ void __launch_bounds__(128, MINB) k_wide(BatchParams p) {
         s_i[e] = (uint8_t)i;
         s_j[e] = (uint8_t)(e - pidx(N, i, i) + i);
     }
-    // the members taken: class N's, or (PAD) those of classes pad_lo..N,
-    // consecutive in the bucketing permutation
-    int count = 0, first = 0;
-    if constexpr (PAD) {
-        for (int c = p.pad_lo; c <= N; ++c) count += p.cls_count[c];
-        first = p.cls_start[p.pad_lo];
-    } else {
-        count = class_count(p, N);
-    }
-    auto member = [&](int k) -> int64_t {
-        if constexpr (PAD) return p.perm[first + k];
-        else return member_index(p, N, k);
-    };
+    const int count = class_count(p, N);
     const int nchunks = (count + MPC - 1) / MPC;
     const float* A = static_cast<const float*>(p.A);
     float* Xo = static_cast<float*>(p.X);
@@ -186,34 +121,28 @@ __global__ void __launch_bounds__(128, MINB) k_wide(BatchParams p) {
         const int m = min(MPC, count - chunk * MPC);
         int ok = 1;
         if (t < m) {
-            const int64_t b = member(chunk * MPC + t);
+            const int64_t b = member_index(p, N, chunk * MPC + t);
             const int64_t o = matrix_offset(p, N, b);
             s_off[t] = o;
             ok = (o % C::U) == 0;
         }
-        const bool vec = (__syncthreads_and(ok) != 0) && p.layout == 1 && p.aligned16 && !PAD;
+        const bool vec = (__syncthreads_and(ok) != 0) && p.layout == 1 && p.aligned16;
+        group_stage<float, N, C>(p, A, mirs, s_off, s_i, s_j, m, vec, s_bar);
+        cp_async_wait<0>();
+        bool late = false;
+        const bool bulk_in = vec && C::TN / C::U > 0;
+        if (bulk_in) late = !mbar_wait_bounded(s_bar, *s_phase);
+        if (__syncthreads_or(late)) {
+            // a bulk copy did not arrive within the bound: report, wait once
+            // more (bounded) for the copies in flight, and stop
+            if (t == 0) report_error(p.err, CHOL_ERR_TIMEOUT);
+            mbar_wait_bounded(s_bar, *s_phase);
+            return;
+        }
+        if (bulk_in && t == 0) *s_phase ^= 1u;  // read again only after later barriers
+
         const bool live = q < m;
         float* M = reinterpret_cast<float*>(mirs + (size_t)(live ? q : 0) * C::STRIDE);
-        // this warp's matrix order (PAD: its own, padded to N)
-        const int nq = (PAD && live) ? p.n[member(chunk * MPC + q)] : N;
-        if constexpr (PAD) {
-            if (live) wide_stage_padded<N>(p, A, M, s_off[q], nq, s_i, s_j, h);
-            __syncthreads();
-        } else {
-            group_stage<float, N, C>(p, A, mirs, s_off, s_i, s_j, m, vec, s_bar);
-            cp_async_wait<0>();
-            bool late = false;
-            const bool bulk_in = vec && C::TN / C::U > 0;
-            if (bulk_in) late = !mbar_wait_bounded(s_bar, *s_phase);
-            if (__syncthreads_or(late)) {
-                // a bulk copy did not arrive within the bound: report, wait once
-                // more (bounded) for the copies in flight, and stop
-                if (t == 0) report_error(p.err, CHOL_ERR_TIMEOUT);
-                mbar_wait_bounded(s_bar, *s_phase);
-                return;
-            }
-            if (bulk_in && t == 0) *s_phase ^= 1u;  // read again only after later barriers
-        }
         float* dinv = s_dinv + q * N;
         // own columns' upper parts (rows r <= j) from the mirror; other rows
         // are don't-care until the inverse fills them
@@ -260,11 +189,7 @@ __global__ void __launch_bounds__(128, MINB) k_wide(BatchParams p) {
         if (live && h == 0) s_info[q] = redo ? kInfoRedo : info;
         if (store_R || !p.want_inv) {
             __syncthreads();
-            if constexpr (PAD) {
-                if (live) wide_store_padded<N>(p, Ro, M, s_off[q], nq, s_info[q], s_i, s_j, true, false, h);
-            } else {
-                group_store<float, N, C, GATE>(p, Ro, mirs, s_off, s_info, s_i, s_j, m, vec, true, false, true);
-            }
+            group_store<float, N, C, GATE>(p, Ro, mirs, s_off, s_info, s_i, s_j, m, vec, true, false, true);
             __syncthreads();
         }
         if (p.want_inv) {
@@ -317,15 +242,11 @@ __global__ void __launch_bounds__(128, MINB) k_wide(BatchParams p) {
                 }
             });
             __syncthreads();
-            if constexpr (PAD) {
-                if (live) wide_store_padded<N>(p, Xo, M, s_off[q], nq, s_info[q], s_i, s_j, false, p.fill_lower != 0, h);
-            } else {
-                group_store<float, N, C, GATE>(p, Xo, mirs, s_off, s_info, s_i, s_j, m, vec, false,
-                                            p.fill_lower != 0, true);
-            }
+            group_store<float, N, C, GATE>(p, Xo, mirs, s_off, s_info, s_i, s_j, m, vec, false, p.fill_lower != 0,
+                                        true);
         }
         if (p.info)
-            for (int k = t; k < m; k += THREADS) p.info[member(chunk * MPC + k)] = s_info[k];
+            for (int k = t; k < m; k += THREADS) p.info[member_index(p, N, chunk * MPC + k)] = s_info[k];
         fence_async_smem();  // the next chunk's bulk copies overwrite the mirrors
         __syncthreads();
     }
@@ -344,10 +265,10 @@ __global__ void __launch_bounds__(128, MINB) k_wide(BatchParams p) {
 
 namespace cholinv {
 
-template <int N, bool GATE, bool PAD = false>
+template <int N, bool GATE>
 static cudaError_t launch_wide_t(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
     using C = WideCfg<N>;
-    auto kern = k_wide<N, wide_minb<N>(), GATE, PAD>;
+    auto kern = k_wide<N, wide_minb<N>(), GATE>;
     static std::once_flag once;
     static int per_sm = 1;
     static cudaError_t setup_err = cudaSuccess;
@@ -365,13 +286,8 @@ static cudaError_t launch_wide_t(const BatchParams& p, int upper_count, cudaStre
     return cudaGetLastError();
 }
 
-// Orders that end a padded group of eight also have the padded kernel.
-constexpr bool wide_pad_top(int n) { return n % 8 == 0; }
-
 template <int N>
 static cudaError_t launch_wide(const BatchParams& p, int upper_count, cudaStream_t s, bool dry) {
-    if constexpr (wide_pad_top(N))
-        if (p.pad_lo > 0 && p.pad_lo < N) return launch_wide_t<N, false, true>(p, upper_count, s, dry);
     if (p.flags & CHOL_FLAG_PIVOT64_AUTO) return launch_wide_t<N, true>(p, upper_count, s, dry);
     return launch_wide_t<N, false>(p, upper_count, s, dry);
 }

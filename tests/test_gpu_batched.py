@@ -472,57 +472,3 @@ def test_order_set_launches_only_stated_orders(orc):
     for k in np.flatnonzero(b.n != 16)[:200]:
         o, T = int(b.off[k]), int(b.n[k]) * (int(b.n[k]) + 1) // 2
         assert np.array_equal(Xa[o:o + T], Xb[o:o + T])
-
-
-@pytest.mark.parametrize("max_n", [64, 50])
-@pytest.mark.parametrize("layout", [0, 1])
-def test_padded_wide_groups(orc, layout, max_n):
-    """FP32 batches of mixed orders 33..max_n go to the register kernel in
-    padded groups of eight orders (8g+33..8g+40 on the order-(8g+40)
-    kernel, each matrix embedded as diag(A, I)); with max_n = 50 the orders
-    49-50 stay on their own kernels.  Against the oracle (X, R, info, the
-    dense lower half), and bit for bit against the same matrices inverted
-    one order at a time (the padding contributes exact zeros only)."""
-    from gpu_helpers import sub_batch
-    from paper_1111_4144_gb300 import _lib as L
-    b = wl.uneven_loguniform(900, nmin=33, nmax=max_n, seed=720 + max_n, layout=layout)
-    assert set(b.n.tolist()) == set(range(33, max_n + 1))
-    for N in range(33, max_n + 1):
-        assert L.chol_tune_get(L.CHOL_F32, N) == 0
-    X, info, R = run_inv(b, "f32", mixed=True, want_R=True, fill_lower=(layout == 0))
-    Ro, Xo, info_o, A_wide = oracle_inv(orc, b, "f32", fill_lower=(layout == 0))
-    assert np.array_equal(info, info_o) and np.all(info == 0)
-    check_errors("f32", b, A_wide, upper_errors(b, X, Xo), "X (padded groups)")
-    check_errors("f32", b, A_wide, upper_errors(b, R, Ro), "R (padded groups)")
-    for N in (33, 40, 41, 48, max_n):
-        idx = np.flatnonzero(b.n == N)
-        sb = sub_batch(b, idx)
-        Xs, info_s, Rs = run_inv(sb, "f32", mixed=False, want_R=True, fill_lower=(layout == 0))
-        assert np.all(info_s == 0)
-        sx = sub_batch(b, idx, flat=X)
-        sr = sub_batch(b, idx, flat=R)
-        assert np.array_equal(sx.A, Xs), N
-        assert np.array_equal(sr.A, Rs), N
-
-
-def test_padded_group_non_pd_and_fp64_pivots(orc):
-    """A non-positive-definite matrix inside a padded group is flagged with
-    its own failing row and NaN-filled, its neighbours untouched; FP64 pivots
-    take the exact-order kernels and agree with the padded result."""
-    from paper_1111_4144_gb300 import _lib as L
-    b = wl.uneven_loguniform(200, nmin=33, nmax=64, seed=730, layout=1)
-    A = b.A.copy()
-    k = int(np.flatnonzero(b.n == 37)[0])
-    A[b.off[k] + 5] = -1e6  # a_{0,5} large: A is no longer positive definite
-    b = wl.Batch(A, b.n, b.off, b.layout)
-    X, info, _ = run_inv(b, "f32", mixed=True)
-    _, Xo, info_o, A_wide = oracle_inv(orc, b, "f32")
-    assert np.array_equal(info, info_o) and info[k] > 0 and np.count_nonzero(info) == 1
-    T = 37 * 38 // 2
-    assert np.all(np.isnan(X[b.off[k]:b.off[k] + T]))
-    good = info_o == 0
-    errs = upper_errors(b, np.where(np.isnan(X), 0, X), Xo)
-    kap = kappas(b, A_wide)
-    assert np.all(errs[good] <= tol32(kap[good]))
-    X64, info64, _ = run_inv(b, "f32", mixed=True, flags=L.CHOL_FLAG_PIVOT64)
-    assert np.array_equal(info64, info_o)
