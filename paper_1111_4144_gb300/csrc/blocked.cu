@@ -1231,47 +1231,57 @@ static chol_status_t blocked_one(const T* A, T* R, T* X, int n, int32_t* info, i
     k_nan_if_failed<T><<<g1, 256, 0, s>>>(X, (int64_t)n * n, failed);
     if (cudaGetLastError() != cudaSuccess) return CHOL_ERR_CUDA;
 
-    // ---------------- refinement (FP32 only): E = I - A X in FP64, X += X E
+    // ---------------- refinement (FP32 only): X += X E, E = I - A X.  The
+    // residual is formed transposed, E^T = I - X A (both are symmetric), so
+    // that the correction's right operand is read by rows, K-major, as the
+    // tensor cores take it.  X E = X - X A X is symmetric: only its upper half
+    // is formed, and after each step the upper half of X is mirrored.
     if (refine_steps > 0 && sizeof(T) == 4) {
         float* Af = w.take<float>((size_t)n * n);
         double* E = w.take<double>((size_t)n * n);
-        float* E32 = w.take<float>((size_t)n * n);
+        float* Et = w.take<float>((size_t)n * n);  // E^T, row-major
         const float* A32 = reinterpret_cast<const float*>(A);
         float* X32 = reinterpret_cast<float*>(X);
         k_sym_full<float><<<g1, 256, 0, s>>>(Af, A32, n);
+        CUtensorMap mapE;
+        const bool tc_corr = use_tc && make_map(&mapE, Et, n, n, n);
         for (int st = 0; st < refine_steps; ++st) {
             cudaError_t e;
             if (resid64) {
                 // IEEE FP64 accumulation of the exact FP64 products of the FP32 values
                 k_identity<double><<<g1, 256, 0, s>>>(E, n);
                 e = timed(kBlkResidual, gemm_flops(n, n, n, 0), s, [&] {
-                    return gemm<float, double, double, false, false>(n, n, n, -1.0, Af, n, X32, n, 1.0, E, n, 0,
+                    return gemm<float, double, double, false, false>(n, n, n, -1.0, X32, n, Af, n, 1.0, E, n, 0,
                                                                      nullptr, 0, s);
                 });
                 if (e != cudaSuccess) return CHOL_ERR_CUDA;
-                k_narrow<<<g1, 256, 0, s>>>(E32, E, (int64_t)n * n);
+                k_narrow<<<g1, 256, 0, s>>>(Et, E, (int64_t)n * n);
             } else {
                 // compensated FP32 pairs (about 48 bits), no FP64 arithmetic
                 e = timed(kBlkResidual, gemm_flops(n, n, n, 0), s, [&] {
                     const dim3 grid((n + GB_N - 1) / GB_N, (n + GB_M - 1) / GB_M);
-                    k_resid_f2<<<grid, GB_THREADS, 0, s>>>(n, Af, X32, E32);
+                    k_resid_f2<<<grid, GB_THREADS, 0, s>>>(n, X32, Af, Et);
                     return cudaGetLastError();
                 });
                 if (e != cudaSuccess) return CHOL_ERR_CUDA;
             }
             // the correction X E goes to a separate buffer (the FP64 one, now free): the
-            // product reads X while it runs
+            // product reads X while it runs.  On the tensor cores as split TF32 (FP32-level
+            // accuracy on a term of relative size kappa u), else on the CUDA cores
             float* Cx = reinterpret_cast<float*>(E);
-            e = timed(kBlkCorrection, gemm_flops(n, n, n, 0), s, [&] {
-                return gemm<float, float, float, false, false>(n, n, n, 1.0f, X32, n, E32, n, 0.0f, Cx, n, 0, nullptr,
-                                                               0, s);
+            e = timed(kBlkCorrection, gemm_flops(n, n, n, 1), s, [&] {
+                if (tc_corr)
+                    return umma_gemm(n, n, n, 1.f, mapX, 0, 0, mapE, 0, 0, 0.f, Cx, n, 1,
+                                     reinterpret_cast<float*>(part), part_elems, 1, umma_err, s);
+                return gemm<float, float, float, false, true>(n, n, n, 1.0f, X32, n, Et, n, 0.0f, Cx, n, 1, nullptr,
+                                                              0, s);
             });
             if (e != cudaSuccess) return CHOL_ERR_CUDA;
             k_axpy<<<g1, 256, 0, s>>>(X32, Cx, (int64_t)n * n);
+            // the upper half is the result (the lower half of Cx was not formed), mirrored in place
+            k_sym_full<float><<<g1, 256, 0, s>>>(X32, X32, n);
         }
-        // X E is not exactly symmetric in floating point: the upper half is
-        // the result, mirrored into the lower half (in place)
-        k_sym_full<float><<<g1, 256, 0, s>>>(X32, X32, n);
+        if (tc_corr) k_report_umma<<<1, 1, 0, s>>>(umma_err, failed, err_word);
         if (cudaGetLastError() != cudaSuccess) return CHOL_ERR_CUDA;
     }
     return CHOL_OK;
