@@ -92,6 +92,23 @@ def test_blocked_non_pd_info(orc):
     assert np.all(np.isnan(X[0]))
 
 
+@pytest.mark.parametrize("pivots", ["fp32", "fp64"])
+def test_blocked_fp32_non_pd_info(orc, pivots):
+    """FP32 input, FP32 or FP64 pivots (Eq. 3): the first row whose pivot
+    argument is not positive is reported, as the oracle reports it."""
+    from paper_1111_4144_gb300 import _lib as L
+    N = 300
+    b = wl.log_spaced(N, decades=2.0, seed=3)
+    A = b.A.reshape(1, N, N).astype(np.float32)
+    A[0, 200, 200] = -5.0
+    A[0, 250, 250] = -5.0
+    flags = L.CHOL_FLAG_PIVOT64 if pivots == "fp64" else 0
+    X, info = _run(A, flags=flags)
+    _, _, info_o = _oracle(orc, A[0].astype(np.float64))
+    assert info[0] == info_o == 201
+    assert np.all(np.isnan(X[0]))
+
+
 def _hermitian_pd(N, seed, decades=3.0):
     """A = U diag(lambda) U^H, U unitary (QR of a complex Gaussian), lambda
     log-spaced over [1, 10^decades]: complex Hermitian, kappa = 10^decades."""
