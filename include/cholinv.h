@@ -255,7 +255,11 @@ chol_status_t chol_inv_backward(chol_dtype_t dt, int32_t batch, const int32_t* n
  * paper has no counterpart for the data movement).
  *   A_host, X_host, n_host, off_host, info_host: host pointers.  Page-locked
  *   (pinned) memory gives full copy speed; with pageable memory the copies
- *   are staged by the driver and lose most of the overlap.
+ *   are staged by the driver and lose most of the overlap.  Each chunk's
+ *   copies start on a 128-byte boundary of host memory (copies from other
+ *   addresses run slower on GB300), so the copy in may also read up to 127
+ *   bytes of A_host before the chunk's first matrix, never before A_host
+ *   itself; X_host is written only where the batch's matrices are.
  *   Batch layout: either n_host == off_host == NULL (every matrix of order
  *   max_n, stored back to back), or both given, with the matrices stored
  *   back to back in index order (off_host[b+1] = off_host[b] + elements of

@@ -61,6 +61,35 @@ def test_odd_byte_offsets_and_refinement(orc):
     check_errors("f32", b, A_wide, upper_errors(b, X, Xo), "X")
 
 
+@pytest.mark.parametrize("tag,a_shift,x_shift", [("c64", 3, 5), ("f32", 7, 2)])
+def test_host_buffers_off_copy_boundaries(orc, tag, a_shift, x_shift):
+    """A_host and X_host as views a few elements into larger pinned buffers
+    (off 16- and 128-byte boundaries, A and X at different offsets): the
+    results match the oracle, and nothing of X's buffer outside the batch is
+    written."""
+    import torch
+    from paper_1111_4144_gb300 import api
+    from gpu_helpers import torch_dtype
+    b = (wl.mimo_covariance(20011, sizes=(4, 8, 16), seed=1105, layout=1) if tag == "c64"
+         else wl.uneven_loguniform(17001, nmin=3, nmax=5, seed=1105, layout=1))
+    A_np, _ = cast_batch(b, tag)
+    total = A_np.shape[0]
+    A_big = torch.zeros(total + 64, dtype=torch_dtype(tag)).pin_memory()
+    X_big = torch.full((total + 64,), 7.0, dtype=torch_dtype(tag)).pin_memory()
+    A_big[a_shift:a_shift + total] = torch.from_numpy(A_np)
+    A_h, X_h = A_big[a_shift:a_shift + total], X_big[x_shift:x_shift + total]
+    info_h = torch.full((b.batch,), -7, dtype=torch.int32).pin_memory()
+    h = api.HostInv(torch_dtype(tag), b.batch, int(b.n.max()), sizes=True, layout=b.layout)
+    s = torch.cuda.Stream()
+    h(A_h, X_h, torch.from_numpy(b.n).pin_memory(), torch.from_numpy(b.off).pin_memory(), info_h, stream=s)
+    s.synchronize()
+    Xb = X_big.numpy()
+    assert np.all(Xb[:x_shift] == 7.0) and np.all(Xb[x_shift + total:] == 7.0)
+    _, Xo, info_o, A_wide = oracle_inv(orc, b, tag)
+    assert np.array_equal(info_h.numpy(), info_o)
+    check_errors(tag, b, A_wide, upper_errors(b, Xb[x_shift:x_shift + total], Xo), "X")
+
+
 def test_info_of_every_chunk(orc):
     """Non-PD matrices in the first, a middle and the last chunk: info (copied
     back for the whole batch in one piece) flags exactly those, with the
