@@ -59,6 +59,30 @@ def test_mmse_filter_matches_oracle(orc, tag, sizes):
         assert err <= tol, (b, N, err, tol)
 
 
+def test_mmse_with_stated_orders(orc):
+    """The channels' order set stated (kernels for those orders only): the
+    filters match the oracle; a channel of an order outside the set gets
+    info = -1 and leaves the others untouched."""
+    H, n, m, hoff, woff = wl.mimo_channels(600, sizes=(4, 8, 16), seed=3101)
+    sigma2 = 0.1
+    W, info = _run_flat("c64", H, n, m, hoff, woff, sigma2, orders=(4, 8, 16))
+    assert np.all(info == 0)
+    Hw = H.astype(np.complex64).astype(np.complex128)
+    for b in range(0, len(n), 7):
+        N, M = int(n[b]), int(m[b])
+        Hb = Hw[hoff[b]:hoff[b] + M * N].reshape(M, N)
+        Wo, _ = orc.mmse_filter(Hb, sigma2)
+        A = np.conj(Hb).T @ Hb + sigma2 * np.eye(N)
+        err = np.linalg.norm(W[woff[b]:woff[b] + N * M].reshape(N, M) - Wo) / np.linalg.norm(Wo)
+        assert err <= 2 * float(tol32(np.linalg.cond(A))), (b, N, err)
+    W2, info2 = _run_flat("c64", H, n, m, hoff, woff, sigma2, orders=(4, 16))
+    assert np.all(info2[n == 8] == -1) and np.all(info2[n != 8] == 0)
+    from paper_1111_4144_gb300 import _lib as L, api
+    assert api.last_device_error() == L.CHOL_ERR_ARG
+    keep = np.concatenate([np.arange(woff[b], woff[b] + int(n[b]) * int(m[b])) for b in np.flatnonzero(n != 8)])
+    assert np.array_equal(W2[keep], W[keep])
+
+
 def test_mmse_uniform_tensor_form(orc):
     import torch
     from paper_1111_4144_gb300 import api
