@@ -114,7 +114,9 @@ typedef enum {
                                    products on tcgen05 tensor cores as error-corrected TF32 (three TF32
                                    products per FP32 product, FP32-level accuracy), then refine_steps
                                    refinement steps as for CHOL_PREC_FP32_REFINE */
-    CHOL_PREC_BF16_REFINE = 3   /* blocked large-N path: BF16 tensor-core products */
+    CHOL_PREC_BF16_REFINE = 3   /* reserved, every call returns CHOL_ERR_UNSUPPORTED: BF16 products (8
+                                   significant bits) leave the unrefined inverse of a kappa = 1e4 matrix
+                                   without a correct digit, so refinement from it does not converge */
 } chol_prec_t;
 
 /* opts->flags */

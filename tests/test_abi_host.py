@@ -75,6 +75,8 @@ FAKE = 0x100000  # a non-null pointer value; never dereferenced because validati
     (dict(flags=0x60), "UNSUPPORTED"),       # not with the LDL form
     (dict(prec=1, dt=1), "UNSUPPORTED"),
     (dict(prec=2), "UNSUPPORTED"),
+    (dict(prec=3), "UNSUPPORTED"),           # BF16 products: reserved
+    (dict(max_n=65, prec=3, ws=FAKE, ws_bytes=1 << 40), "UNSUPPORTED"),
     (dict(n=FAKE), "WORKSPACE"),
     (dict(n=FAKE, ws=FAKE + 8, ws_bytes=1 << 20), "WORKSPACE"),
     (dict(n=FAKE, ws=FAKE, ws_bytes=16), "WORKSPACE"),
