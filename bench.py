@@ -94,6 +94,12 @@ def alg_flops(n, cplx=True):
     return int(macs * (8 if cplx else 2))
 
 
+def fp32_fma_peak_tflops(sms, sm_mhz=2070.0):
+    """FP32 CUDA-core peak: every SM's 128 FP32 lanes retire one fused
+    multiply-add (2 flops) per clock, at the maximum SM clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -417,11 +423,18 @@ def extra_workloads(dev, stream, steps):
                 kms[N] += plan_t.kernel_ms(N) / reps
         torch.cuda.synchronize()
         buckets = {}
+        alu_peak = fp32_fma_peak_tflops(torch.cuda.get_device_properties(dev).multi_processor_count)
         for N in range(2, 65):
             cnt = int((b.n == N).sum())
             nb = cnt * 2 * (N * (N + 1) // 2) * 4
             buckets[str(N)] = {"matrices": cnt, "kernel_ms": kms[N], "gbs": nb / (kms[N] / 1e3) / 1e9,
                                "frac": nb / (kms[N] / 1e3) / 1e9 / hbm}
+            if N > 32 and kms[N] > 0:
+                # orders above 32 approach the FP32 ALU ridge: their algorithmic
+                # flops against the CUDA-core FMA peak as well
+                tf = alg_flops(np.full(cnt, N), cplx=False) / (kms[N] / 1e3) / 1e12
+                buckets[str(N)]["alg_tflops"] = tf
+                buckets[str(N)]["alu_frac"] = tf / alu_peak
         # the same batch in one persistent launch (CHOL_FLAG_SINGLE_LAUNCH), for comparison
         X1 = torch.zeros_like(A)
         plan1 = api.Plan(A, X1, n, off, 64, flags=L.CHOL_FLAG_SINGLE_LAUNCH)
@@ -452,6 +465,9 @@ def extra_workloads(dev, stream, steps):
             "per_order": buckets,
             "bytes_rule": "2 * N(N+1)/2 * 4 B per matrix (A upper read, X upper written)",
             "peak": hbm, "peak_source": peak_kind + " (hbm_gbs)",
+            "alu_peak_tflops": alu_peak,
+            "alu_rule": "orders 33-64: (N^3 - N) flops per matrix (Table 1's N^3/2 multiply-adds) over the order's "
+                        "kernel time, against SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
             "max_err_over_tol": r[0], "max_rel_err": r[1],
             "cpu_baseline": {"value": cpu_v, "unit": METRIC, "cores": thr, "kind": "oracle",
                              "sample": f"{len(idx)} seeded matrices of the batch"}}
