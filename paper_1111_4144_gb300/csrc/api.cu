@@ -384,7 +384,8 @@ size_t mmse_ws_matrices(chol_dtype_t dt, int32_t batch, int32_t max_n) {
 
 // ---------------------------------------------------------------------------
 // Host-resident batches (chol_inv_batched_host): chunks of whole matrices
-// move through kHostSlots device slots, one internal stream per slot.
+// move through kHostSlots device slots on four internal streams (copy in,
+// two for the kernels of alternate chunks, copy out).
 // ---------------------------------------------------------------------------
 constexpr int kHostSlots = 4;
 constexpr int kHostChunks = 16;         // chunks per call (fewer for small batches)
