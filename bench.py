@@ -196,6 +196,25 @@ def oracle_time(b, A_wide, min_wall=1.0):
     return reps * b.batch / el, threads, reps, res
 
 
+def oracle_time_single(b, A_wide, count, min_wall=0.5):
+    """The oracle on one thread over the batch's first `count` matrices (stored
+    back to back from offset 0); returns (inverses/s, matrices, passes)."""
+    import oracle
+    count = min(count, b.batch)
+    last = int(b.n[count - 1])
+    end = int(b.off[count - 1]) + (last * (last + 1) // 2 if b.layout else last * last)
+    A = np.ascontiguousarray(A_wide[:end])
+    cplx = np.iscomplexobj(A_wide)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.inv_batch(A, b.n[:count], b.off[:count], b.layout, cplx, nthreads=1)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_wall:
+            break
+    return reps * count / el, count, reps
+
+
 def upper_err_ratio(b, Xg, Xo, kappa, fp64):
     """max over matrices of (relative Frobenius error of the upper triangle) / tolerance."""
     n = b.n.astype(np.int64)
@@ -1016,9 +1035,13 @@ def run_ours(args, rank, world, local_rank):
                            "fp32_median_rel_err": r32[2], "info_nonzero": int(np.count_nonzero(info)),
                            "info_matches_oracle": bool(np.array_equal(info, info_o)),
                            "tolerance": "max(1e-7*kappa, 2.4e-7) relative Frobenius, upper triangle"}
+        cpu_1, cnt_1, reps_1 = oracle_time_single(b, A_wide, 131072)
         out["cpu_baseline"] = {"value": cpu_v, "unit": METRIC, "cores": threads, "kind": "oracle",
                                "sample": f"{reps} x the full {b.batch}-matrix batch, FP64 C oracle, "
-                                         f"{threads} threads"}
+                                         f"{threads} threads",
+                               "single_thread": {"value": cpu_1, "unit": METRIC, "cores": 1,
+                                                 "sample": f"{reps_1} x the batch's first {cnt_1} matrices, "
+                                                           f"FP64 C oracle, 1 thread"}}
         # plain FP64 form (complex128) of the same library on the same matrices
         A128 = torch.from_numpy(A_wide).to(dev)
         X128 = torch.zeros_like(A128)

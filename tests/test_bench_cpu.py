@@ -77,3 +77,19 @@ def test_condition_numbers_of_packed_matrices():
     A = np.array([1.0, 0.0, 100.0, 2.0, 1j, 2.0], dtype=np.complex128)
     b = wl.Batch(A, np.array([2, 2], dtype=np.int32), np.array([0, 3], dtype=np.int64), wl.LAYOUT_PACKED)
     assert bench.kappa_of(b, A) == pytest.approx([100.0, 3.0])
+
+
+def test_single_thread_oracle_timing_on_a_prefix(orc):
+    """The one-thread oracle figure runs on the first matrices of the batch
+    (a contiguous prefix of the packed buffer) and inverts them correctly."""
+    b = wl.mimo_covariance(300, sizes=(4, 8, 16), seed=7, layout=wl.LAYOUT_PACKED)
+    A = b.A.astype(np.complex64).astype(np.complex128)
+    v, count, reps = bench.oracle_time_single(b, A, 100, min_wall=0.0)
+    assert count == 100 and reps >= 1 and v > 0
+    v, count, _ = bench.oracle_time_single(b, A, 10 ** 6, min_wall=0.0)
+    assert count == 300
+    last = int(b.n[99])
+    end = int(b.off[99]) + last * (last + 1) // 2
+    _, X1, info1 = orc.inv_batch(A[:end], b.n[:100], b.off[:100], 1, True, nthreads=1)
+    _, Xa, infoa = orc.inv_batch(A, b.n, b.off, 1, True)
+    assert np.all(info1 == 0) and np.array_equal(X1, Xa[:end])
